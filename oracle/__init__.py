@@ -1,0 +1,22 @@
+"""Plain FP64 CPU oracle of the MOL^T Cahn-Hilliard hot path (arXiv 1611.04214).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import anything from this package.  The
+product path (the CUDA library and its binding) never imports it, and this
+package never imports the product path: the two share no code.
+
+The oracle is slow and literal on purpose.  Each function restates one passage
+of the paper (cited in its docstring) in FP64 numpy, in the paper's order and
+notation, with no blocking, fusion or reordering:
+
+* ``weights``   - local quadrature weights of the fast convolution (Sec. 3.2)
+* ``helmholtz`` - the 1D modified-Helmholtz inverse L^{-1} = (I - c d_xx)^{-1}
+                  by particular + homogeneous solution (Eq. L_Inverse, Iu, IL,
+                  IR, homogeneous)
+* ``solver``    - stage parameters, the 1D and 2D fixed-point stage solves
+                  (Eq. CH_BE_fixed2_factor, CH_BE_fixed_complete, Sec. 5.1),
+                  time schemes (BE, BDF2, SDIRK2, SDIRK3) and the discrete
+                  energy / mass.
+
+Readings of passages the paper leaves open are listed in each docstring.
+"""
