@@ -1,0 +1,171 @@
+/*
+ * molt.h - C ABI of the GB300 (sm_103a) MOL^T Cahn-Hilliard library.
+ *
+ * The library implements the hot path of arXiv 1611.04214 (Causley, Cho, Christlieb,
+ * "Method of lines transpose: energy gradient flows using direct operator inversion for
+ * phase field models"): the O(N) inversion of the 1D modified Helmholtz operator
+ * L = I - c d_xx by fast convolution (Sec. 3.2), applied line by line in x and y
+ * (Sec. 5), inside the lagged fixed-point stage solve of the Cahn-Hilliard equation
+ * u_t = -Lap(eps^2 Lap u - f(u)), f(u) = u^3 - u (Eq. CahnHilliard), stepped by BE,
+ * BDF2, SDIRK2, SDIRK3 or SDC2 (Sec. 3-4).
+ *
+ * Conventions for every entry point:
+ *  - C linkage; every call returns a molt_status (0 = MOLT_OK, negative = error) and never
+ *    throws.  After an error, molt_last_error(solver) returns a message (static lifetime
+ *    until the next call on that solver).
+ *  - Handles are opaque and owned by the library; create/destroy pairs free everything.
+ *  - Field buffers passed as "device" pointers are caller-owned device memory of nx*ny
+ *    elements, row-major [ny][nx] with x contiguous (1D problems: ny = 1), of the
+ *    solver's precision (float for MOLT_FP32, double for MOLT_FP64).  Device pointers must
+ *    be aligned to the element size.  "host" pointers are caller-owned host memory of the
+ *    same layout (pinned or pageable).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  All
+ *    work of a call is ordered on that stream; calls that return a number read it back and
+ *    synchronize that stream.
+ *  - One solver per stream at a time: a solver owns device workspace and time history and
+ *    is not safe for concurrent calls.
+ *  - Grid convention: a periodic line of n stored nodes has h = L/n (node n is node 0); a
+ *    Neumann or Dirichlet line of n stored nodes has both walls as nodes and h = L/(n-1).
+ *  - Dirichlet lines hold u = -1 on the walls (v = u + 1 = 0 per inversion, the wall value
+ *    compatible with Remark Laplacian).
+ */
+#ifndef MOLT_H
+#define MOLT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MOLT_OK = 0,
+    MOLT_ERR_ARG = -1,            /* bad size, parameter or pointer */
+    MOLT_ERR_NOT_CONVERGED = -2,  /* a stage hit max_iter; the field holds the last iterate */
+    MOLT_ERR_CUDA = -3,           /* a CUDA runtime call failed */
+    MOLT_ERR_OOM = -4,            /* device workspace could not be allocated */
+    MOLT_ERR_UNSUPPORTED = -5     /* valid request this build does not implement */
+} molt_status;
+
+typedef enum { MOLT_BC_PERIODIC = 0, MOLT_BC_NEUMANN = 1, MOLT_BC_DIRICHLET = 2 } molt_bc;
+typedef enum { MOLT_FP32 = 0, MOLT_FP64 = 1 } molt_precision;
+typedef enum {
+    MOLT_BE = 0,      /* Eq. CH_BE: one stage, tau = dt */
+    MOLT_BDF2 = 1,    /* Eq. BDF2: tau = 2dt/3; first step (and after a dt change) is BE */
+    MOLT_SDIRK2 = 2,  /* Sec. 4.2: two stages, eta = 1 - sqrt(2)/2 */
+    MOLT_SDIRK3 = 3,  /* Sec. 4.4: Alexander's three-stage method, eta = 0.43587 */
+    MOLT_SDC2 = 4     /* Sec. 4.3 Eq. SDC_fixed: BE level [0] + trapezoid level [1] */
+} molt_scheme;
+
+typedef struct molt_grid molt_grid;
+typedef struct molt_solver molt_solver;
+
+/* Solver parameters (Sec. 3-4, Eq. parameters). */
+typedef struct {
+    double eps;        /* interface width epsilon > 0 */
+    int quad_order;    /* spatial quadrature order M in {2, 4, 6} (Sec. 3.2) */
+    int precision;     /* molt_precision of fields and sweeps */
+    double tol;        /* fixed-point tolerance on ||v^{k+1} - v^k||_inf (Sec. 4.4) */
+    int max_iter;      /* fixed-point iteration cap per stage (N_maxit, Sec. 6) */
+} molt_params;
+
+/* Per-step report. */
+typedef struct {
+    int status;          /* MOLT_OK or MOLT_ERR_NOT_CONVERGED */
+    int stages;          /* stage solves run by this step */
+    int iters[4];        /* fixed-point iterations of each stage (first 4) */
+    int total_iters;     /* sum over all stages */
+    double residual;     /* largest final ||v^{k+1} - v^k||_inf over the stages (FP64) */
+    double tol_used;     /* tolerance actually applied (FP32 runs: see molt_step) */
+} molt_step_info;
+
+/* Create a grid description (host only, no device work).
+ * dim = 1: an nx-node line, ny must be 1.  dim = 2: an ny-by-nx grid.  Lx, Ly > 0 are the
+ * domain lengths; bc is a molt_bc used in both directions.  Each direction needs at least
+ * 8 nodes.  Errors: MOLT_ERR_ARG. */
+molt_status molt_grid_create(molt_grid** grid, int dim, int nx, int ny, double Lx, double Ly, int bc);
+void molt_grid_destroy(molt_grid* grid);
+
+/* Create a solver on the current CUDA device for `grid` with parameters `p` (copied).
+ * Allocates the device workspace (about 12 fields of the grid's size).
+ * Errors: MOLT_ERR_ARG (eps <= 0, M not in {2,4,6}, tol <= 0, max_iter < 1,
+ * line shorter than M+1 or longer than the sweep kernels support), MOLT_ERR_OOM,
+ * MOLT_ERR_CUDA. */
+molt_status molt_solver_create(molt_solver** solver, const molt_grid* grid, const molt_params* p);
+void molt_solver_destroy(molt_solver* solver);
+
+/* Replace the parameters (the precision cannot change).  Clears the time history. */
+molt_status molt_set_params(molt_solver* solver, const molt_params* p);
+
+/* Change the boundary condition of both directions.  Clears the time history. */
+molt_status molt_set_bc(molt_solver* solver, int bc);
+
+/* Forget the time history (BDF2 previous level, SDC2 level-[0] state). */
+molt_status molt_reset_history(molt_solver* solver);
+
+/* Advance the physical field u (device, in place) by one time step dt > 0 of `scheme`.
+ * Every stage solves v - tau F(v) = r with the lagged fixed-point iteration of
+ * Eq. CH_BE_fixed2_factor (tau >= eps^2) or Eq. CH_BE_fixed_complete (tau < eps^2),
+ * in 2D with the splitting error lagged as in Sec. 5.1.  The sweeps run in the solver's
+ * precision; the residual max-norm is exact (Sterbenz) and compared in FP64.  FP32 fields
+ * cannot resolve a change below a few units in the last place of the stored variable w
+ * (w = u on periodic/Neumann grids, w = u + 1 on Dirichlet grids), so for FP32 solvers the
+ * tolerance applied is max(tol, 4 * 2^-24 * max|w|), and an iteration whose residual is below
+ * 64 * 2^-24 * max|w| and has not improved by 10% for 8 iterations is accepted as converged at
+ * FP32 precision; `info->tol_used` reports the tolerance (or residual) that ended the stage.  BDF2 and SDC2 keep history between calls made
+ * with the same dt.  Returns MOLT_ERR_NOT_CONVERGED (field = last iterate, history
+ * updated) when a stage hits max_iter; `info` may be NULL. */
+molt_status molt_step(molt_solver* solver, void* u_dev, double dt, int scheme, void* stream,
+                      molt_step_info* info);
+
+/* End-to-end variant of molt_step on a HOST buffer: copies u_host to the device, runs
+ * `nsteps` steps, copies the result back into u_host and synchronizes `stream`.
+ * `info` (may be NULL) reports the last step. */
+molt_status molt_run_host(molt_solver* solver, void* u_host, double dt, int scheme, int nsteps,
+                          void* stream, molt_step_info* info);
+
+/* Discrete free energy (Eq. EnergyFunctional) of the physical field u (device):
+ * h_x h_y [ sum over grid edges of eps^2/2 (difference/h)^2 weighted by the trapezoid
+ * weight across the edge + sum over nodes of trapezoid-weighted (u^2-1)^2/4 ], accumulated
+ * in FP64 with a fixed summation order.  Synchronizes `stream`. */
+molt_status molt_energy(molt_solver* solver, const void* u_dev, double* energy, void* stream);
+
+/* Trapezoid-weighted integral of u (device), FP64, fixed summation order.  Synchronizes. */
+molt_status molt_mass(molt_solver* solver, const void* u_dev, double* mass, void* stream);
+
+/* One application of H_c = (I - c d^2)^{-1} (Eq. L_Inverse with alpha = c^{-1/2}) along
+ * `axis` (0 = x: every row; 1 = y: every column) to every line of `in_dev`, written to
+ * `out_dev` (device; may equal in_dev only for axis 0).  Local quadrature of order M
+ * (Sec. 3.2), left/right exponential recurrences (Eq. IL, IR), and the boundary
+ * correction of the solver's bc (Eq. homogeneous and its Neumann/Dirichlet analogues).
+ * The boundary condition is homogeneous in the values passed in.  c > 0. */
+molt_status molt_helmholtz_apply(molt_solver* solver, int axis, double c, const void* in_dev,
+                                 void* out_dev, void* stream);
+
+/* Host-only diagnostic: the local quadrature weights of Sec. 3.2 for one stencil.
+ * Writes M+1 weights of J^L (side = 0) or J^R (side = 1) for node offsets
+ * offsets[0..M] (integers relative to the node) at nu = alpha*h > 0, including the
+ * factor 1/2 of Eq. IL.  No device work. */
+molt_status molt_quadrature_weights(double nu, int M, const int* offsets, int side, double* weights);
+
+/* Last error message of `solver` (or of the last failed create/ABI call when NULL). */
+const char* molt_last_error(const molt_solver* solver);
+
+/* Number of kernels this solver has launched so far (all entry points), for reporting. */
+long long molt_kernel_launches(const molt_solver* solver);
+
+/* Diagnostic timing (not part of the method; off by default).  While enabled, every sweep
+ * kernel launch is bracketed by two CUDA events on its stream. */
+molt_status molt_profile_enable(molt_solver* solver, int enable);
+
+/* Wait for the recorded events and write, per kernel slot (MOLT_PROFILE_SLOTS entries), the
+ * summed device milliseconds and launch counts since the last collect; then forget them.
+ * Slots: row kernel of fused pass k = k, column aggregate kernel of pass k = 8 + k, column
+ * carry kernel = 16, column final kernel of pass k = 17 + k, with k = 0 plain H_c, 1 pass 1,
+ * 2 pass 2, 3 pass 3, 4 pass 4, 5 and 6 the two 1D passes. */
+#define MOLT_PROFILE_SLOTS 32
+molt_status molt_profile_collect(molt_solver* solver, double* ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOLT_H */

@@ -1,0 +1,304 @@
+// Launch layer: builds the fused op of each pass, picks the launch geometry and dispatches
+// on the quadrature order.  Included once per precision (kernels_f32.cu, kernels_f64.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "molt_internal.h"
+#include "sweep_kernels.cuh"
+
+namespace molt {
+
+namespace detail {
+
+constexpr int kRowMaxSmem = 225 * 1024;   // planning bound (opt-in limit minus static shared memory)
+constexpr int kColKY = 16;   // positions per thread in a column tile
+constexpr int kColWY = 8;    // warps per column tile
+constexpr int kColR = kColKY * kColWY;
+
+template <typename T>
+inline void set_strides(OpBase<T>& o, long long ls, long long ps) {
+    o.ls = ls;
+    o.ps = ps;
+}
+
+template <typename T> inline OpCopy<T> build(const OpArgs<T>& a, OpCopy<T>*) {
+    OpCopy<T> o; o.in = a.in0; o.out = a.out0; return o;
+}
+template <typename T> inline OpP1<T> build(const OpArgs<T>& a, OpP1<T>*) {
+    OpP1<T> o; o.w = a.in0; o.t_out = a.out0; o.s_out = a.out1; o.g2 = a.g2; o.g1 = a.g1; return o;
+}
+template <typename T> inline OpP2<T> build(const OpArgs<T>& a, OpP2<T>*) {
+    OpP2<T> o; o.w = a.in0; o.t_in = a.in1; o.s_in = a.in2; o.p_out = a.out0; o.u_out = a.out1;
+    o.g2 = a.g2; o.g1 = a.g1; o.beta = a.beta; return o;
+}
+template <typename T> inline OpP3<T> build(const OpArgs<T>& a, OpP3<T>*) {
+    OpP3<T> o; o.p_in = a.in0; o.u_in = a.in1; o.q1_out = a.out0; o.q2_out = a.out1; return o;
+}
+template <typename T> inline OpP4<T> build(const OpArgs<T>& a, OpP4<T>*) {
+    OpP4<T> o; o.q1_in = a.in0; o.q2_in = a.in1; o.u_in = a.in2; o.y_in = a.in3; o.w = a.out0;
+    o.shift = a.shift; return o;
+}
+template <typename T> inline Op1a<T> build(const OpArgs<T>& a, Op1a<T>*) {
+    Op1a<T> o; o.r = a.in0; o.w = a.in1; o.e_out = a.out0; o.g2 = a.g2; o.g1 = a.g1; o.beta = a.beta; return o;
+}
+template <typename T> inline Op1b<T> build(const OpArgs<T>& a, Op1b<T>*) {
+    Op1b<T> o; o.e_in = a.in0; o.w = a.out0; o.shift = a.shift; return o;
+}
+
+// Opt the kernel into the largest dynamic shared memory the device allows next to its static
+// shared memory; returns that limit (bytes) or -1 on error.
+template <class Kern>
+int smem_optin(Kern kern) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return -1;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return -1;
+    const int limit = optin - static_cast<int>(fa.sharedSizeBytes);
+    if (limit <= 0) return -1;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess) return -1;
+    return limit;
+}
+
+inline int next_pow2_log2(int x) {
+    int l = 0;
+    while ((1 << l) < x) ++l;
+    return l;
+}
+
+inline void prof_begin(Prof* p, int slot, cudaStream_t st) {
+    if (p && p->on) p->begin(slot, st);
+}
+inline void prof_end(Prof* p, cudaStream_t st) {
+    if (p && p->on) p->end(st);
+}
+
+template <typename T, int M, class Op>
+cudaError_t rows(const LineParams<T>& lp, const Op& op, int nlines, unsigned long long* red, cudaStream_t st,
+                 Prof* prof, int kind) {
+    constexpr int NF = Op::NF;
+    const int n = lp.n;
+    const int pitch = n + (n >> 5) + 1;
+    if (n <= 8192) {
+        constexpr int K = 8;
+        const int tl_log2 = next_pow2_log2((n + K - 1) / K);
+        const int TL = 1 << tl_log2;
+        const int threads = TL < 128 ? 128 : TL;
+        int lpb = threads / TL;
+        while (lpb > 1 && static_cast<long long>(lpb) * NF * pitch * sizeof(T) > 48 * 1024) lpb >>= 1;
+        const int block = lpb * TL < 32 ? 32 : lpb * TL;
+        const size_t smem = static_cast<size_t>(lpb) * NF * pitch * sizeof(T);
+        auto kern = rows_kernel<T, M, K, Op>;
+        static int limit = smem_optin(kern);
+        if (limit < 0 || smem > static_cast<size_t>(limit)) return cudaErrorInvalidValue;
+        const int grid = (nlines + lpb - 1) / lpb;
+        prof_begin(prof, kind, st);
+        kern<<<grid, block, smem, st>>>(lp, op, nlines, tl_log2, lpb, pitch, red);
+        prof_end(prof, st);
+    } else if constexpr (NF == 1) {
+        constexpr int K = 16;
+        const int tl_log2 = next_pow2_log2((n + K - 1) / K);
+        const int TL = 1 << tl_log2;
+        if (TL > 1024) return cudaErrorInvalidValue;
+        const size_t smem = static_cast<size_t>(NF) * pitch * sizeof(T);
+        auto kern = rows_kernel<T, M, K, Op>;
+        static int limit = smem_optin(kern);
+        if (limit < 0 || smem > static_cast<size_t>(limit)) return cudaErrorInvalidValue;
+        prof_begin(prof, kind, st);
+        kern<<<nlines, TL, smem, st>>>(lp, op, nlines, tl_log2, 1, pitch, red);
+        prof_end(prof, st);
+    } else {
+        return cudaErrorInvalidValue;   // two-field rows are limited to 8192 nodes
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, int M, class Op>
+cudaError_t cols(const LineParams<T>& lp, const Op& op, int nlines, ColScratch<T>* cs,
+                 unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof, int kind) {
+    constexpr int NF = Op::NF;
+    const int n = lp.n;
+    const int tiles = (n + kColR - 1) / kColR;
+    if (cs == nullptr || cs->capacity_lines < nlines || cs->capacity_fields < NF || cs->tiles < tiles)
+        return cudaErrorInvalidValue;
+    dim3 block(32, kColWY);
+    dim3 grid((nlines + 31) / 32, tiles);
+    prof_begin(prof, 8 + kind, st);
+    cols_agg_kernel<T, M, kColKY, kColWY, Op><<<grid, block, 0, st>>>(lp, op, nlines, cs->aggL, cs->aggR, tiles);
+    prof_end(prof, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int total = nlines * NF;
+    prof_begin(prof, 16, st);
+    cols_carry_kernel<T><<<(total + 127) / 128, 128, 0, st>>>(lp, nlines, NF, tiles, kColR, cs->aggL, cs->aggR,
+                                                             cs->carL, cs->carR);
+    prof_end(prof, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    prof_begin(prof, 17 + kind, st);
+    cols_final_kernel<T, M, kColKY, kColWY, Op><<<grid, block, 0, st>>>(lp, op, nlines, cs->carL, cs->carR, tiles, red);
+    prof_end(prof, st);
+    if (launches) *launches += 2;   // the caller counts one
+    return cudaGetLastError();
+}
+
+template <typename T, class Op>
+cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int nx, int ny, ColScratch<T>* cs,
+                     unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof, int kind) {
+    Op op = build(a, static_cast<Op*>(nullptr));
+    const int nlines = axis == 0 ? ny : nx;
+    set_strides<T>(op, axis == 0 ? nx : 1, axis == 0 ? 1 : nx);
+    if (launches) *launches += 1;
+    if (axis == 0) {
+        if constexpr ((Op::kAxes & 1) != 0) {
+            switch (lp.M) {
+                case 2: return rows<T, 2>(lp, op, nlines, red, st, prof, kind);
+                case 4: return rows<T, 4>(lp, op, nlines, red, st, prof, kind);
+                case 6: return rows<T, 6>(lp, op, nlines, red, st, prof, kind);
+            }
+        }
+    } else {
+        if constexpr ((Op::kAxes & 2) != 0) {
+            switch (lp.M) {
+                case 2: return cols<T, 2>(lp, op, nlines, cs, red, st, launches, prof, kind);
+                case 4: return cols<T, 4>(lp, op, nlines, cs, red, st, launches, prof, kind);
+                case 6: return cols<T, 6>(lp, op, nlines, cs, red, st, launches, prof, kind);
+            }
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ---- pointwise and reductions ----
+template <typename T>
+__global__ void lincomb_kernel(T* out, long long n, const T* x0, double c0, const T* x1, double c1, const T* x2,
+                               double c2, const T* x3, double c3, double c4) {
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+        double acc = c4;
+        if (x0) acc += c0 * static_cast<double>(x0[i]);
+        if (x1) acc += c1 * static_cast<double>(x1[i]);
+        if (x2) acc += c2 * static_cast<double>(x2[i]);
+        if (x3) acc += c3 * static_cast<double>(x3[i]);
+        out[i] = static_cast<T>(acc);
+    }
+}
+
+constexpr int kRedBlocks = 1024;
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double s[kRedThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) s[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kRedThreads / 32; ++i) r += s[i];
+    return r;
+}
+
+// which = 0: energy, 1: mass (trapezoid weights 1/2 on non-periodic wall nodes).
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+energy_mass_kernel(const T* u, int nx, int ny, int bc, double hx, double hy, double eps, int which, double* partials) {
+    const long long total = static_cast<long long>(nx) * ny;
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    const bool periodic = bc == BC_PERIODIC;
+    const double e2 = 0.5 * eps * eps;
+    double acc = 0.0;
+    for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total; idx += stride) {
+        const int i = static_cast<int>(idx % nx);
+        const int j = static_cast<int>(idx / nx);
+        const double wx = (!periodic && (i == 0 || i == nx - 1)) ? 0.5 : 1.0;
+        const double wy = (ny == 1) ? 1.0 : ((!periodic && (j == 0 || j == ny - 1)) ? 0.5 : 1.0);
+        const double x = static_cast<double>(u[idx]);
+        if (which == 1) {
+            acc += wx * wy * x;
+            continue;
+        }
+        const double q = x * x - 1.0;
+        acc += wx * wy * 0.25 * q * q;
+        if (periodic || i < nx - 1) {
+            const int i1 = (i + 1 == nx) ? 0 : i + 1;
+            const double g = (static_cast<double>(u[static_cast<long long>(j) * nx + i1]) - x) / hx;
+            acc += wy * e2 * g * g;
+        }
+        if (ny > 1 && (periodic || j < ny - 1)) {
+            const int j1 = (j + 1 == ny) ? 0 : j + 1;
+            const double g = (static_cast<double>(u[static_cast<long long>(j1) * nx + i]) - x) / hy;
+            acc += wx * e2 * g * g;
+        }
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s * hx * (ny == 1 ? 1.0 : hy);
+}
+
+__global__ void sum_partials_kernel(const double* partials, int n, double* result);
+
+}  // namespace detail
+
+template <typename T>
+cudaError_t sweep(int axis, const LineParams<T>& lp, int kind, const OpArgs<T>& a, int nx, int ny, ColScratch<T>* cs,
+                  unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof) {
+    using namespace detail;
+    switch (kind) {
+        case OP_COPY: return dispatch<T, OpCopy<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
+        case OP_P1: return dispatch<T, OpP1<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
+        case OP_P2: return dispatch<T, OpP2<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
+        case OP_P3: return dispatch<T, OpP3<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
+        case OP_P4: return dispatch<T, OpP4<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
+        case OP_1A: return dispatch<T, Op1a<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
+        case OP_1B: return dispatch<T, Op1b<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+int max_row_length(int nf) {
+    // one line per block: nf * (n + n/32 + 1) * sizeof(T) <= 227 KB; TL <= 1024 with K = 8
+    // (two fields) or K = 16 (one field)
+    long long n = nf == 1 ? 16384 : 8192;
+    while (n > 8 && static_cast<long long>(nf) * (n + (n >> 5) + 1) * static_cast<long long>(sizeof(T)) >
+                        detail::kRowMaxSmem)
+        n -= 64;
+    return static_cast<int>(n);
+}
+
+template <typename T>
+cudaError_t lincomb(T* out, long long n, const T* x0, double c0, const T* x1, double c1, const T* x2, double c2,
+                    const T* x3, double c3, double c4, cudaStream_t st, long long* launches) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    detail::lincomb_kernel<T><<<static_cast<int>(blocks), 256, 0, st>>>(out, n, x0, c0, x1, c1, x2, c2, x3, c3, c4);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t energy_mass(const T* u, int nx, int ny, int bc, double hx, double hy, double eps, int which,
+                        double* partials, double* result, cudaStream_t st, long long* launches) {
+    detail::energy_mass_kernel<T><<<detail::kRedBlocks, detail::kRedThreads, 0, st>>>(u, nx, ny, bc, hx, hy, eps,
+                                                                                      which, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    detail::sum_partials_kernel<<<1, detail::kRedThreads, 0, st>>>(partials, detail::kRedBlocks, result);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace molt
+
+#define MOLT_INSTANTIATE(T)                                                                                   \
+    template cudaError_t molt::sweep<T>(int, const molt::LineParams<T>&, int, const molt::OpArgs<T>&, int, int, \
+                                        molt::ColScratch<T>*, unsigned long long*, cudaStream_t, long long*,    \
+                                        molt::Prof*);                                                           \
+    template int molt::max_row_length<T>(int);                                                                \
+    template cudaError_t molt::lincomb<T>(T*, long long, const T*, double, const T*, double, const T*, double,  \
+                                          const T*, double, double, cudaStream_t, long long*);                  \
+    template cudaError_t molt::energy_mass<T>(const T*, int, int, int, double, double, double, int, double*,    \
+                                              double*, cudaStream_t, long long*);

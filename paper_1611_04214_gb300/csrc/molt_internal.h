@@ -1,0 +1,134 @@
+// Internal declarations shared by the host driver and the sweep kernels.
+//
+// A "line" is one row (x-sweep) or one column (y-sweep) of a row-major [ny][nx] field.
+// Positions along a line are 0..n-1.  Periodic lines have N = n intervals (position n is
+// position 0); Neumann / Dirichlet lines have N = n - 1 intervals and both walls as nodes.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace molt {
+
+enum Bc { BC_PERIODIC = 0, BC_NEUMANN = 1, BC_DIRICHLET = 2 };
+
+constexpr int kMaxM = 6;           // largest quadrature order
+constexpr int kMaxStencil = kMaxM + 1;
+constexpr int kMaxWall = kMaxM / 2;
+
+// Everything one application of H_c along one axis needs (Sec. 3.2), precomputed on the
+// host in FP64 and passed by value to the kernels.
+template <typename T>
+struct LineParams {
+    int n;          // stored nodes per line
+    int N;          // intervals
+    int M;          // quadrature order (the kernel is also instantiated on it)
+    int bc;         // Bc
+    T d;            // e^{-nu}, nu = h / sqrt(c)
+    T nu;           // nu in the kernel precision (powers d^k = exp(-nu k))
+    // Interior stencil, offsets -M/2..M/2: J^L_j = sum wl[o] v_{j+o-M/2}, J^R_j likewise with wr.
+    T wl[kMaxStencil];
+    T wr[kMaxStencil];
+    // Wall stencils of non-periodic lines (Sec. 3.2 reading: shifted inward, same cell).
+    // wlA[j-1]: J^L_j, j = 1..M/2-1, on nodes 0..M.   wrA[j]: J^R_j, j = 0..M/2-1, on nodes 0..M.
+    // wlB[j-jb]: J^L_j, j = jb..N with jb = N-M/2+1, on nodes N-M..N.
+    // wrB[j-jb]: J^R_j, j = jb..N-1, on nodes N-M..N.
+    T wlA[kMaxWall][kMaxStencil];
+    T wrA[kMaxWall][kMaxStencil];
+    T wlB[kMaxWall][kMaxStencil];
+    T wrB[kMaxWall][kMaxStencil];
+    // Boundary correction in FP64.  Non-periodic: B_a = bAA I_0 + bAB I_N, B_b = bBA I_0 + bBB I_N
+    // with I_0 = I^R_0, I_N = I^L_N.  Periodic: carries X = total / (1 - mu) = total * inv1mmu.
+    double bAA, bAB, bBA, bBB;
+    double inv1mmu;
+};
+
+// Host: build the parameters of H_c on a line of n nodes with spacing h.
+// Returns false (and a message) on invalid input.
+bool build_line_params(double c, double h, int n, int M, int bc, LineParams<double>* out,
+                       const char** err);
+template <typename T>
+LineParams<T> cast_line_params(const LineParams<double>& p);
+
+// Host: local quadrature weights of Sec. 3.2 for one stencil (factor 1/2 included).
+bool quadrature_weights(double nu, int M, const int* offsets, int side, double* w);
+
+// Scratch for the column (y) sweeps: per (field, tile, column) aggregates and carries.
+template <typename T>
+struct ColScratch {
+    T* aggL;    // [NF][tiles][nlines]
+    T* aggR;
+    T* carL;
+    T* carR;
+    int tiles;
+    int capacity_lines;   // nlines the buffers were sized for
+    int capacity_fields;
+};
+
+}  // namespace molt
+
+// ------------------------------------------------------------------------------------------
+// Kernel launch layer (implemented per precision in kernels_f32.cu / kernels_f64.cu).
+// ------------------------------------------------------------------------------------------
+#include <cuda_runtime_api.h>
+
+#include <vector>
+
+namespace molt {
+
+// Which fused prologue/epilogue a sweep runs (see sweep_common.cuh for the formulas).
+enum OpKind { OP_COPY = 0, OP_P1, OP_P2, OP_P3, OP_P4, OP_1A, OP_1B };
+
+template <typename T>
+struct OpArgs {
+    const T* in0 = nullptr;
+    const T* in1 = nullptr;
+    const T* in2 = nullptr;
+    const T* in3 = nullptr;
+    T* out0 = nullptr;
+    T* out1 = nullptr;
+    T g2 = 0, g1 = 0, beta = 0, shift = 0;
+};
+
+// Optional per-kernel event timing (diagnostic; off unless a solver enables it).
+// Slots: rows kernel of op k = k; column aggregate kernel = 8 + k; column carry = 16;
+// column final kernel = 17 + k.
+constexpr int kProfSlots = 32;
+struct Prof {
+    bool on = false;
+    struct Mark { int slot; int a, b; };   // indices into the event pool
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    // record an event before (begin) / after (end) one kernel launch on `st`
+    bool begin(int slot, cudaStream_t st);
+    void end(cudaStream_t st);
+    // wait for the recorded events, add elapsed ms and launch counts per slot, forget the marks
+    cudaError_t collect(double* ms, long long* count);
+    void release();
+};
+
+// Fields are [ny][nx]; axis 0 sweeps the ny rows (lines of nx), axis 1 the nx columns.
+template <typename T>
+cudaError_t sweep(int axis, const LineParams<T>& lp, int kind, const OpArgs<T>& a, int nx, int ny,
+                  ColScratch<T>* cs, unsigned long long* red, cudaStream_t st, long long* launches,
+                  Prof* prof = nullptr);
+
+// Largest line length the row kernel supports for a field count (shared-memory bound).
+template <typename T>
+int max_row_length(int nf);
+
+// out = c0 x0 + c1 x1 + c2 x2 + c3 x3 + c4 (null inputs are skipped), n elements.
+template <typename T>
+cudaError_t lincomb(T* out, long long n, const T* x0, double c0, const T* x1, double c1, const T* x2,
+                    double c2, const T* x3, double c3, double c4, cudaStream_t st, long long* launches);
+
+// FP64 energy / mass partial sums: per-block partials into `partials` (>= reduce_blocks()),
+// then a single-block fixed-order sum into `result`.
+template <typename T>
+cudaError_t energy_mass(const T* u, int nx, int ny, int bc, double hx, double hy, double eps,
+                        int which, double* partials, double* result, cudaStream_t st,
+                        long long* launches);
+int reduce_blocks();
+
+}  // namespace molt

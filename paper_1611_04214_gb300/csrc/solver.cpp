@@ -1,0 +1,629 @@
+// C ABI of the library (include/molt.h): handles, stage solves and time schemes.
+//
+// Stored variable.  The kernels work on w = v - s with v = u + 1 (Sec. 3): s = 1 (w = u) on
+// periodic and Neumann grids, where every line inverse maps constants to themselves so the
+// constant part of v never needs to be carried through FP32 arithmetic; s = 0 (w = v) on
+// Dirichlet grids, whose inverses hold v = 0 on the walls.  The fixed-point map keeps the same
+// form in w because D = I - H annihilates constants and all right-hand-side combinations
+// below have coefficients summing to one.
+//
+// Stage solve (v - tau F(v) = r):  parameters from the regime switch of Sec. 3.1.2 (with
+// dt -> tau as in Sec. 4.1-4.2), inner factor = larger c.
+//   1D:  w <- H_o[ H_i[r + beta G(w)] - beta G(w) ]                     (2 sweeps)
+//   2D:  Y = H_ox H_oy H_ix H_iy r once, then per iteration
+//        (y, c_i)  T = H_iy G(w),  S = H_iy w
+//        (x, c_i)  U = S + H_ix(w - S),  P = beta (H_ix(2T - G) - T) + U
+//        (y, c_o)  Q1 = H_oy P,  Q2 = H_oy U
+//        (x, c_o)  w <- Y + w - Q2 + H_ox(Q1 - U)
+//   which is, term by term, Y + M_o^{-1}[beta (M_i^{-1}G - G + D_ix D_iy G)]
+//   + (D_ox D_oy + D_ix D_iy - D_ox D_oy D_ix D_iy) w  (Sec. 5.1 with c_o != c_i).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/molt.h"
+#include "molt_internal.h"
+
+struct molt_grid {
+    int dim, nx, ny;
+    double Lx, Ly;
+    int bc;
+};
+
+namespace {
+
+thread_local std::string g_last_error = "";
+
+constexpr double kEta2 = 0.29289321881345247560;   // 1 - sqrt(2)/2 (Sec. 4.2)
+
+double alexander_eta() {
+    // root of x^3 - 3x^2 + 3x/2 - 1/6 in (0.4, 0.5): Alexander's L-stable SDIRK3 (Sec. 4.4 quotes 0.4359)
+    double lo = 0.4, hi = 0.5;
+    auto p = [](double x) { return ((x - 3.0) * x + 1.5) * x - 1.0 / 6.0; };
+    for (int i = 0; i < 200; ++i) {
+        const double mid = 0.5 * (lo + hi);
+        if (p(lo) * p(mid) <= 0) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+struct StageParams {
+    bool factor;
+    double c_in, c_out, beta, lam;
+};
+
+StageParams stage_params(double tau, double eps) {
+    StageParams sp;
+    double c1, c2;
+    if (tau >= eps * eps) {
+        const double disc = std::sqrt(tau * tau - eps * eps * tau);
+        c1 = tau + disc;
+        c2 = tau - disc;
+        sp.factor = true;
+    } else {
+        c1 = c2 = std::sqrt(eps * eps * tau);
+        sp.factor = false;
+    }
+    sp.c_in = std::max(c1, c2);
+    sp.c_out = std::min(c1, c2);
+    sp.beta = tau / sp.c_in;
+    sp.lam = 2.0 - (c1 + c2) / tau;
+    return sp;
+}
+
+double grid_h(int n, double L, int bc) { return bc == molt::BC_PERIODIC ? L / n : L / (n - 1); }
+
+}  // namespace
+
+namespace molt {
+
+static bool next_event(Prof* p, int* idx) {
+    if (p->used == p->pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return false;
+        p->pool.push_back(e);
+    }
+    *idx = static_cast<int>(p->used++);
+    return true;
+}
+
+bool Prof::begin(int slot, cudaStream_t st) {
+    int a, b;
+    if (!next_event(this, &a) || !next_event(this, &b)) return false;
+    cudaEventRecord(pool[a], st);
+    marks.push_back({slot, a, b});
+    return true;
+}
+
+void Prof::end(cudaStream_t st) {
+    if (!marks.empty()) cudaEventRecord(pool[marks.back().b], st);
+}
+
+cudaError_t Prof::collect(double* ms, long long* count) {
+    for (int i = 0; i < kProfSlots; ++i) {
+        ms[i] = 0.0;
+        count[i] = 0;
+    }
+    for (const Mark& m : marks) {
+        cudaError_t e = cudaEventSynchronize(pool[m.b]);
+        if (e != cudaSuccess) return e;
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, pool[m.a], pool[m.b]);
+        if (e != cudaSuccess) return e;
+        if (m.slot >= 0 && m.slot < kProfSlots) {
+            ms[m.slot] += t;
+            count[m.slot] += 1;
+        }
+    }
+    marks.clear();
+    used = 0;
+    return cudaSuccess;
+}
+
+void Prof::release() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+    marks.clear();
+    used = 0;
+}
+
+}  // namespace molt
+
+// Precision-independent part of the solver handle.
+struct molt_solver {
+    molt_grid g;
+    molt_params p;
+    int bc;
+    int device = 0;
+    std::string err;
+    long long launches = 0;
+    molt::Prof prof;
+    // history
+    bool have_prev = false;
+    double dt_prev = 0.0;
+    bool have_sdc = false;
+    virtual ~molt_solver() { prof.release(); }
+    virtual molt_status step(void* u, double dt, int scheme, cudaStream_t st, molt_step_info* info) = 0;
+    virtual molt_status run_host(void* u_host, double dt, int scheme, int nsteps, cudaStream_t st,
+                                 molt_step_info* info) = 0;
+    virtual molt_status reduce(const void* u, int which, double* out, cudaStream_t st) = 0;
+    virtual molt_status apply(int axis, double c, const void* in, void* out, cudaStream_t st) = 0;
+    virtual molt_status init() = 0;
+};
+
+namespace {
+
+template <typename T>
+struct Solver final : molt_solver {
+    // device fields (nx*ny elements each)
+    T *w = nullptr, *wn = nullptr, *wprev = nullptr, *r = nullptr, *Y = nullptr;
+    T *f1 = nullptr, *f2 = nullptr, *f3 = nullptr, *f4 = nullptr, *f5 = nullptr, *f6 = nullptr;
+    T *k0 = nullptr, *k1 = nullptr, *ubuf = nullptr;
+    molt::ColScratch<T> cs{};
+    unsigned long long* red = nullptr;       // device [2]
+    unsigned long long* red_host = nullptr;  // pinned [2]
+    double* partials = nullptr;              // device [reduce_blocks]
+    double* result = nullptr;                // device [1]
+    double* result_host = nullptr;           // pinned [1]
+    std::vector<void*> allocs;
+
+    size_t count() const { return static_cast<size_t>(g.nx) * g.ny; }
+    bool fp32() const { return sizeof(T) == 4; }
+    T shift() const { return bc == molt::BC_DIRICHLET ? T(0) : T(1); }
+
+    ~Solver() override {
+        for (void* a : allocs) cudaFree(a);
+        if (red_host) cudaFreeHost(red_host);
+        if (result_host) cudaFreeHost(result_host);
+    }
+
+    molt_status fail(molt_status s, const std::string& m) {
+        err = m;
+        return s;
+    }
+    molt_status cuda_fail(cudaError_t e, const char* where) {
+        err = std::string(where) + ": " + cudaGetErrorString(e);
+        return MOLT_ERR_CUDA;
+    }
+
+    template <typename U>
+    bool alloc(U** p, size_t n) {
+        void* q = nullptr;
+        if (cudaMalloc(&q, n * sizeof(U)) != cudaSuccess) return false;
+        allocs.push_back(q);
+        *p = static_cast<U*>(q);
+        return true;
+    }
+
+    molt_status init() override {
+        const size_t n = count();
+        T** fields[] = {&w, &wn, &wprev, &r, &Y, &f1, &f2, &f3, &f4, &f5, &f6, &k0, &k1};
+        for (T** f : fields)
+            if (!alloc(f, n)) return fail(MOLT_ERR_OOM, "device workspace allocation failed");
+        const int nlines = g.nx;
+        const int tiles = (g.ny + 127) / 128;
+        cs.tiles = tiles;
+        cs.capacity_lines = nlines;
+        cs.capacity_fields = 2;
+        const size_t sc = static_cast<size_t>(2) * tiles * nlines;
+        if (!alloc(&cs.aggL, sc) || !alloc(&cs.aggR, sc) || !alloc(&cs.carL, sc) || !alloc(&cs.carR, sc) ||
+            !alloc(&red, 2) || !alloc(&partials, static_cast<size_t>(molt::reduce_blocks())) || !alloc(&result, 1))
+            return fail(MOLT_ERR_OOM, "device scratch allocation failed");
+        if (cudaMallocHost(&red_host, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMallocHost(&result_host, sizeof(double)) != cudaSuccess)
+            return fail(MOLT_ERR_OOM, "pinned host allocation failed");
+        return MOLT_OK;
+    }
+
+    bool line_params(double c, int axis, molt::LineParams<T>* out) {
+        molt::LineParams<double> lp;
+        const char* e = nullptr;
+        const int n = axis == 0 ? g.nx : g.ny;
+        const double L = axis == 0 ? g.Lx : g.Ly;
+        if (!molt::build_line_params(c, grid_h(n, L, bc), n, p.quad_order, bc, &lp, &e)) {
+            err = e ? e : "line parameters";
+            return false;
+        }
+        *out = molt::cast_line_params<T>(lp);
+        return true;
+    }
+
+    cudaError_t sweep(int axis, const molt::LineParams<T>& lp, int kind, const molt::OpArgs<T>& a,
+                      cudaStream_t st) {
+        return molt::sweep<T>(axis, lp, kind, a, g.nx, g.ny, &cs, red, st, &launches, &prof);
+    }
+
+    cudaError_t copy_sweep(int axis, const molt::LineParams<T>& lp, const T* in, T* out, cudaStream_t st) {
+        molt::OpArgs<T> a;
+        a.in0 = in;
+        a.out0 = out;
+        return sweep(axis, lp, molt::OP_COPY, a, st);
+    }
+
+    cudaError_t lin(T* out, const T* x0, double c0, const T* x1 = nullptr, double c1 = 0, const T* x2 = nullptr,
+                    double c2 = 0, const T* x3 = nullptr, double c3 = 0, double c4 = 0, cudaStream_t st = nullptr) {
+        return molt::lincomb<T>(out, static_cast<long long>(count()), x0, c0, x1, c1, x2, c2, x3, c3, c4, st,
+                                &launches);
+    }
+
+    // Solve v - tau F(v) = r for w (in: first guess, out: last iterate), r in stored form.
+    molt_status stage(double tau, const T* rhs, cudaStream_t st, int* iters, double* res_out, double* tol_out) {
+        const StageParams sp = stage_params(tau, p.eps);
+        molt::LineParams<T> lix, lox, liy, loy;
+        if (!line_params(sp.c_in, 0, &lix) || !line_params(sp.c_out, 0, &lox)) return MOLT_ERR_ARG;
+        const bool two_d = g.dim == 2;
+        if (two_d && (!line_params(sp.c_in, 1, &liy) || !line_params(sp.c_out, 1, &loy))) return MOLT_ERR_ARG;
+        const T s = shift();
+        const T g2 = s == T(1) ? T(0) : T(-3);
+        const T g1 = s == T(1) ? static_cast<T>(sp.lam - 3.0) : static_cast<T>(sp.lam);
+        const T beta = static_cast<T>(sp.beta);
+        cudaError_t e = cudaSuccess;
+        if (two_d) {
+            // Y = M_o^{-1} M_i^{-1} r
+            if ((e = copy_sweep(1, liy, rhs, f1, st)) != cudaSuccess) return cuda_fail(e, "sweep");
+            if ((e = copy_sweep(0, lix, f1, f2, st)) != cudaSuccess) return cuda_fail(e, "sweep");
+            if ((e = copy_sweep(1, loy, f2, f1, st)) != cudaSuccess) return cuda_fail(e, "sweep");
+            if ((e = copy_sweep(0, lox, f1, Y, st)) != cudaSuccess) return cuda_fail(e, "sweep");
+        }
+        double res = INFINITY, tol_used = p.tol, best = INFINITY;
+        int k = 0, stall = 0;
+        bool converged = false;
+        for (k = 1; k <= p.max_iter; ++k) {
+            if ((e = cudaMemsetAsync(red, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
+                return cuda_fail(e, "memset");
+            if (two_d) {
+                molt::OpArgs<T> a1;
+                a1.in0 = w; a1.out0 = f1; a1.out1 = f2; a1.g2 = g2; a1.g1 = g1;
+                if ((e = sweep(1, liy, molt::OP_P1, a1, st)) != cudaSuccess) return cuda_fail(e, "pass 1");
+                molt::OpArgs<T> a2;
+                a2.in0 = w; a2.in1 = f1; a2.in2 = f2; a2.out0 = f3; a2.out1 = f4;
+                a2.g2 = g2; a2.g1 = g1; a2.beta = beta;
+                if ((e = sweep(0, lix, molt::OP_P2, a2, st)) != cudaSuccess) return cuda_fail(e, "pass 2");
+                molt::OpArgs<T> a3;
+                a3.in0 = f3; a3.in1 = f4; a3.out0 = f5; a3.out1 = f6;
+                if ((e = sweep(1, loy, molt::OP_P3, a3, st)) != cudaSuccess) return cuda_fail(e, "pass 3");
+                molt::OpArgs<T> a4;
+                a4.in0 = f5; a4.in1 = f6; a4.in2 = f4; a4.in3 = Y; a4.out0 = w; a4.shift = s;
+                if ((e = sweep(0, lox, molt::OP_P4, a4, st)) != cudaSuccess) return cuda_fail(e, "pass 4");
+            } else {
+                molt::OpArgs<T> aa;
+                aa.in0 = rhs; aa.in1 = w; aa.out0 = f1; aa.g2 = g2; aa.g1 = g1; aa.beta = beta;
+                if ((e = sweep(0, lix, molt::OP_1A, aa, st)) != cudaSuccess) return cuda_fail(e, "pass a");
+                molt::OpArgs<T> ab;
+                ab.in0 = f1; ab.out0 = w; ab.shift = s;
+                if ((e = sweep(0, lox, molt::OP_1B, ab, st)) != cudaSuccess) return cuda_fail(e, "pass b");
+            }
+            if ((e = cudaMemcpyAsync(red_host, red, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess)
+                return cuda_fail(e, "residual copy");
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream sync");
+            double dmax, wmax;
+            std::memcpy(&dmax, &red_host[0], sizeof(double));
+            std::memcpy(&wmax, &red_host[1], sizeof(double));
+            res = dmax;
+            if (!std::isfinite(res)) break;
+            // FP32 fields cannot resolve changes below a few units in the last place of the
+            // stored variable: the tolerance is floored at 4 ulp of max|w|, and an iteration that
+            // has reached 64 ulp and stopped improving for 8 steps is at FP32 precision.
+            const double ulp = std::ldexp(1.0, -24) * wmax;
+            tol_used = fp32() ? std::max(p.tol, 4.0 * ulp) : p.tol;
+            if (res < tol_used) {
+                converged = true;
+                break;
+            }
+            if (res < 0.9 * best) {
+                best = res;
+                stall = 0;
+            } else if (fp32() && res < 64.0 * ulp && ++stall >= 8) {
+                converged = true;
+                tol_used = res;
+                break;
+            }
+        }
+        *iters = converged ? k : std::min(k, p.max_iter);
+        *res_out = res;
+        *tol_out = tol_used;
+        return converged ? MOLT_OK : MOLT_ERR_NOT_CONVERGED;
+    }
+
+    void record(molt_step_info* info, int stage_idx, int it, double res, double tol_used) {
+        if (!info) return;
+        if (stage_idx < 4) info->iters[stage_idx] = it;
+        info->stages = stage_idx + 1;
+        info->total_iters += it;
+        info->residual = std::max(info->residual, res);
+        info->tol_used = tol_used;
+    }
+
+    molt_status sdirk(double dt, const double A[3][3], int s_count, cudaStream_t st, molt_step_info* info,
+                      int stage0) {
+        // stage-value form: V_i - eta dt F(V_i) = w^n + dt sum_{l<i} a_il K_l, K_l = (V_l - R_l)/(eta dt)
+        const double eta = A[0][0];
+        T* K[2] = {k0, k1};
+        molt_status worst = MOLT_OK;
+        cudaError_t e;
+        for (int i = 0; i < s_count; ++i) {
+            if (i == 0) e = lin(r, wn, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st);
+            else if (i == 1) e = lin(r, wn, 1.0, K[0], dt * A[1][0], nullptr, 0, nullptr, 0, 0, st);
+            else e = lin(r, wn, 1.0, K[0], dt * A[2][0], K[1], dt * A[2][1], nullptr, 0, 0, st);
+            if (e != cudaSuccess) return cuda_fail(e, "stage rhs");
+            int it;
+            double res, tu;
+            molt_status ms = stage(eta * dt, r, st, &it, &res, &tu);
+            if (ms != MOLT_OK && ms != MOLT_ERR_NOT_CONVERGED) return ms;
+            if (ms != MOLT_OK) worst = ms;
+            record(info, stage0 + i, it, res, tu);
+            if (i + 1 < s_count) {
+                if ((e = lin(K[i], w, 1.0 / (eta * dt), r, -1.0 / (eta * dt), nullptr, 0, nullptr, 0, 0, st)) !=
+                    cudaSuccess)
+                    return cuda_fail(e, "stage slope");
+            }
+        }
+        return worst;
+    }
+
+    molt_status step(void* u_void, double dt, int scheme, cudaStream_t st, molt_step_info* info) override {
+        T* u = static_cast<T*>(u_void);
+        if (info) std::memset(info, 0, sizeof(*info));
+        const double in_shift = 1.0 - static_cast<double>(shift());   // w = u + (1 - s)
+        cudaError_t e;
+        if ((e = lin(w, u, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, in_shift, st)) != cudaSuccess)
+            return cuda_fail(e, "load field");
+        if ((e = lin(wn, w, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
+            return cuda_fail(e, "copy field");
+        molt_status ms = MOLT_OK;
+        int it;
+        double res, tu;
+        switch (scheme) {
+            case MOLT_BE:
+                ms = stage(dt, wn, st, &it, &res, &tu);
+                record(info, 0, it, res, tu);
+                break;
+            case MOLT_BDF2:
+                if (!have_prev || dt_prev != dt) {
+                    ms = stage(dt, wn, st, &it, &res, &tu);          // BE start
+                } else {
+                    if ((e = lin(r, wn, 4.0 / 3.0, wprev, -1.0 / 3.0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
+                        return cuda_fail(e, "bdf2 rhs");
+                    ms = stage(2.0 * dt / 3.0, r, st, &it, &res, &tu);
+                }
+                record(info, 0, it, res, tu);
+                break;
+            case MOLT_SDIRK2: {
+                const double A[3][3] = {{kEta2, 0, 0}, {1.0 - kEta2, kEta2, 0}, {0, 0, 0}};
+                ms = sdirk(dt, A, 2, st, info, 0);
+                break;
+            }
+            case MOLT_SDIRK3: {
+                const double eta = alexander_eta();
+                const double A[3][3] = {{eta, 0, 0},
+                                        {(1.0 - eta) / 2.0, eta, 0},
+                                        {-(6 * eta * eta - 16 * eta + 1) / 4.0, (6 * eta * eta - 20 * eta + 5) / 4.0, eta}};
+                ms = sdirk(dt, A, 3, st, info, 0);
+                break;
+            }
+            default:
+                return fail(MOLT_ERR_UNSUPPORTED, "scheme not supported by this build");
+        }
+        if (ms != MOLT_OK && ms != MOLT_ERR_NOT_CONVERGED) return ms;
+        // history for BDF2: previous level
+        std::swap(wprev, wn);
+        have_prev = true;
+        dt_prev = dt;
+        if ((e = lin(u, w, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, -in_shift, st)) != cudaSuccess)
+            return cuda_fail(e, "store field");
+        if (info) info->status = ms;
+        if (ms == MOLT_ERR_NOT_CONVERGED) err = "a stage reached max_iter before the fixed-point tolerance";
+        return ms;
+    }
+
+    molt_status run_host(void* u_host, double dt, int scheme, int nsteps, cudaStream_t st,
+                         molt_step_info* info) override {
+        if (!ubuf && !alloc(&ubuf, count())) return fail(MOLT_ERR_OOM, "device buffer allocation failed");
+        const size_t bytes = count() * sizeof(T);
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(ubuf, u_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "host to device copy");
+        molt_status ms = MOLT_OK;
+        for (int i = 0; i < nsteps; ++i) {
+            ms = step(ubuf, dt, scheme, st, info);
+            if (ms != MOLT_OK && ms != MOLT_ERR_NOT_CONVERGED) return ms;
+        }
+        if ((e = cudaMemcpyAsync(u_host, ubuf, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(e, "device to host copy");
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream sync");
+        return ms;
+    }
+
+    molt_status reduce(const void* u, int which, double* out, cudaStream_t st) override {
+        const double hx = grid_h(g.nx, g.Lx, bc);
+        const double hy = g.dim == 2 ? grid_h(g.ny, g.Ly, bc) : 1.0;
+        cudaError_t e = molt::energy_mass<T>(static_cast<const T*>(u), g.nx, g.ny, bc, hx, hy, p.eps, which,
+                                             partials, result, st, &launches);
+        if (e != cudaSuccess) return cuda_fail(e, "reduction");
+        if ((e = cudaMemcpyAsync(result_host, result, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(e, "reduction copy");
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream sync");
+        *out = *result_host;
+        return MOLT_OK;
+    }
+
+    molt_status apply(int axis, double c, const void* in, void* out, cudaStream_t st) override {
+        if (axis != 0 && axis != 1) return fail(MOLT_ERR_ARG, "axis must be 0 (x) or 1 (y)");
+        if (axis == 1 && g.dim != 2) return fail(MOLT_ERR_ARG, "axis 1 needs a 2D grid");
+        if (axis == 1 && in == out) return fail(MOLT_ERR_ARG, "column sweeps cannot run in place");
+        if (!(c > 0.0) || !std::isfinite(c)) return fail(MOLT_ERR_ARG, "c must be positive and finite");
+        molt::LineParams<T> lp;
+        if (!line_params(c, axis, &lp)) return MOLT_ERR_ARG;
+        cudaError_t e = copy_sweep(axis, lp, static_cast<const T*>(in), static_cast<T*>(out), st);
+        if (e != cudaSuccess) return cuda_fail(e, "sweep");
+        return MOLT_OK;
+    }
+};
+
+molt_status validate_params(const molt_grid* g, const molt_params* p, std::string* m) {
+    if (!p) { *m = "null parameters"; return MOLT_ERR_ARG; }
+    if (!(p->eps > 0.0) || !std::isfinite(p->eps)) { *m = "eps must be positive"; return MOLT_ERR_ARG; }
+    if (p->quad_order != 2 && p->quad_order != 4 && p->quad_order != 6) { *m = "quad_order must be 2, 4 or 6"; return MOLT_ERR_ARG; }
+    if (p->precision != MOLT_FP32 && p->precision != MOLT_FP64) { *m = "unknown precision"; return MOLT_ERR_ARG; }
+    if (!(p->tol > 0.0)) { *m = "tol must be positive"; return MOLT_ERR_ARG; }
+    if (p->max_iter < 1) { *m = "max_iter must be >= 1"; return MOLT_ERR_ARG; }
+    const int minn = p->quad_order + 2;
+    if (g->nx < minn || (g->dim == 2 && g->ny < minn)) { *m = "grid lines too short for the quadrature order"; return MOLT_ERR_ARG; }
+    const int maxn = p->precision == MOLT_FP32 ? molt::max_row_length<float>(2) : molt::max_row_length<double>(2);
+    if (g->nx > maxn) { *m = "x lines longer than the row kernels support"; return MOLT_ERR_ARG; }
+    return MOLT_OK;
+}
+
+molt_status set_global_error(molt_status s, const char* m) {
+    g_last_error = m;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+molt_status molt_grid_create(molt_grid** grid, int dim, int nx, int ny, double Lx, double Ly, int bc) {
+    if (!grid) return set_global_error(MOLT_ERR_ARG, "null grid pointer");
+    *grid = nullptr;
+    if (dim != 1 && dim != 2) return set_global_error(MOLT_ERR_ARG, "dim must be 1 or 2");
+    if (dim == 1 && ny != 1) return set_global_error(MOLT_ERR_ARG, "1D grids need ny = 1");
+    if (nx < 8 || (dim == 2 && ny < 8)) return set_global_error(MOLT_ERR_ARG, "each direction needs at least 8 nodes");
+    if (!(Lx > 0.0) || (dim == 2 && !(Ly > 0.0))) return set_global_error(MOLT_ERR_ARG, "domain lengths must be positive");
+    if (bc < MOLT_BC_PERIODIC || bc > MOLT_BC_DIRICHLET) return set_global_error(MOLT_ERR_ARG, "unknown boundary condition");
+    if (static_cast<long long>(nx) * ny > (1LL << 31) - 1) return set_global_error(MOLT_ERR_ARG, "grid too large");
+    molt_grid* g = new (std::nothrow) molt_grid{dim, nx, ny, Lx, dim == 2 ? Ly : 1.0, bc};
+    if (!g) return set_global_error(MOLT_ERR_OOM, "host allocation failed");
+    *grid = g;
+    return MOLT_OK;
+}
+
+void molt_grid_destroy(molt_grid* grid) { delete grid; }
+
+molt_status molt_solver_create(molt_solver** solver, const molt_grid* grid, const molt_params* p) {
+    if (!solver || !grid) return set_global_error(MOLT_ERR_ARG, "null argument");
+    *solver = nullptr;
+    std::string m;
+    molt_status s = validate_params(grid, p, &m);
+    if (s != MOLT_OK) return set_global_error(s, m.c_str());
+    molt_solver* h = nullptr;
+    if (p->precision == MOLT_FP32) h = new (std::nothrow) Solver<float>();
+    else h = new (std::nothrow) Solver<double>();
+    if (!h) return set_global_error(MOLT_ERR_OOM, "host allocation failed");
+    h->g = *grid;
+    h->p = *p;
+    h->bc = grid->bc;
+    cudaGetDevice(&h->device);
+    s = h->init();
+    if (s != MOLT_OK) {
+        g_last_error = h->err;
+        delete h;
+        return s;
+    }
+    *solver = h;
+    return MOLT_OK;
+}
+
+void molt_solver_destroy(molt_solver* solver) { delete solver; }
+
+molt_status molt_set_params(molt_solver* s, const molt_params* p) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    std::string m;
+    molt_status st = validate_params(&s->g, p, &m);
+    if (st != MOLT_OK) { s->err = m; return st; }
+    if (p->precision != s->p.precision) { s->err = "precision cannot change"; return MOLT_ERR_ARG; }
+    s->p = *p;
+    s->have_prev = false;
+    s->have_sdc = false;
+    return MOLT_OK;
+}
+
+molt_status molt_set_bc(molt_solver* s, int bc) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    if (bc < MOLT_BC_PERIODIC || bc > MOLT_BC_DIRICHLET) { s->err = "unknown boundary condition"; return MOLT_ERR_ARG; }
+    s->bc = bc;
+    s->g.bc = bc;
+    s->have_prev = false;
+    s->have_sdc = false;
+    return MOLT_OK;
+}
+
+molt_status molt_reset_history(molt_solver* s) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    s->have_prev = false;
+    s->have_sdc = false;
+    return MOLT_OK;
+}
+
+molt_status molt_step(molt_solver* s, void* u_dev, double dt, int scheme, void* stream, molt_step_info* info) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    if (!u_dev) { s->err = "null field"; return MOLT_ERR_ARG; }
+    if (!(dt > 0.0) || !std::isfinite(dt)) { s->err = "dt must be positive"; return MOLT_ERR_ARG; }
+    if (scheme < MOLT_BE || scheme > MOLT_SDC2) { s->err = "unknown scheme"; return MOLT_ERR_ARG; }
+    return s->step(u_dev, dt, scheme, static_cast<cudaStream_t>(stream), info);
+}
+
+molt_status molt_run_host(molt_solver* s, void* u_host, double dt, int scheme, int nsteps, void* stream,
+                          molt_step_info* info) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    if (!u_host || nsteps < 0) { s->err = "bad host buffer or step count"; return MOLT_ERR_ARG; }
+    if (!(dt > 0.0) || !std::isfinite(dt)) { s->err = "dt must be positive"; return MOLT_ERR_ARG; }
+    if (scheme < MOLT_BE || scheme > MOLT_SDC2) { s->err = "unknown scheme"; return MOLT_ERR_ARG; }
+    return s->run_host(u_host, dt, scheme, nsteps, static_cast<cudaStream_t>(stream), info);
+}
+
+molt_status molt_energy(molt_solver* s, const void* u_dev, double* energy, void* stream) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    if (!u_dev || !energy) { s->err = "null argument"; return MOLT_ERR_ARG; }
+    return s->reduce(u_dev, 0, energy, static_cast<cudaStream_t>(stream));
+}
+
+molt_status molt_mass(molt_solver* s, const void* u_dev, double* mass, void* stream) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    if (!u_dev || !mass) { s->err = "null argument"; return MOLT_ERR_ARG; }
+    return s->reduce(u_dev, 1, mass, static_cast<cudaStream_t>(stream));
+}
+
+molt_status molt_helmholtz_apply(molt_solver* s, int axis, double c, const void* in_dev, void* out_dev, void* stream) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    if (!in_dev || !out_dev) { s->err = "null field"; return MOLT_ERR_ARG; }
+    return s->apply(axis, c, in_dev, out_dev, static_cast<cudaStream_t>(stream));
+}
+
+molt_status molt_quadrature_weights(double nu, int M, const int* offsets, int side, double* weights) {
+    if (M != 2 && M != 4 && M != 6) return set_global_error(MOLT_ERR_ARG, "M must be 2, 4 or 6");
+    if (side != 0 && side != 1) return set_global_error(MOLT_ERR_ARG, "side must be 0 (L) or 1 (R)");
+    if (!molt::quadrature_weights(nu, M, offsets, side, weights)) return set_global_error(MOLT_ERR_ARG, "bad nu or pointer");
+    return MOLT_OK;
+}
+
+const char* molt_last_error(const molt_solver* s) {
+    if (!s) return g_last_error.c_str();
+    return s->err.c_str();
+}
+
+long long molt_kernel_launches(const molt_solver* s) { return s ? s->launches : 0; }
+
+molt_status molt_profile_enable(molt_solver* s, int enable) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    s->prof.on = enable != 0;
+    return MOLT_OK;
+}
+
+molt_status molt_profile_collect(molt_solver* s, double* ms, long long* launches) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    if (!ms || !launches) { s->err = "null output"; return MOLT_ERR_ARG; }
+    cudaError_t e = s->prof.collect(ms, launches);
+    if (e != cudaSuccess) { s->err = std::string("profile: ") + cudaGetErrorString(e); return MOLT_ERR_CUDA; }
+    return MOLT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,339 @@
+// Device building blocks of the Helmholtz line sweeps (Sec. 3.2) and the fused per-point
+// work of the fixed-point iteration (Sec. 3.1.2, Sec. 5.1).
+//
+// A thread owns K consecutive positions of one line.  For them it forms the local
+// quadrature integrals J^L_j, J^R_j from an (M+1)-point stencil, runs the two exponential
+// recurrences of Eq. IL / IR with zero start, and reduces its chunk to a segment
+// (D, A): decay over the chunk and recurrence value at the chunk's far end.  Segments
+// compose associatively, (D1, A1) then (D2, A2) = (D1 D2, A1 D2 + A2), so a scan over the
+// threads of a line gives each chunk the recurrence value entering it; the line totals give
+// I_0 and I_N for the boundary 2x2 solve, done in FP64.  A second pass over the chunk, started
+// from those carries, produces out_j = I^L_j + B_a d^j + I^R_j + B_b d^{N-j}.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "molt_internal.h"
+
+namespace molt {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float dev_exp(float x) { return expf(x); }
+__device__ __forceinline__ double dev_exp(double x) { return exp(x); }
+
+// Wrap (periodic) or clamp (walls) a position that may lie up to 2n outside the line.
+__device__ __forceinline__ int fold_pos(int p, int n, bool periodic) {
+    if (periodic) {
+        if (p < 0) p += n;
+        if (p < 0) p += n;
+        if (p >= n) p -= n;
+        if (p >= n) p -= n;
+        return p;
+    }
+    return p < 0 ? 0 : (p >= n ? n - 1 : p);
+}
+
+// J^L, J^R for positions start..start+K-1 (entries past cnt are left as computed and never
+// used).  `win[i]` holds the value at position start - M/2 + i.  `at(p)` returns the value at
+// absolute position p; it is only called by the few threads whose chunk touches a wall of a
+// non-periodic line (shifted wall stencils, Sec. 3.2 reading).
+template <typename T, int M, int K, class At>
+__device__ __forceinline__ void local_integrals(const LineParams<T>& lp, int start, int cnt,
+                                                const T (&win)[K + M], At at, T (&JL)[K],
+                                                T (&JR)[K]) {
+    constexpr int H = M / 2;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        T jl = T(0), jr = T(0);
+#pragma unroll
+        for (int o = 0; o <= M; ++o) {
+            jl = fma(lp.wl[o], win[k + o], jl);
+            jr = fma(lp.wr[o], win[k + o], jr);
+        }
+        JL[k] = jl;
+        JR[k] = jr;
+    }
+    if (lp.bc != BC_PERIODIC) {
+        const int N = lp.N;
+        const int jb = N - H + 1;
+        if (start < H || start + cnt - 1 >= jb) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int j = start + k;
+                if (k >= cnt) continue;
+                if (j < H) {
+                    T jl = T(0), jr = T(0);
+                    for (int o = 0; o <= M; ++o) {
+                        const T v = at(o);
+                        if (j >= 1) jl = fma(lp.wlA[j - 1][o], v, jl);
+                        jr = fma(lp.wrA[j][o], v, jr);
+                    }
+                    JL[k] = jl;      // J^L_0 = 0: I^L_0 = 0 (Eq. IL)
+                    JR[k] = jr;
+                } else if (j >= jb) {
+                    T jl = T(0), jr = T(0);
+                    for (int o = 0; o <= M; ++o) {
+                        const T v = at(N - M + o);
+                        jl = fma(lp.wlB[j - jb][o], v, jl);
+                        if (j < N) jr = fma(lp.wrB[j - jb][o], v, jr);
+                    }
+                    JL[k] = jl;
+                    JR[k] = jr;      // J^R_N = 0: I^R_N = 0 (Eq. IR)
+                }
+            }
+        }
+    }
+}
+
+// Zero-start recurrences over the chunk: aL = I^L at the chunk's last position,
+// aR = I^R at its first position (Eq. IL / IR restricted to the chunk).
+template <typename T, int K>
+__device__ __forceinline__ void chunk_aggregates(T d, int cnt, const T (&JL)[K], const T (&JR)[K],
+                                                 T& aL, T& aR) {
+    T a = T(0), b = T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        if (k < cnt) a = fma(d, a, JL[k]);
+#pragma unroll
+    for (int k = K - 1; k >= 0; --k)
+        if (k < cnt) b = fma(d, b, JR[k]);
+    aL = a;
+    aR = b;
+}
+
+// Second pass: out_k = P^R_k + P^L_k from the carries entering the chunk from the right (cR)
+// and from the left (cL).  The result overwrites JR.
+template <typename T, int K>
+__device__ __forceinline__ void chunk_finish(T d, int cnt, T cL, T cR, const T (&JL)[K], T (&JR)[K]) {
+    T p = cR;
+#pragma unroll
+    for (int k = K - 1; k >= 0; --k)
+        if (k < cnt) {
+            p = fma(d, p, JR[k]);
+            JR[k] = p;
+        }
+    T q = cL;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        if (k < cnt) {
+            q = fma(d, q, JL[k]);
+            JR[k] += q;
+        }
+}
+
+// ---------------------------------------------------------------------------------------
+// Per-point work of each pass, fused into the sweeps as load (prologue) / store (epilogue).
+// kAxes: 1 = runs on rows (x), 2 = on columns (y), 3 = both.
+// A field element of a line is at index line * ls + pos * ps.
+// G(x) = x (x (x + g2) + g1) is the lagged nonlinear term in the stored variable x:
+//   shifted storage x = u (= v - 1), periodic/Neumann: G = x^3 + (lam - 3) x   (the constant
+//   lam - 2 of G(v) is dropped: every operator it passes through maps constants to zero);
+//   unshifted x = v (Dirichlet):                       G = v^3 - 3 v^2 + lam v.
+// ---------------------------------------------------------------------------------------
+
+// Residual accumulators in the kernel precision: |w_new - w| of two nearby floats is exact
+// (Sterbenz), and a max is exact in any precision; the block result is widened to FP64.
+template <typename T>
+struct RedAcc {
+    T dmax;   // max |w_new - w|
+    T vmax;   // max |w_new| (stored variable)
+};
+
+template <typename T>
+struct OpBase {
+    long long ls, ps;
+    __device__ __forceinline__ size_t at(int line, int pos) const {
+        return static_cast<size_t>(line) * static_cast<size_t>(ls) + static_cast<size_t>(pos) * static_cast<size_t>(ps);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T g_lag(T x, T g2, T g1) { return x * fma(x, x + g2, g1); }
+
+// H applied to one field.
+template <typename T>
+struct OpCopy : OpBase<T> {
+    static constexpr int NF = 1;
+    static constexpr int kAxes = 3;
+    static constexpr bool kReduce = false;
+    const T* in;
+    T* out;
+    __device__ __forceinline__ void load(int line, int pos, T (&f)[1]) const { f[0] = in[this->at(line, pos)]; }
+    __device__ __forceinline__ void store(int line, int pos, const T (&h)[1], RedAcc<T>&) const { out[this->at(line, pos)] = h[0]; }
+};
+
+// 2D pass 1 (y, inner c): T = H_iy G(w), S = H_iy w.
+template <typename T>
+struct OpP1 : OpBase<T> {
+    static constexpr int NF = 2;
+    static constexpr int kAxes = 2;
+    static constexpr bool kReduce = false;
+    const T* w;
+    T* t_out;
+    T* s_out;
+    T g2, g1;
+    __device__ __forceinline__ void load(int line, int pos, T (&f)[2]) const {
+        const T x = w[this->at(line, pos)];
+        f[0] = g_lag(x, g2, g1);
+        f[1] = x;
+    }
+    __device__ __forceinline__ void store(int line, int pos, const T (&h)[2], RedAcc<T>&) const {
+        const size_t i = this->at(line, pos);
+        t_out[i] = h[0];
+        s_out[i] = h[1];
+    }
+};
+
+// 2D pass 2 (x, inner c): with A1 = H_ix(2T - G), A2 = H_ix(w - S):
+//   U = S + A2 (= w - D_ix D_iy w),  P = beta (A1 - T) + U
+// (beta (A1 - T) = beta (M_i^{-1} G - G + D_ix D_iy G)).
+template <typename T>
+struct OpP2 : OpBase<T> {
+    static constexpr int NF = 2;
+    static constexpr int kAxes = 1;
+    static constexpr bool kReduce = false;
+    const T* w;
+    const T* t_in;
+    const T* s_in;
+    T* p_out;
+    T* u_out;
+    T g2, g1, beta;
+    __device__ __forceinline__ void load(int line, int pos, T (&f)[2]) const {
+        const size_t i = this->at(line, pos);
+        const T x = w[i];
+        f[0] = T(2) * t_in[i] - g_lag(x, g2, g1);
+        f[1] = x - s_in[i];
+    }
+    __device__ __forceinline__ void store(int line, int pos, const T (&h)[2], RedAcc<T>&) const {
+        const size_t i = this->at(line, pos);
+        const T u = s_in[i] + h[1];
+        u_out[i] = u;
+        p_out[i] = fma(beta, h[0] - t_in[i], u);
+    }
+};
+
+// 2D pass 3 (y, outer c): Q1 = H_oy P, Q2 = H_oy U.
+template <typename T>
+struct OpP3 : OpBase<T> {
+    static constexpr int NF = 2;
+    static constexpr int kAxes = 2;
+    static constexpr bool kReduce = false;
+    const T* p_in;
+    const T* u_in;
+    T* q1_out;
+    T* q2_out;
+    __device__ __forceinline__ void load(int line, int pos, T (&f)[2]) const {
+        const size_t i = this->at(line, pos);
+        f[0] = p_in[i];
+        f[1] = u_in[i];
+    }
+    __device__ __forceinline__ void store(int line, int pos, const T (&h)[2], RedAcc<T>&) const {
+        const size_t i = this->at(line, pos);
+        q1_out[i] = h[0];
+        q2_out[i] = h[1];
+    }
+};
+
+// 2D pass 4 (x, outer c): w_new = Y + w - Q2 + H_ox(Q1 - U), written over w, with the
+// residual max |w_new - w| and the scale max |w_new|.
+template <typename T>
+struct OpP4 : OpBase<T> {
+    static constexpr int NF = 1;
+    static constexpr int kAxes = 1;
+    static constexpr bool kReduce = true;
+    const T* q1_in;
+    const T* q2_in;
+    const T* u_in;
+    const T* y_in;
+    T* w;
+    T shift;
+    __device__ __forceinline__ void load(int line, int pos, T (&f)[1]) const {
+        const size_t i = this->at(line, pos);
+        f[0] = q1_in[i] - u_in[i];
+    }
+    __device__ __forceinline__ void store(int line, int pos, const T (&h)[1], RedAcc<T>& r) const {
+        const size_t i = this->at(line, pos);
+        const T old = w[i];
+        const T nw = (y_in[i] + old - q2_in[i]) + h[0];
+        w[i] = nw;
+        r.dmax = fmax(r.dmax, fabs(nw - old));
+        r.vmax = fmax(r.vmax, fabs(nw));
+    }
+};
+
+// 1D pass a (inner c): E = H_i[r + beta G(w)] - beta G(w).
+template <typename T>
+struct Op1a : OpBase<T> {
+    static constexpr int NF = 1;
+    static constexpr int kAxes = 1;
+    static constexpr bool kReduce = false;
+    const T* r;
+    const T* w;
+    T* e_out;
+    T g2, g1, beta;
+    __device__ __forceinline__ void load(int line, int pos, T (&f)[1]) const {
+        const size_t i = this->at(line, pos);
+        f[0] = fma(beta, g_lag(w[i], g2, g1), r[i]);
+    }
+    __device__ __forceinline__ void store(int line, int pos, const T (&h)[1], RedAcc<T>&) const {
+        const size_t i = this->at(line, pos);
+        e_out[i] = h[0] - beta * g_lag(w[i], g2, g1);
+    }
+};
+
+// 1D pass b (outer c): w_new = H_o E over w, with the residual.
+template <typename T>
+struct Op1b : OpBase<T> {
+    static constexpr int NF = 1;
+    static constexpr int kAxes = 1;
+    static constexpr bool kReduce = true;
+    const T* e_in;
+    T* w;
+    T shift;
+    __device__ __forceinline__ void load(int line, int pos, T (&f)[1]) const { f[0] = e_in[this->at(line, pos)]; }
+    __device__ __forceinline__ void store(int line, int pos, const T (&h)[1], RedAcc<T>& r) const {
+        const size_t i = this->at(line, pos);
+        const T old = w[i];
+        w[i] = h[0];
+        r.dmax = fmax(r.dmax, fabs(h[0] - old));
+        r.vmax = fmax(r.vmax, fabs(h[0]));
+    }
+};
+
+// Block-wide max of the two residual values, then one atomic max per block on the
+// bit patterns (non-negative doubles order like their unsigned bits).
+template <typename T>
+__device__ __forceinline__ void block_reduce_store(RedAcc<T> r, unsigned long long* slots) {
+    __shared__ double s_d[32], s_v[32];
+    double a = static_cast<double>(r.dmax), b = static_cast<double>(r.vmax);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fmax(a, __shfl_xor_sync(kFull, a, o));
+        b = fmax(b, __shfl_xor_sync(kFull, b, o));
+    }
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nthreads = blockDim.x * blockDim.y;
+    const int warp = tid >> 5, lane = tid & 31;
+    if (lane == 0) {
+        s_d[warp] = a;
+        s_v[warp] = b;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (nthreads + 31) >> 5;
+        a = lane < nw ? s_d[lane] : 0.0;
+        b = lane < nw ? s_v[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fmax(a, __shfl_xor_sync(kFull, a, o));
+            b = fmax(b, __shfl_xor_sync(kFull, b, o));
+        }
+        if (lane == 0) {
+            atomicMax(&slots[0], static_cast<unsigned long long>(__double_as_longlong(a)));
+            atomicMax(&slots[1], static_cast<unsigned long long>(__double_as_longlong(b)));
+        }
+    }
+}
+
+}  // namespace molt

@@ -1,0 +1,261 @@
+"""Python binding of the C ABI in ``include/molt.h`` (argument marshalling only).
+
+Every computation runs in ``libmolt.so``; this module converts torch tensors and streams to
+raw pointers and return codes to exceptions.  There is no fallback: if the library is
+missing, importing the binding's loader raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libmolt.so")
+
+MOLT_OK, MOLT_ERR_ARG, MOLT_ERR_NOT_CONVERGED, MOLT_ERR_CUDA, MOLT_ERR_OOM, MOLT_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+BC = {"periodic": 0, "neumann": 1, "dirichlet": 2}
+PRECISION = {"fp32": 0, "fp64": 1}
+SCHEME = {"be": 0, "bdf2": 1, "sdirk2": 2, "sdirk3": 3, "sdc2": 4}
+
+# Every symbol declared in include/molt.h.
+EXPORTS = [
+    "molt_grid_create", "molt_grid_destroy", "molt_solver_create", "molt_solver_destroy",
+    "molt_set_params", "molt_set_bc", "molt_reset_history", "molt_step", "molt_run_host",
+    "molt_energy", "molt_mass", "molt_helmholtz_apply", "molt_quadrature_weights",
+    "molt_last_error", "molt_kernel_launches", "molt_profile_enable", "molt_profile_collect",
+]
+PROFILE_SLOTS = 32
+PASS_NAMES = ["H", "pass1", "pass2", "pass3", "pass4", "pass1d_a", "pass1d_b", ""]
+
+
+class MoltError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"molt status {status}: {message}")
+        self.status = status
+
+
+class NotConverged(MoltError):
+    pass
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("quad_order", ctypes.c_int), ("precision", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int)]
+
+
+class _StepInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("stages", ctypes.c_int), ("iters", ctypes.c_int * 4),
+                ("total_iters", ctypes.c_int), ("residual", ctypes.c_double), ("tol_used", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libmolt.so (built by ``paper_1611_04214_gb300.build``); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1611_04214_gb300.build` "
+                          "(the library has no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P, I, D, VP = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "molt_grid_create": ([ctypes.POINTER(P), I, I, I, D, D, I], I),
+        "molt_grid_destroy": ([P], None),
+        "molt_solver_create": ([ctypes.POINTER(P), P, ctypes.POINTER(_Params)], I),
+        "molt_solver_destroy": ([P], None),
+        "molt_set_params": ([P, ctypes.POINTER(_Params)], I),
+        "molt_set_bc": ([P, I], I),
+        "molt_reset_history": ([P], I),
+        "molt_step": ([P, VP, D, I, VP, ctypes.POINTER(_StepInfo)], I),
+        "molt_run_host": ([P, VP, D, I, I, VP, ctypes.POINTER(_StepInfo)], I),
+        "molt_energy": ([P, VP, ctypes.POINTER(D), VP], I),
+        "molt_mass": ([P, VP, ctypes.POINTER(D), VP], I),
+        "molt_helmholtz_apply": ([P, I, D, VP, VP, VP], I),
+        "molt_quadrature_weights": ([D, I, ctypes.POINTER(I), I, ctypes.POINTER(D)], I),
+        "molt_last_error": ([P], ctypes.c_char_p),
+        "molt_kernel_launches": ([P], ctypes.c_longlong),
+        "molt_profile_enable": ([P, I], I),
+        "molt_profile_collect": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int, handle=None):
+    if status == MOLT_OK:
+        return
+    msg = load_library().molt_last_error(handle).decode()
+    if status == MOLT_ERR_NOT_CONVERGED:
+        raise NotConverged(status, msg)
+    raise MoltError(status, msg)
+
+
+def molt_quadrature_weights(nu: float, M: int, offsets, side: str):
+    """Weights of J^L (side 'L') or J^R ('R') for integer node offsets (host-only call)."""
+    lib = load_library()
+    offs = (ctypes.c_int * (M + 1))(*[int(o) for o in offsets])
+    out = (ctypes.c_double * (M + 1))()
+    _check(lib.molt_quadrature_weights(float(nu), int(M), offs, 0 if side == "L" else 1, out))
+    return list(out)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+@dataclass
+class StepInfo:
+    status: int
+    stages: int
+    iters: list = field(default_factory=list)
+    total_iters: int = 0
+    residual: float = 0.0
+    tol_used: float = 0.0
+
+
+class Solver:
+    """A grid + solver pair of the C ABI (molt_grid_create + molt_solver_create)."""
+
+    def __init__(self, nx: int, ny: int = 1, Lx: float = 6.283185307179586, Ly: float = 6.283185307179586,
+                 bc: str = "periodic", eps: float = 0.1, quad_order: int = 4, precision: str = "fp32",
+                 tol: float = 1e-10, max_iter: int = 500):
+        lib = load_library()
+        self._lib = lib
+        self.nx, self.ny, self.bc, self.precision = nx, ny, bc, precision
+        self.dim = 1 if ny == 1 else 2
+        g = ctypes.c_void_p()
+        _check(lib.molt_grid_create(ctypes.byref(g), self.dim, nx, ny, Lx, Ly, BC[bc]))
+        self._grid = g
+        self._params = _Params(eps, quad_order, PRECISION[precision], tol, max_iter)
+        s = ctypes.c_void_p()
+        st = lib.molt_solver_create(ctypes.byref(s), g, ctypes.byref(self._params))
+        if st != MOLT_OK:
+            msg = lib.molt_last_error(None).decode()
+            lib.molt_grid_destroy(g)
+            self._grid = None
+            raise MoltError(st, msg)
+        self._h = s
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float32 if self.precision == "fp32" else torch.float64
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.molt_solver_destroy(self._h)
+            self._h = None
+        if getattr(self, "_grid", None):
+            self._lib.molt_grid_destroy(self._grid)
+            self._grid = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _field(self, t):
+        if not t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != self.nx * self.ny:
+            raise ValueError(f"expected a contiguous CUDA {self.dtype} tensor of {self.ny}x{self.nx} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def set_params(self, eps=None, quad_order=None, tol=None, max_iter=None):
+        p = self._params
+        if eps is not None:
+            p.eps = eps
+        if quad_order is not None:
+            p.quad_order = quad_order
+        if tol is not None:
+            p.tol = tol
+        if max_iter is not None:
+            p.max_iter = max_iter
+        _check(self._lib.molt_set_params(self._h, ctypes.byref(p)), self._h)
+
+    def set_bc(self, bc: str):
+        _check(self._lib.molt_set_bc(self._h, BC[bc]), self._h)
+        self.bc = bc
+
+    def reset_history(self):
+        _check(self._lib.molt_reset_history(self._h), self._h)
+
+    def step(self, u, dt: float, scheme: str, stream=None, raise_on_nonconvergence: bool = True) -> StepInfo:
+        info = _StepInfo()
+        st = self._lib.molt_step(self._h, self._field(u), float(dt), SCHEME[scheme], _stream_handle(stream),
+                                 ctypes.byref(info))
+        out = StepInfo(info.status, info.stages, list(info.iters)[: max(info.stages, 0)], info.total_iters,
+                       info.residual, info.tol_used)
+        if st == MOLT_ERR_NOT_CONVERGED and not raise_on_nonconvergence:
+            return out
+        _check(st, self._h)
+        return out
+
+    def run_host(self, u_host, dt: float, scheme: str, nsteps: int, stream=None) -> StepInfo:
+        """End-to-end call on a host (CPU) tensor: copy in, nsteps steps, copy back."""
+        if u_host.is_cuda or u_host.dtype != self.dtype or not u_host.is_contiguous():
+            raise ValueError("expected a contiguous host tensor of the solver's dtype")
+        info = _StepInfo()
+        st = self._lib.molt_run_host(self._h, ctypes.c_void_p(u_host.data_ptr()), float(dt), SCHEME[scheme],
+                                     int(nsteps), _stream_handle(stream), ctypes.byref(info))
+        _check(st, self._h)
+        return StepInfo(info.status, info.stages, list(info.iters)[: max(info.stages, 0)], info.total_iters,
+                        info.residual, info.tol_used)
+
+    def energy(self, u, stream=None) -> float:
+        out = ctypes.c_double()
+        _check(self._lib.molt_energy(self._h, self._field(u), ctypes.byref(out), _stream_handle(stream)), self._h)
+        return out.value
+
+    def mass(self, u, stream=None) -> float:
+        out = ctypes.c_double()
+        _check(self._lib.molt_mass(self._h, self._field(u), ctypes.byref(out), _stream_handle(stream)), self._h)
+        return out.value
+
+    def helmholtz_apply(self, axis: int, c: float, inp, out, stream=None):
+        _check(self._lib.molt_helmholtz_apply(self._h, int(axis), float(c), self._field(inp), self._field(out),
+                                              _stream_handle(stream)), self._h)
+
+    def kernel_launches(self) -> int:
+        return int(self._lib.molt_kernel_launches(self._h))
+
+    def profile_enable(self, on: bool = True):
+        _check(self._lib.molt_profile_enable(self._h, 1 if on else 0), self._h)
+
+    def profile_collect(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last collect (slots of molt_profile_collect)."""
+        ms = (ctypes.c_double * PROFILE_SLOTS)()
+        cnt = (ctypes.c_longlong * PROFILE_SLOTS)()
+        _check(self._lib.molt_profile_collect(self._h, ms, cnt), self._h)
+        out = {}
+        for slot in range(PROFILE_SLOTS):
+            if cnt[slot] == 0:
+                continue
+            if slot < 8:
+                name = f"rows_{PASS_NAMES[slot]}"
+            elif slot < 16:
+                name = f"cols_agg_{PASS_NAMES[slot - 8]}"
+            elif slot == 16:
+                name = "cols_carry"
+            else:
+                name = f"cols_final_{PASS_NAMES[slot - 17]}"
+            out[name] = (ms[slot], int(cnt[slot]))
+        return out

@@ -1,0 +1,247 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
+
+Tolerances.  FP64 runs must agree to rounding (1e-11 relative to the field's scale for single
+sweeps; fixed-point runs to a small multiple of the fixed-point tolerance).  FP32 runs are held
+to the 1e-6 relative bar: one sweep rounds each of its ~M+3 fused multiply-adds per point at
+2^-24 and the recurrences damp earlier rounding by d < 1 per step, so a few 1e-7 is expected.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle.helmholtz import helmholtz_inverse  # noqa: E402
+from oracle.solver import OracleSolver, Problem, energy, mass  # noqa: E402
+from paper_1611_04214_gb300.inputs import (paper_ic_1d, spacing, uniform_noise)  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_04214_gb300 import build
+    build.build_library()
+
+
+def _solver(**kw):
+    from paper_1611_04214_gb300.molt import Solver
+    return Solver(**kw)
+
+
+def _dev(a, precision):
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    return torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def _host(t):
+    return t.detach().to("cpu", torch.float64).numpy()
+
+
+SWEEP_TOL = {"fp64": 1e-11, "fp32": 1e-6}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+@pytest.mark.parametrize("M", [2, 4, 6])
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("nu", [0.02, 0.3, 4.0])
+def test_helmholtz_sweep_matches_oracle(precision, bc, M, axis, nu):
+    # 300 x 1000: rows of 1000 leave a ragged last chunk; columns of 300 span three tiles of 128
+    # with a ragged tail.
+    ny, nx = 300, 1000
+    L = 2 * np.pi
+    n = nx if axis == 0 else ny
+    h = spacing(n, L, bc == "periodic")
+    c = (h / nu) ** 2
+    f = uniform_noise((ny, nx), 1.0, seed=11 + M, mean=1.0)
+    with _solver(nx=nx, ny=ny, bc=bc, quad_order=M, precision=precision, eps=0.1) as s:
+        fin = _dev(f, precision)
+        out = torch.empty_like(fin)
+        s.helmholtz_apply(axis, c, fin, out)
+        torch.cuda.synchronize()
+        got = _host(out)
+    ref = helmholtz_inverse(f, c, h, bc, M, axis=1 if axis == 0 else 0)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    assert err < SWEEP_TOL[precision], err
+
+
+@pytest.mark.parametrize("n", [8, 9, 17, 33, 130, 257, 2049])
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+def test_sweep_line_lengths(n, bc):
+    # Team sizes 1..1024 threads per line, several lines per block, minimum lengths for M = 6.
+    M = 6 if n >= 9 else 4
+    nlines = 37
+    h = spacing(n, 1.0, bc == "periodic")
+    c = (h / 0.2) ** 2
+    f = uniform_noise((nlines, n), 1.0, seed=n, mean=0.5)
+    with _solver(nx=n, ny=nlines, bc=bc, quad_order=M, precision="fp64", eps=0.1, Lx=1.0, Ly=1.0) as s:
+        fin = _dev(f, "fp64")
+        out = torch.empty_like(fin)
+        s.helmholtz_apply(0, c, fin, out)
+        got = _host(out)
+        fT = _dev(f.T.copy(), "fp64")
+        outT = torch.empty_like(fT)
+    ref = helmholtz_inverse(f, c, h, bc, M, axis=1)
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+    if n >= 8:
+        with _solver(nx=nlines, ny=n, bc=bc, quad_order=M, precision="fp64", eps=0.1, Lx=1.0, Ly=1.0) as s:
+            s.helmholtz_apply(1, c, fT, outT)
+            gotT = _host(outT)
+        assert np.abs(gotT - ref.T).max() <= 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+@pytest.mark.parametrize("axis", [0, 1])
+def test_full_size_sweep_sampled(bc, axis):
+    # 8192^2 FP32 (the benchmark size): sampled lines against the oracle, one line at a time.
+    n = 8192
+    M = 4
+    h = spacing(n, 2 * np.pi, bc == "periodic")
+    c = (h / 0.08) ** 2
+    g = torch.Generator(device="cuda").manual_seed(5)
+    fin = torch.rand((n, n), generator=g, device="cuda", dtype=torch.float32) * 2
+    out = torch.empty_like(fin)
+    with _solver(nx=n, ny=n, bc=bc, quad_order=M, precision="fp32", eps=0.02) as s:
+        s.helmholtz_apply(axis, c, fin, out)
+        torch.cuda.synchronize()
+    for line in [0, 1, 777, 4095, 8190, 8191]:
+        if axis == 0:
+            f_line = fin[line].double().cpu().numpy()
+            got = out[line].double().cpu().numpy()
+        else:
+            f_line = fin[:, line].double().cpu().numpy()
+            got = out[:, line].double().cpu().numpy()
+        ref = helmholtz_inverse(f_line, c, h, bc, M)
+        assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-6
+
+
+def test_long_rows_single_field():
+    # Rows longer than 8192 use 16 positions per thread; 8193 is the first such length.
+    for n in (8193, 16384):
+        nlines = 8
+        h = spacing(n, 2 * np.pi, True)
+        c = (h / 0.05) ** 2
+        f = uniform_noise((nlines, n), 1.0, seed=3, mean=1.0)
+        with _solver(nx=n, ny=nlines, bc="periodic", quad_order=4, precision="fp32", eps=0.02) as s:
+            fin = _dev(f, "fp32")
+            out = torch.empty_like(fin)
+            s.helmholtz_apply(0, c, fin, out)
+            got = _host(out)
+        ref = helmholtz_inverse(f.astype(np.float32).astype(np.float64), c, h, "periodic", 4, axis=1)
+        assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+@pytest.mark.parametrize("dims", [(1, 200), (60, 80)])
+def test_energy_and_mass(precision, bc, dims):
+    ny, nx = dims
+    u = uniform_noise((ny, nx), 0.8, seed=2)
+    prob = Problem(nx=nx, ny=ny, bc=bc, eps=0.07)
+    with _solver(nx=nx, ny=ny, bc=bc, precision=precision, eps=0.07) as s:
+        ud = _dev(u, precision)
+        uq = _host(ud)           # the values the GPU sees (FP32 rounding included)
+        E, m = s.energy(ud), s.mass(ud)
+    assert abs(E - energy(prob, uq)) <= 1e-12 * abs(energy(prob, uq))
+    assert abs(m - mass(prob, uq)) <= 1e-12 * max(1.0, abs(mass(prob, uq)))
+
+
+def _run_both(nx, ny, bc, eps, M, tol, max_iter, scheme, dt, steps, precision, u0):
+    prob = Problem(nx=nx, ny=ny, bc=bc, eps=eps, M=M, tol=tol, max_iter=max_iter)
+    ref_solver = OracleSolver(prob)
+    with _solver(nx=nx, ny=ny, bc=bc, quad_order=M, precision=precision, eps=eps, tol=tol, max_iter=max_iter) as s:
+        ud = _dev(u0, precision)
+        u_ref = _host(ud).reshape(ny, nx)     # start both from the same (rounded) values
+        iters_gpu, iters_ref = [], []
+        for _ in range(steps):
+            info = s.step(ud, dt, scheme)
+            iters_gpu.append(info.iters)
+            u_ref, rinfo = ref_solver.step(u_ref, dt, scheme)
+            iters_ref.append(rinfo.iters)
+        got = _host(ud).reshape(ny, nx)
+    return got, u_ref, iters_gpu, iters_ref
+
+
+@pytest.mark.parametrize("scheme", ["be", "bdf2", "sdirk2", "sdirk3"])
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+def test_steps_2d_fp64_match_oracle(scheme, bc):
+    ny, nx = 72, 96
+    u0 = uniform_noise((ny, nx), 0.05, seed=7, mean=0.1)
+    if bc == "dirichlet":
+        u0[0, :] = u0[-1, :] = -1
+        u0[:, 0] = u0[:, -1] = -1
+    got, ref, ig, ir = _run_both(nx, ny, bc, 0.1, 4, 1e-11, 2000, scheme, 2e-3, 3, "fp64", u0)
+    assert np.abs(got - ref).max() < 1e-9
+    # iteration counts: identical up to a last-iteration tie at the tolerance
+    for a, b in zip(ig, ir):
+        assert all(abs(x - y) <= 1 for x, y in zip(a, b)), (ig, ir)
+
+
+@pytest.mark.parametrize("scheme", ["be", "bdf2", "sdirk3"])
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+def test_steps_2d_fp32_within_bar(scheme, bc):
+    ny, nx = 72, 96
+    u0 = uniform_noise((ny, nx), 0.05, seed=8, mean=0.1)
+    if bc == "dirichlet":
+        u0[0, :] = u0[-1, :] = -1
+        u0[:, 0] = u0[:, -1] = -1
+    got, ref, ig, ir = _run_both(nx, ny, bc, 0.1, 4, 1e-10, 2000, scheme, 2e-3, 3, "fp32", u0)
+    v_scale = np.abs(ref + 1).max()
+    assert np.abs(got - ref).max() / v_scale < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_1d_neumann_be_matches_oracle(precision):
+    # The 1D Neumann BE workload (N = 256, eps = 0.1, dt = 1e-3), first 20 steps.
+    n = 256
+    u0 = uniform_noise((1, n), 0.05, seed=0)
+    got, ref, ig, ir = _run_both(n, 1, "neumann", 0.1, 4, 1e-10, 500, "be", 1e-3, 20, precision, u0)
+    bar = 1e-10 if precision == "fp64" else 1e-6
+    assert np.abs(got - ref).max() / np.abs(ref + 1).max() < bar
+    if precision == "fp64":
+        assert all(abs(a[0] - b[0]) <= 1 for a, b in zip(ig, ir))
+
+
+def test_1d_periodic_paper_ic_sdirk2():
+    n = 512
+    u0 = paper_ic_1d(n)[None, :]
+    got, ref, _, _ = _run_both(n, 1, "periodic", 0.18, 6, 1e-12, 2000, "sdirk2", 0.025, 4, "fp64", u0)
+    assert np.abs(got - ref).max() < 1e-10
+
+
+def test_run_host_matches_device_path():
+    ny, nx = 40, 48
+    u0 = uniform_noise((ny, nx), 0.05, seed=9)
+    with _solver(nx=nx, ny=ny, bc="periodic", precision="fp64", eps=0.1, tol=1e-11) as s:
+        ud = _dev(u0, "fp64")
+        for _ in range(2):
+            s.step(ud, 1e-3, "bdf2")
+        dev_result = _host(ud)
+    with _solver(nx=nx, ny=ny, bc="periodic", precision="fp64", eps=0.1, tol=1e-11) as s:
+        uh = torch.tensor(u0, dtype=torch.float64)
+        s.run_host(uh, 1e-3, "bdf2", 2)
+        host_result = uh.numpy()
+    assert np.array_equal(dev_result, host_result)
+
+
+def test_not_converged_and_bad_arguments():
+    from paper_1611_04214_gb300.molt import MoltError, NotConverged
+    ny, nx = 32, 40
+    u0 = uniform_noise((ny, nx), 0.05, seed=1)
+    with _solver(nx=nx, ny=ny, bc="neumann", precision="fp64", eps=0.1, tol=1e-14, max_iter=1) as s:
+        ud = _dev(u0, "fp64")
+        with pytest.raises(NotConverged):
+            s.step(ud, 1e-3, "be")
+        info = s.step(ud, 1e-3, "be", raise_on_nonconvergence=False)
+        assert info.status == -2 and info.iters == [1]
+        with pytest.raises(MoltError):
+            s.step(ud, -1.0, "be")
+        out = torch.empty_like(ud)
+        with pytest.raises(MoltError):
+            s.helmholtz_apply(1, 0.01, ud, ud)        # column sweeps are not in place
+        with pytest.raises(MoltError):
+            s.helmholtz_apply(0, -0.01, ud, out)
+    with pytest.raises(MoltError):
+        _solver(nx=nx, ny=ny, quad_order=3)

@@ -1,0 +1,82 @@
+"""CPU-only checks of the C-ABI library: it builds, loads, exports every symbol the header
+declares, and its host-side quadrature weights agree with the oracle's (no GPU calls)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1611_04214_gb300 import build as molt_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    molt_build.build_library()
+    from paper_1611_04214_gb300 import molt
+    return molt.load_library()
+
+
+def _declared_symbols():
+    with open(os.path.join(ROOT, "include", "molt.h")) as fh:
+        text = fh.read()
+    decl = re.compile(r"^\s*(?:molt_status|void|const char\s*\*|long long)\s+(molt_[a-z_]+)\s*\(", re.M)
+    return sorted(set(decl.findall(text)))
+
+
+def test_header_symbols_exported(lib):
+    from paper_1611_04214_gb300 import molt
+    declared = _declared_symbols()
+    assert declared, "no declarations parsed"
+    assert sorted(molt.EXPORTS) == declared
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("M", [2, 4, 6])
+@pytest.mark.parametrize("nu", [1e-3, 0.08, 0.27, 1.5, 2.5, 9.0])
+def test_host_weights_match_oracle(lib, M, nu):
+    # The library computes the weights from exponential moments (series / recursion); the oracle
+    # integrates the definition by Gauss-Legendre quadrature.  Same Sec. 3.2 definition.
+    from oracle.weights import local_weights
+    from paper_1611_04214_gb300.molt import molt_quadrature_weights
+    H = M // 2
+    for offs in [list(range(-H, H + 1)), list(range(0, M + 1)), list(range(-M, 1)), list(range(-1, M))]:
+        for side in ("L", "R"):
+            got = np.array(molt_quadrature_weights(nu, M, offs, side))
+            ref = local_weights(nu, tuple(offs), side)
+            np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-15 * max(nu, 1.0))
+
+
+def test_weights_reject_bad_arguments(lib):
+    from paper_1611_04214_gb300.molt import MoltError, molt_quadrature_weights
+    with pytest.raises(MoltError):
+        molt_quadrature_weights(0.0, 4, [-2, -1, 0, 1, 2], "L")
+    with pytest.raises(MoltError):
+        molt_quadrature_weights(0.1, 3, [-1, 0, 1, 2], "L")
+
+
+def test_grid_validation_host_only(lib):
+    # molt_grid_create does no device work, so its argument checks run without a GPU.
+    g = ctypes.c_void_p()
+    assert lib.molt_grid_create(ctypes.byref(g), 2, 64, 48, 1.0, 1.0, 1) == 0
+    lib.molt_grid_destroy(g)
+    assert lib.molt_grid_create(ctypes.byref(g), 1, 64, 2, 1.0, 1.0, 0) == -1       # 1D needs ny = 1
+    assert b"ny = 1" in lib.molt_last_error(None)
+    assert lib.molt_grid_create(ctypes.byref(g), 2, 4, 48, 1.0, 1.0, 0) == -1       # too short
+    assert lib.molt_grid_create(ctypes.byref(g), 2, 64, 48, -1.0, 1.0, 0) == -1     # bad length
+    assert lib.molt_grid_create(ctypes.byref(g), 2, 64, 48, 1.0, 1.0, 7) == -1      # bad bc
+    assert lib.molt_grid_create(ctypes.byref(g), 3, 64, 48, 1.0, 1.0, 0) == -1      # bad dim
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1611_04214_gb300 import molt
+    saved = molt._lib
+    try:
+        molt._lib = None
+        with pytest.raises(ImportError):
+            molt.load_library(str(tmp_path / "libmolt.so"))
+    finally:
+        molt._lib = saved
