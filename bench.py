@@ -252,7 +252,7 @@ def run_ours(args, rank, world, dist):
         e2e_steps = max(1, min(2, args.steps))
         e2e_pts, t0 = 0, time.perf_counter()
         for _ in range(e2e_steps):
-            info = solver.run_host(uh, WORKLOAD["dt"], WORKLOAD["scheme"], 1)
+            info = solver.run_host(uh, WORKLOAD["dt"], WORKLOAD["scheme"], 1, raise_on_nonconvergence=False)
             e2e_pts += sum(SWEEPS_RHS + SWEEPS_ITER * k for k in info.iters) * n * n
         e2e_secs = time.perf_counter() - t0
         e2e = {"value": e2e_pts / e2e_secs / 1e9, "unit": UNIT, "h2d_bytes_per_step": n * n * elem,

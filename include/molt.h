@@ -87,8 +87,9 @@ void molt_grid_destroy(molt_grid* grid);
 /* Create a solver on the current CUDA device for `grid` with parameters `p` (copied).
  * Allocates the device workspace (about 12 fields of the grid's size).
  * Errors: MOLT_ERR_ARG (eps <= 0, M not in {2,4,6}, tol <= 0, max_iter < 1,
- * line shorter than M+1 or longer than the sweep kernels support), MOLT_ERR_OOM,
- * MOLT_ERR_CUDA. */
+ * line shorter than M+2, or x lines longer than the row kernels support: 16384 nodes),
+ * MOLT_ERR_OOM, MOLT_ERR_CUDA.  2D time steps additionally need nx <= 8192
+ * (their row passes sweep two fields); molt_step returns MOLT_ERR_UNSUPPORTED otherwise. */
 molt_status molt_solver_create(molt_solver** solver, const molt_grid* grid, const molt_params* p);
 void molt_solver_destroy(molt_solver* solver);
 
@@ -108,9 +109,9 @@ molt_status molt_reset_history(molt_solver* solver);
  * precision; the residual max-norm is exact (Sterbenz) and compared in FP64.  FP32 fields
  * cannot resolve a change below a few units in the last place of the stored variable w
  * (w = u on periodic/Neumann grids, w = u + 1 on Dirichlet grids), so for FP32 solvers the
- * tolerance applied is max(tol, 4 * 2^-24 * max|w|), and an iteration whose residual is below
- * 64 * 2^-24 * max|w| and has not improved by 10% for 8 iterations is accepted as converged at
- * FP32 precision; `info->tol_used` reports the tolerance (or residual) that ended the stage.  BDF2 and SDC2 keep history between calls made
+ * tolerance applied is max(tol, 2 * 2^-24 * max|w|), and an iteration whose residual is below
+ * 64 * 2^-24 * max|w| and has not reached a new minimum for 6 iterations is accepted as
+ * converged at FP32 precision (the rounding noise floor); `info->tol_used` reports the tolerance (or residual) that ended the stage.  BDF2 and SDC2 keep history between calls made
  * with the same dt.  Returns MOLT_ERR_NOT_CONVERGED (field = last iterate, history
  * updated) when a stage hits max_iter; `info` may be NULL. */
 molt_status molt_step(molt_solver* solver, void* u_dev, double dt, int scheme, void* stream,

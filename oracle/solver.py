@@ -117,6 +117,15 @@ class StageResult:
     iters: int
     residual: float
     converged: bool
+    history: list = field(default_factory=list)   # residual after each iteration
+
+    def contraction(self, last: int = 5) -> float:
+        """Observed contraction factor: geometric mean of the last residual ratios."""
+        h = [r for r in self.history if r > 0]
+        if len(h) < 2:
+            return 0.0
+        h = h[-(last + 1):]
+        return float((h[-1] / h[0]) ** (1.0 / (len(h) - 1)))
 
 
 def _H(prob: Problem, f: np.ndarray, c: float, axis: str) -> np.ndarray:
@@ -172,13 +181,15 @@ def stage_solve(prob: Problem, r: np.ndarray, v0: np.ndarray, tau: float, Y: np.
         Y = stage_rhs_inverse(prob, r, sp)
     v = np.array(v0, dtype=np.float64)
     res = np.inf
+    hist = []
     for k in range(1, prob.max_iter + 1):
         v_new = fixed_point_map(prob, Y, v, sp)
         res = float(np.max(np.abs(v_new - v)))
+        hist.append(res)
         v = v_new
         if res < prob.tol:
-            return StageResult(v, k, res, True)
-    return StageResult(v, prob.max_iter, res, False)
+            return StageResult(v, k, res, True, hist)
+    return StageResult(v, prob.max_iter, res, False, hist)
 
 
 ETA2 = 1.0 - np.sqrt(2.0) / 2.0
@@ -212,6 +223,7 @@ class StepInfo:
     iters: list = field(default_factory=list)
     residual: float = 0.0
     converged: bool = True
+    contraction: float = 0.0      # largest observed contraction factor over the stages
 
 
 class OracleSolver:
@@ -228,6 +240,7 @@ class OracleSolver:
         info.iters.append(res.iters)
         info.residual = max(info.residual, res.residual)
         info.converged = info.converged and res.converged
+        info.contraction = max(info.contraction, res.contraction())
 
     def _sdirk(self, v: np.ndarray, dt: float, A: np.ndarray, info: StepInfo) -> np.ndarray:
         eta = A[0, 0]

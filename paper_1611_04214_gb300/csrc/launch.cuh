@@ -4,6 +4,9 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
+#include <type_traits>
+
 #include "molt_internal.h"
 #include "sweep_kernels.cuh"
 
@@ -143,6 +146,63 @@ cudaError_t cols(const LineParams<T>& lp, const Op& op, int nlines, ColScratch<T
     return cudaGetLastError();
 }
 
+// ---- pipelined FP32 rows: pointwise op for each row pass ----
+template <class Op> struct PipeOf { using type = void; };
+template <> struct PipeOf<OpCopy<float>> { using type = PipeCopy<float>; };
+template <> struct PipeOf<OpP2<float>> { using type = PipeP2<float>; };
+template <> struct PipeOf<OpP4<float>> { using type = PipeP4<float>; };
+template <> struct PipeOf<Op1a<float>> { using type = Pipe1a<float>; };
+template <> struct PipeOf<Op1b<float>> { using type = Pipe1b<float>; };
+
+template <class P>
+P pipe_build(int kind, const OpArgs<float>& a) {
+    P p{};
+    p.g2 = a.g2;
+    p.g1 = a.g1;
+    p.beta = a.beta;
+    switch (kind) {
+        case OP_COPY: p.s[0] = a.in0; p.o[0] = a.out0; break;
+        case OP_P2: p.s[0] = a.in0; p.s[1] = a.in1; p.s[2] = a.in2; p.o[0] = a.out0; p.o[1] = a.out1; break;
+        case OP_P4: p.s[0] = a.in0; p.s[1] = a.in2; p.a[0] = a.out0; p.a[1] = a.in3; p.a[2] = a.in1; p.o[0] = a.out0; break;
+        case OP_1A: p.s[0] = a.in0; p.s[1] = a.in1; p.o[0] = a.out0; break;
+        case OP_1B: p.s[0] = a.in0; p.a[0] = a.out0; p.o[0] = a.out0; break;
+    }
+    return p;
+}
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+template <class P>
+bool pipe_eligible(const P& p, int n) {
+    if (n % 512 != 0 || n < 1024 || n > 8192) return false;
+    for (int f = 0; f < P::NS; ++f) if (!aligned16(p.s[f])) return false;
+    for (int f = 0; f < P::NA; ++f) if (!aligned16(p.a[f])) return false;
+    for (int f = 0; f < P::NO; ++f) if (!aligned16(p.o[f])) return false;
+    return true;
+}
+
+template <int M, class P>
+cudaError_t rows_pipe(const LineParams<float>& lp, const P& op, int nlines, unsigned long long* red, cudaStream_t st,
+                      Prof* prof, int kind) {
+    const int n = lp.n;
+    const int TL = n / 16;
+    const size_t smem = static_cast<size_t>(2 * P::NS + P::NA) * n * sizeof(float);
+    auto kern = rows_pipe_kernel<M, P>;
+    static int limit = smem_optin(kern);
+    if (limit < 0 || smem > static_cast<size_t>(limit)) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TL, smem);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int grid = sms * per_sm;
+    if (grid > nlines) grid = nlines;
+    prof_begin(prof, kind, st);
+    kern<<<grid, TL, smem, st>>>(lp, op, nlines, static_cast<long long>(n), red);
+    prof_end(prof, st);
+    return cudaGetLastError();
+}
+
 template <typename T, class Op>
 cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int nx, int ny, ColScratch<T>* cs,
                      unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof, int kind) {
@@ -151,6 +211,17 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
     set_strides<T>(op, axis == 0 ? nx : 1, axis == 0 ? 1 : nx);
     if (launches) *launches += 1;
     if (axis == 0) {
+        if constexpr (std::is_same<T, float>::value && !std::is_same<typename PipeOf<Op>::type, void>::value) {
+            using P = typename PipeOf<Op>::type;
+            const P pop = pipe_build<P>(kind, a);
+            if (pipe_eligible(pop, lp.n)) {
+                switch (lp.M) {
+                    case 2: return rows_pipe<2>(lp, pop, nlines, red, st, prof, kind);
+                    case 4: return rows_pipe<4>(lp, pop, nlines, red, st, prof, kind);
+                    case 6: return rows_pipe<6>(lp, pop, nlines, red, st, prof, kind);
+                }
+            }
+        }
         if constexpr ((Op::kAxes & 1) != 0) {
             switch (lp.M) {
                 case 2: return rows<T, 2>(lp, op, nlines, red, st, prof, kind);

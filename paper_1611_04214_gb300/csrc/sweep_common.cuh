@@ -151,22 +151,31 @@ struct OpBase {
 template <typename T>
 __device__ __forceinline__ T g_lag(T x, T g2, T g1) { return x * fma(x, x + g2, g1); }
 
+// Each op: load() = prologue (reads the inputs at a point, returns the NF fields to sweep);
+// fetch() = the extra inputs the epilogue needs (NA values, read before any store so that the
+// loads of a batch of points are in flight together); put() = epilogue arithmetic and stores.
+
 // H applied to one field.
 template <typename T>
 struct OpCopy : OpBase<T> {
     static constexpr int NF = 1;
+    static constexpr int NA = 1;
     static constexpr int kAxes = 3;
     static constexpr bool kReduce = false;
     const T* in;
     T* out;
     __device__ __forceinline__ void load(int line, int pos, T (&f)[1]) const { f[0] = in[this->at(line, pos)]; }
-    __device__ __forceinline__ void store(int line, int pos, const T (&h)[1], RedAcc<T>&) const { out[this->at(line, pos)] = h[0]; }
+    __device__ __forceinline__ void fetch(int, int, T (&)[NA]) const {}
+    __device__ __forceinline__ void put(int line, int pos, const T (&h)[1], const T (&)[NA], RedAcc<T>&) const {
+        out[this->at(line, pos)] = h[0];
+    }
 };
 
 // 2D pass 1 (y, inner c): T = H_iy G(w), S = H_iy w.
 template <typename T>
 struct OpP1 : OpBase<T> {
     static constexpr int NF = 2;
+    static constexpr int NA = 1;
     static constexpr int kAxes = 2;
     static constexpr bool kReduce = false;
     const T* w;
@@ -178,7 +187,8 @@ struct OpP1 : OpBase<T> {
         f[0] = g_lag(x, g2, g1);
         f[1] = x;
     }
-    __device__ __forceinline__ void store(int line, int pos, const T (&h)[2], RedAcc<T>&) const {
+    __device__ __forceinline__ void fetch(int, int, T (&)[NA]) const {}
+    __device__ __forceinline__ void put(int line, int pos, const T (&h)[2], const T (&)[NA], RedAcc<T>&) const {
         const size_t i = this->at(line, pos);
         t_out[i] = h[0];
         s_out[i] = h[1];
@@ -191,6 +201,7 @@ struct OpP1 : OpBase<T> {
 template <typename T>
 struct OpP2 : OpBase<T> {
     static constexpr int NF = 2;
+    static constexpr int NA = 2;
     static constexpr int kAxes = 1;
     static constexpr bool kReduce = false;
     const T* w;
@@ -205,11 +216,16 @@ struct OpP2 : OpBase<T> {
         f[0] = T(2) * t_in[i] - g_lag(x, g2, g1);
         f[1] = x - s_in[i];
     }
-    __device__ __forceinline__ void store(int line, int pos, const T (&h)[2], RedAcc<T>&) const {
+    __device__ __forceinline__ void fetch(int line, int pos, T (&a)[NA]) const {
         const size_t i = this->at(line, pos);
-        const T u = s_in[i] + h[1];
+        a[0] = t_in[i];
+        a[1] = s_in[i];
+    }
+    __device__ __forceinline__ void put(int line, int pos, const T (&h)[2], const T (&a)[NA], RedAcc<T>&) const {
+        const size_t i = this->at(line, pos);
+        const T u = a[1] + h[1];
         u_out[i] = u;
-        p_out[i] = fma(beta, h[0] - t_in[i], u);
+        p_out[i] = fma(beta, h[0] - a[0], u);
     }
 };
 
@@ -217,6 +233,7 @@ struct OpP2 : OpBase<T> {
 template <typename T>
 struct OpP3 : OpBase<T> {
     static constexpr int NF = 2;
+    static constexpr int NA = 1;
     static constexpr int kAxes = 2;
     static constexpr bool kReduce = false;
     const T* p_in;
@@ -228,7 +245,8 @@ struct OpP3 : OpBase<T> {
         f[0] = p_in[i];
         f[1] = u_in[i];
     }
-    __device__ __forceinline__ void store(int line, int pos, const T (&h)[2], RedAcc<T>&) const {
+    __device__ __forceinline__ void fetch(int, int, T (&)[NA]) const {}
+    __device__ __forceinline__ void put(int line, int pos, const T (&h)[2], const T (&)[NA], RedAcc<T>&) const {
         const size_t i = this->at(line, pos);
         q1_out[i] = h[0];
         q2_out[i] = h[1];
@@ -240,6 +258,7 @@ struct OpP3 : OpBase<T> {
 template <typename T>
 struct OpP4 : OpBase<T> {
     static constexpr int NF = 1;
+    static constexpr int NA = 3;
     static constexpr int kAxes = 1;
     static constexpr bool kReduce = true;
     const T* q1_in;
@@ -252,12 +271,16 @@ struct OpP4 : OpBase<T> {
         const size_t i = this->at(line, pos);
         f[0] = q1_in[i] - u_in[i];
     }
-    __device__ __forceinline__ void store(int line, int pos, const T (&h)[1], RedAcc<T>& r) const {
+    __device__ __forceinline__ void fetch(int line, int pos, T (&a)[NA]) const {
         const size_t i = this->at(line, pos);
-        const T old = w[i];
-        const T nw = (y_in[i] + old - q2_in[i]) + h[0];
-        w[i] = nw;
-        r.dmax = fmax(r.dmax, fabs(nw - old));
+        a[0] = w[i];
+        a[1] = y_in[i];
+        a[2] = q2_in[i];
+    }
+    __device__ __forceinline__ void put(int line, int pos, const T (&h)[1], const T (&a)[NA], RedAcc<T>& r) const {
+        const T nw = (a[1] + a[0] - a[2]) + h[0];
+        w[this->at(line, pos)] = nw;
+        r.dmax = fmax(r.dmax, fabs(nw - a[0]));
         r.vmax = fmax(r.vmax, fabs(nw));
     }
 };
@@ -266,6 +289,7 @@ struct OpP4 : OpBase<T> {
 template <typename T>
 struct Op1a : OpBase<T> {
     static constexpr int NF = 1;
+    static constexpr int NA = 1;
     static constexpr int kAxes = 1;
     static constexpr bool kReduce = false;
     const T* r;
@@ -276,9 +300,9 @@ struct Op1a : OpBase<T> {
         const size_t i = this->at(line, pos);
         f[0] = fma(beta, g_lag(w[i], g2, g1), r[i]);
     }
-    __device__ __forceinline__ void store(int line, int pos, const T (&h)[1], RedAcc<T>&) const {
-        const size_t i = this->at(line, pos);
-        e_out[i] = h[0] - beta * g_lag(w[i], g2, g1);
+    __device__ __forceinline__ void fetch(int line, int pos, T (&a)[NA]) const { a[0] = w[this->at(line, pos)]; }
+    __device__ __forceinline__ void put(int line, int pos, const T (&h)[1], const T (&a)[NA], RedAcc<T>&) const {
+        e_out[this->at(line, pos)] = h[0] - beta * g_lag(a[0], g2, g1);
     }
 };
 
@@ -286,17 +310,17 @@ struct Op1a : OpBase<T> {
 template <typename T>
 struct Op1b : OpBase<T> {
     static constexpr int NF = 1;
+    static constexpr int NA = 1;
     static constexpr int kAxes = 1;
     static constexpr bool kReduce = true;
     const T* e_in;
     T* w;
     T shift;
     __device__ __forceinline__ void load(int line, int pos, T (&f)[1]) const { f[0] = e_in[this->at(line, pos)]; }
-    __device__ __forceinline__ void store(int line, int pos, const T (&h)[1], RedAcc<T>& r) const {
-        const size_t i = this->at(line, pos);
-        const T old = w[i];
-        w[i] = h[0];
-        r.dmax = fmax(r.dmax, fabs(h[0] - old));
+    __device__ __forceinline__ void fetch(int line, int pos, T (&a)[NA]) const { a[0] = w[this->at(line, pos)]; }
+    __device__ __forceinline__ void put(int line, int pos, const T (&h)[1], const T (&a)[NA], RedAcc<T>& r) const {
+        w[this->at(line, pos)] = h[0];
+        r.dmax = fmax(r.dmax, fabs(h[0] - a[0]));
         r.vmax = fmax(r.vmax, fabs(h[0]));
     }
 };
@@ -335,5 +359,118 @@ __device__ __forceinline__ void block_reduce_store(RedAcc<T> r, unsigned long lo
         }
     }
 }
+
+}  // namespace molt
+
+namespace molt {
+
+// ---------------------------------------------------------------------------------------
+// Pointwise forms of the row passes for the pipelined FP32 row kernel: NS fields are staged
+// (double-buffered in shared memory), NA auxiliary fields are prefetched for the epilogue,
+// NO outputs are written.  prologue(): staged values -> fields to sweep; epilogue(): swept
+// values + staged + auxiliary -> outputs.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct PipeCopy {
+    static constexpr int NS = 1, NA = 0, NF = 1, NO = 1;
+    static constexpr bool kReduce = false;
+    const T* s[NS];
+    const T* a[1];
+    T* o[NO];
+    T g2, g1, beta;
+    __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const { f[0] = sv[0]; }
+    __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&)[NS], const T (&)[1], T (&ov)[NO],
+                                             RedAcc<T>&) const { ov[0] = h[0]; }
+};
+
+// pass 2 (x, inner c): staged w, T, S; outputs P, U (see OpP2)
+template <typename T>
+struct PipeP2 {
+    static constexpr int NS = 3, NA = 0, NF = 2, NO = 2;
+    static constexpr bool kReduce = false;
+    const T* s[NS];
+    const T* a[1];
+    T* o[NO];
+    T g2, g1, beta;
+    __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const {
+        f[0] = T(2) * sv[1] - g_lag(sv[0], g2, g1);
+        f[1] = sv[0] - sv[2];
+    }
+    __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&sv)[NS], const T (&)[1], T (&ov)[NO],
+                                             RedAcc<T>&) const {
+        const T u = sv[2] + h[1];
+        ov[0] = fma(beta, h[0] - sv[1], u);
+        ov[1] = u;
+    }
+};
+
+// pass 4 (x, outer c): staged Q1, U; auxiliary w, Y, Q2; output w_new (over w)
+template <typename T>
+struct PipeP4 {
+    static constexpr int NS = 2, NA = 3, NF = 1, NO = 1;
+    static constexpr bool kReduce = true;
+    const T* s[NS];
+    const T* a[NA];
+    T* o[NO];
+    T g2, g1, beta;
+    __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const { f[0] = sv[0] - sv[1]; }
+    __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&)[NS], const T (&av)[NA], T (&ov)[NO],
+                                             RedAcc<T>& r) const {
+        const T nw = (av[1] + av[0] - av[2]) + h[0];
+        ov[0] = nw;
+        r.dmax = fmax(r.dmax, fabs(nw - av[0]));
+        r.vmax = fmax(r.vmax, fabs(nw));
+    }
+};
+
+// 1D pass a: staged r, w; output E = H_i[r + beta G(w)] - beta G(w)
+template <typename T>
+struct Pipe1a {
+    static constexpr int NS = 2, NA = 0, NF = 1, NO = 1;
+    static constexpr bool kReduce = false;
+    const T* s[NS];
+    const T* a[1];
+    T* o[NO];
+    T g2, g1, beta;
+    __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const {
+        f[0] = fma(beta, g_lag(sv[1], g2, g1), sv[0]);
+    }
+    __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&sv)[NS], const T (&)[1], T (&ov)[NO],
+                                             RedAcc<T>&) const {
+        ov[0] = h[0] - beta * g_lag(sv[1], g2, g1);
+    }
+};
+
+// 1D pass b: staged E; auxiliary w; output w_new = H_o E (over w)
+template <typename T>
+struct Pipe1b {
+    static constexpr int NS = 1, NA = 1, NF = 1, NO = 1;
+    static constexpr bool kReduce = true;
+    const T* s[NS];
+    const T* a[NA];
+    T* o[NO];
+    T g2, g1, beta;
+    __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const { f[0] = sv[0]; }
+    __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&)[NS], const T (&av)[NA], T (&ov)[NO],
+                                             RedAcc<T>& r) const {
+        ov[0] = h[0];
+        r.dmax = fmax(r.dmax, fabs(h[0] - av[0]));
+        r.vmax = fmax(r.vmax, fabs(h[0]));
+    }
+};
+
+// Ampere-style asynchronous 16-byte global -> shared copies (LDGSTS), grouped and awaited.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// 16-byte chunk swizzle inside each 128-byte group of 8 chunks: chunk c lives at
+// c ^ ((c >> 3) & 7).  With 4 (or 2) chunks per thread the 8 lanes of each 128-bit
+// shared access phase hit 8 distinct bank groups.
+__device__ __forceinline__ int swz(int c) { return c ^ ((c >> 3) & 7); }
 
 }  // namespace molt

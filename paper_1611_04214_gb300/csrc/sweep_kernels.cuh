@@ -32,16 +32,27 @@ rows_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, i
     const int t = tid & (TL - 1);
     const int line0 = blockIdx.x * lpb;
 
-    // ---- stage the block's lines (prologue) ----
+    // ---- stage the block's lines (prologue): batches of U independent loads per thread ----
+    constexpr int U = 8;
     for (int l = 0; l < lpb; ++l) {
         const int gl = line0 + l;
         if (gl >= nlines) break;
         T* dst = sm + static_cast<size_t>(l) * NF * pitch;
-        for (int p = tid; p < n; p += blockDim.x) {
-            T f[NF];
-            op.load(gl, p, f);
+        for (int base = 0; base < n; base += U * blockDim.x) {
+            T f[U][NF];
 #pragma unroll
-            for (int q = 0; q < NF; ++q) dst[q * pitch + p + (p >> 5)] = f[q];
+            for (int u = 0; u < U; ++u) {
+                const int p = base + u * blockDim.x + tid;
+                if (p < n) op.load(gl, p, f[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int p = base + u * blockDim.x + tid;
+                if (p < n) {
+#pragma unroll
+                    for (int q = 0; q < NF; ++q) dst[q * pitch + p + (p >> 5)] = f[u][q];
+                }
+            }
         }
     }
     __syncthreads();
@@ -263,13 +274,311 @@ rows_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, i
         const int gl = line0 + l;
         if (gl >= nlines) break;
         const T* src = sm + static_cast<size_t>(l) * NF * pitch;
-        for (int p = tid; p < n; p += blockDim.x) {
-            T h[NF];
+        for (int base = 0; base < n; base += U * blockDim.x) {
+            T aux[U][Op::NA];
 #pragma unroll
-            for (int q = 0; q < NF; ++q) h[q] = src[q * pitch + p + (p >> 5)];
-            op.store(gl, p, h, red);
+            for (int u = 0; u < U; ++u) {
+                const int p = base + u * blockDim.x + tid;
+                if (p < n) op.fetch(gl, p, aux[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int p = base + u * blockDim.x + tid;
+                if (p < n) {
+                    T h[NF];
+#pragma unroll
+                    for (int q = 0; q < NF; ++q) h[q] = src[q * pitch + p + (p >> 5)];
+                    op.put(gl, p, h, aux[u], red);
+                }
+            }
         }
     }
+    if (Op::kReduce) block_reduce_store<T>(red, red_slots);
+}
+
+// =========================================================================================
+// Rows, FP32, persistent and pipelined.  A block owns one line per iteration with K = 16
+// positions per thread (TL = n / 16 threads) and loops over lines blockIdx.x, +gridDim.x, ...
+// The staged input fields of the next line arrive by cp.async (16-byte chunks, swizzled) into
+// the other half of a double buffer while the current line is swept; the epilogue's auxiliary
+// fields of the current line are fetched the same way during the sweep.  Window reads and the
+// epilogue work on 128-bit chunks; outputs are stored from registers.
+// Requires n % 512 == 0, 1024 <= n <= 8192, 16-byte aligned rows.
+// =========================================================================================
+__device__ __forceinline__ float comp4(const float4& v, int e) {
+    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void set4(float4& v, int e, float x) {
+    if (e == 0) v.x = x;
+    else if (e == 1) v.y = x;
+    else if (e == 2) v.z = x;
+    else v.w = x;
+}
+
+template <int M, class Op>
+__global__ void __launch_bounds__(512, 1)
+rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const Op op, int nlines, long long ld,
+                 unsigned long long* red_slots) {
+    using T = float;
+    constexpr int K = 16, V = 4, KC = K / V, H = M / 2, WC = KC + 2;
+    constexpr int NS = Op::NS, NA = Op::NA, NF = Op::NF, NO = Op::NO;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float4* sm = reinterpret_cast<float4*>(smraw);
+    __shared__ T s_scan[16][2 + 2 * NF];   // per-warp segments: D_f, D_b, A_f[NF], A_b[NF]
+    __shared__ T s_bnd[2 * NF];            // carries / B values of the line (FP64 solve)
+
+    const int n = lp.n;
+    const int nch = n / V;
+    const int TL = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wpl = TL >> 5;
+    const bool periodic = lp.bc == BC_PERIODIC;
+    const T d = lp.d;
+    const int start = tid * K;
+    T D = T(1);
+#pragma unroll
+    for (int k = 0; k < K; ++k) D *= d;
+    const T pl = dev_exp(-lp.nu * T(periodic ? start : start - 1));
+    const T pr = dev_exp(-lp.nu * T(periodic ? n - start - K : n - start - K - 1));
+
+    auto stage_buf = [&](int sb, int f) { return sm + (static_cast<size_t>(sb) * NS + f) * nch; };
+    auto aux_buf = [&](int f) { return sm + (static_cast<size_t>(2 * NS) + f) * nch; };
+    auto issue_staged = [&](int ln, int sb) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) {
+            const float4* src = reinterpret_cast<const float4*>(op.s[f] + ln * ld);
+            float4* dst = stage_buf(sb, f);
+            for (int c = tid; c < nch; c += TL) cp_async16(dst + swz(c), src + c);
+        }
+    };
+
+    RedAcc<T> red{T(0), T(0)};
+    int line = blockIdx.x;
+    if (line < nlines) issue_staged(line, 0);
+    cp_async_commit();
+    for (int it = 0; line < nlines; ++it, line += gridDim.x) {
+        const int sb = it & 1;
+        cp_async_wait<0>();          // this line's staged fields (the only group in flight)
+        __syncthreads();             // ... visible to all; every warp is done with the last line
+        // auxiliary fields of this line, then the staged fields of the next line
+#pragma unroll
+        for (int f = 0; f < NA; ++f) {
+            const float4* src = reinterpret_cast<const float4*>(op.a[f] + line * ld);
+            float4* dst = aux_buf(f);
+            for (int c = tid; c < nch; c += TL) cp_async16(dst + swz(c), src + c);
+        }
+        cp_async_commit();
+        const int next = line + gridDim.x;
+        if (next < nlines) issue_staged(next, sb ^ 1);
+        cp_async_commit();
+
+        // ---- window (prologue applied) from chunks start/V - 1 .. start/V + KC ----
+        T fw[NF][WC * V];
+#pragma unroll
+        for (int j = 0; j < WC; ++j) {
+            int c = start / V - 1 + j;
+            if (periodic) c = c < 0 ? c + nch : (c >= nch ? c - nch : c);
+            else c = c < 0 ? 0 : (c >= nch ? nch - 1 : c);
+            float4 raw[NS];
+#pragma unroll
+            for (int f = 0; f < NS; ++f) raw[f] = stage_buf(sb, f)[swz(c)];
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                T sv[NS], fv[NF];
+#pragma unroll
+                for (int f = 0; f < NS; ++f) sv[f] = comp4(raw[f], e);
+                op.prologue(sv, fv);
+#pragma unroll
+                for (int q = 0; q < NF; ++q) fw[q][j * V + e] = fv[q];
+            }
+        }
+        T JL[NF][K], JR[NF][K], aL[NF], aR[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            T win[K + M];
+#pragma unroll
+            for (int i = 0; i < K + M; ++i) win[i] = fw[q][V - H + i];
+            auto at = [&](int p) {
+                T sv[NS], fv[NF];
+#pragma unroll
+                for (int f = 0; f < NS; ++f) sv[f] = reinterpret_cast<const T*>(stage_buf(sb, f) + swz(p / V))[p % V];
+                op.prologue(sv, fv);
+                return fv[q];
+            };
+            local_integrals<T, M, K>(lp, start, K, win, at, JL[q], JR[q]);
+            chunk_aggregates<T, K>(d, K, JL[q], JR[q], aL[q], aR[q]);
+        }
+
+        // ---- scan of the chunk segments: shuffles inside each warp ----
+        T Df = D, Db = D, Af[NF], Ab[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            Af[q] = aL[q];
+            Ab[q] = aR[q];
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T dpf = __shfl_up_sync(kFull, Df, o);
+            const T dpb = __shfl_down_sync(kFull, Db, o);
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                const T apf = __shfl_up_sync(kFull, Af[q], o);
+                const T apb = __shfl_down_sync(kFull, Ab[q], o);
+                if (lane >= o) Af[q] = fma(apf, Df, Af[q]);
+                if (lane + o < 32) Ab[q] = fma(apb, Db, Ab[q]);
+            }
+            if (lane >= o) Df = dpf * Df;
+            if (lane + o < 32) Db = dpb * Db;
+        }
+        T Dxf = __shfl_up_sync(kFull, Df, 1), Dxb = __shfl_down_sync(kFull, Db, 1);
+        T Axf[NF], Axb[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            Axf[q] = __shfl_up_sync(kFull, Af[q], 1);
+            Axb[q] = __shfl_down_sync(kFull, Ab[q], 1);
+            if (lane == 0) Axf[q] = T(0);
+            if (lane == 31) Axb[q] = T(0);
+        }
+        if (lane == 0) Dxf = T(1);
+        if (lane == 31) Dxb = T(1);
+        if (lane == 31) {
+            s_scan[warp][0] = Df;
+#pragma unroll
+            for (int q = 0; q < NF; ++q) s_scan[warp][2 + q] = Af[q];
+        }
+        if (lane == 0) {
+            s_scan[warp][1] = Db;
+#pragma unroll
+            for (int q = 0; q < NF; ++q) s_scan[warp][2 + NF + q] = Ab[q];
+        }
+        __syncthreads();
+        // ---- warp 0 scans the warp segments (log depth) and solves the boundary system ----
+        if (warp == 0) {
+            const bool has = lane < wpl;
+            T fD = has ? s_scan[lane][0] : T(1);
+            T bD = has ? s_scan[lane][1] : T(1);
+            T fA[NF], bA[NF];
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                fA[q] = has ? s_scan[lane][2 + q] : T(0);
+                bA[q] = has ? s_scan[lane][2 + NF + q] : T(0);
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const T pfD = __shfl_up_sync(kFull, fD, o);
+                const T pbD = __shfl_down_sync(kFull, bD, o);
+#pragma unroll
+                for (int q = 0; q < NF; ++q) {
+                    const T pf = __shfl_up_sync(kFull, fA[q], o);
+                    const T pb = __shfl_down_sync(kFull, bA[q], o);
+                    if (lane >= o) fA[q] = fma(pf, fD, fA[q]);
+                    if (lane + o < 32) bA[q] = fma(pb, bD, bA[q]);
+                }
+                if (lane >= o) fD = pfD * fD;
+                if (lane + o < 32) bD = pbD * bD;
+            }
+            T exF[NF], exB[NF], totF[NF], totB[NF];
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                exF[q] = __shfl_up_sync(kFull, fA[q], 1);
+                exB[q] = __shfl_down_sync(kFull, bA[q], 1);
+                totF[q] = __shfl_sync(kFull, fA[q], 31);
+                totB[q] = __shfl_sync(kFull, bA[q], 0);
+                if (lane == 0) exF[q] = T(0);
+                if (lane + 1 >= wpl) exB[q] = T(0);
+            }
+            __syncwarp();
+            if (has) {
+#pragma unroll
+                for (int q = 0; q < NF; ++q) {
+                    s_scan[lane][2 + q] = exF[q];
+                    s_scan[lane][2 + NF + q] = exB[q];
+                }
+            }
+            if (lane == 0) {
+                // one FP64 2x2 boundary solve per line (Eq. homogeneous and analogues)
+#pragma unroll
+                for (int q = 0; q < NF; ++q) {
+                    const double I0 = static_cast<double>(totB[q]);
+                    const double IN = static_cast<double>(totF[q]);
+                    double a, b;
+                    if (periodic) {
+                        a = IN * lp.inv1mmu;
+                        b = I0 * lp.inv1mmu;
+                    } else {
+                        a = lp.bAA * I0 + lp.bAB * IN;
+                        b = lp.bBA * I0 + lp.bBB * IN;
+                    }
+                    s_bnd[q] = static_cast<T>(a);
+                    s_bnd[NF + q] = static_cast<T>(b);
+                }
+            }
+        }
+        __syncthreads();
+        T pF[NF], pB[NF], xl[NF], xr[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            pF[q] = s_scan[warp][2 + q];
+            pB[q] = s_scan[warp][2 + NF + q];
+            xl[q] = s_bnd[q];
+            xr[q] = s_bnd[NF + q];
+        }
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            const T ax = fma(pF[q], Dxf, Axf[q]);
+            const T bx = fma(pB[q], Dxb, Axb[q]);
+            T cl, cr;
+            if (periodic) {
+                cl = fma(pl, xl[q], ax);
+                cr = fma(pr, xr[q], bx);
+            } else {
+                if (start == 0) {
+                    JL[q][0] += xl[q];                    // P^L_0 = B_a
+                    cl = T(0);
+                } else {
+                    cl = fma(pl, xl[q], ax);
+                }
+                if (start + K == n) {
+                    JR[q][K - 1] += xr[q];                // P^R_N = B_b
+                    cr = T(0);
+                } else {
+                    cr = fma(pr, xr[q], bx);
+                }
+            }
+            chunk_finish<T, K>(d, K, cl, cr, JL[q], JR[q]);
+        }
+
+        // ---- epilogue on this thread's own chunks ----
+        if constexpr (NA > 0) {
+            cp_async_wait<1>();      // this line's auxiliary group is complete
+            __syncthreads();
+        }
+#pragma unroll
+        for (int kc = 0; kc < KC; ++kc) {
+            const int c = start / V + kc;
+            float4 sraw[NS], araw[NA > 0 ? NA : 1], outv[NO];
+#pragma unroll
+            for (int f = 0; f < NS; ++f) sraw[f] = stage_buf(sb, f)[swz(c)];
+#pragma unroll
+            for (int f = 0; f < NA; ++f) araw[f] = aux_buf(f)[swz(c)];
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                T h[NF], sv[NS], av[NA > 0 ? NA : 1], ov[NO];
+#pragma unroll
+                for (int q = 0; q < NF; ++q) h[q] = JR[q][kc * V + e];
+#pragma unroll
+                for (int f = 0; f < NS; ++f) sv[f] = comp4(sraw[f], e);
+#pragma unroll
+                for (int f = 0; f < NA; ++f) av[f] = comp4(araw[f], e);
+                if constexpr (NA == 0) av[0] = T(0);
+                op.epilogue(h, sv, av, ov, red);
+#pragma unroll
+                for (int o = 0; o < NO; ++o) set4(outv[o], e, ov[o]);
+            }
+#pragma unroll
+            for (int o = 0; o < NO; ++o) reinterpret_cast<float4*>(op.o[o] + line * ld)[c] = outv[o];
+        }
+    }
+    cp_async_wait<0>();
     if (Op::kReduce) block_reduce_store<T>(red, red_slots);
 }
 
@@ -356,7 +665,8 @@ cols_agg_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nline
 // Decays are products of two constants (full tile, last tile), never per-tile exponentials.
 template <typename T>
 __global__ void cols_carry_kernel(const __grid_constant__ LineParams<T> lp, int nlines, int nf, int tiles,
-                                  int R, const T* aggL, const T* aggR, T* carL, T* carR) {
+                                  int R, const T* __restrict__ aggL, const T* __restrict__ aggR,
+                                  T* __restrict__ carL, T* __restrict__ carR) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nlines * nf) return;
     const int q = idx / nlines, line = idx % nlines;
@@ -369,9 +679,11 @@ __global__ void cols_carry_kernel(const __grid_constant__ LineParams<T> lp, int 
     const size_t b0 = static_cast<size_t>(q) * tiles * nlines + line;
     auto dec = [&](int t) { return t == tiles - 1 ? Dlast : Dfull; };
     double E = 0.0;
+#pragma unroll 8
     for (int t = 0; t < tiles; ++t) E = E * dec(t) + static_cast<double>(aggL[b0 + static_cast<size_t>(t) * nlines]);
     const double IN = E;
     E = 0.0;
+#pragma unroll 8
     for (int t = tiles - 1; t >= 0; --t) E = E * dec(t) + static_cast<double>(aggR[b0 + static_cast<size_t>(t) * nlines]);
     const double I0 = E;
     const bool periodic = lp.bc == BC_PERIODIC;
@@ -386,6 +698,7 @@ __global__ void cols_carry_kernel(const __grid_constant__ LineParams<T> lp, int 
     // forward: carry entering tile t = E_t + d^{s_t} XL (periodic) or E_t + d^{s_t - 1} B_a
     E = 0.0;
     double pw = 1.0;                        // d^{s_t}
+#pragma unroll 8
     for (int t = 0; t < tiles; ++t) {
         double c;
         if (periodic) c = E + pw * XL;
@@ -398,6 +711,7 @@ __global__ void cols_carry_kernel(const __grid_constant__ LineParams<T> lp, int 
     // E_t + d^{n-2-e_t} B_b, with e_t the tile's last position
     E = 0.0;
     double qw = 1.0;                        // d^{n-1-e_t}
+#pragma unroll 8
     for (int t = tiles - 1; t >= 0; --t) {
         double c;
         if (periodic) c = E + qw * XR;
@@ -473,13 +787,17 @@ cols_final_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nli
         chunk_finish<T, KY>(lp.d, cnt, cl, cr, JL[q], JR[q]);
     }
     RedAcc<T> red{T(0), T(0)};
+    T aux[KY][Op::NA];
+#pragma unroll
+    for (int k = 0; k < KY; ++k)
+        if (k < cnt) op.fetch(line, start + k, aux[k]);
 #pragma unroll
     for (int k = 0; k < KY; ++k) {
         if (k < cnt) {
             T h[NF];
 #pragma unroll
             for (int q = 0; q < NF; ++q) h[q] = JR[q][k];
-            op.store(line, start + k, h, red);
+            op.put(line, start + k, h, aux[k], red);
         }
     }
     if (Op::kReduce) block_reduce_store<T>(red, red_slots);

@@ -209,14 +209,16 @@ class Solver:
         _check(st, self._h)
         return out
 
-    def run_host(self, u_host, dt: float, scheme: str, nsteps: int, stream=None) -> StepInfo:
+    def run_host(self, u_host, dt: float, scheme: str, nsteps: int, stream=None,
+                 raise_on_nonconvergence: bool = True) -> StepInfo:
         """End-to-end call on a host (CPU) tensor: copy in, nsteps steps, copy back."""
         if u_host.is_cuda or u_host.dtype != self.dtype or not u_host.is_contiguous():
             raise ValueError("expected a contiguous host tensor of the solver's dtype")
         info = _StepInfo()
         st = self._lib.molt_run_host(self._h, ctypes.c_void_p(u_host.data_ptr()), float(dt), SCHEME[scheme],
                                      int(nsteps), _stream_handle(stream), ctypes.byref(info))
-        _check(st, self._h)
+        if not (st == MOLT_ERR_NOT_CONVERGED and not raise_on_nonconvergence):
+            _check(st, self._h)
         return StepInfo(info.status, info.stages, list(info.iters)[: max(info.stages, 0)], info.total_iters,
                         info.residual, info.tol_used)
 
