@@ -203,6 +203,79 @@ cudaError_t rows_pipe(const LineParams<float>& lp, const P& op, int nlines, unsi
     return cudaGetLastError();
 }
 
+// ---- pipelined FP32 columns ----
+template <class Op> struct ColPipeOf { using type = void; };
+template <> struct ColPipeOf<OpCopy<float>> { using type = PipeCopy<float>; };
+template <> struct ColPipeOf<OpP1<float>> { using type = PipeP1<float>; };
+template <> struct ColPipeOf<OpP3<float>> { using type = PipeP3<float>; };
+
+template <class P>
+P col_pipe_build(int kind, const OpArgs<float>& a) {
+    P p{};
+    p.g2 = a.g2;
+    p.g1 = a.g1;
+    p.beta = a.beta;
+    switch (kind) {
+        case OP_COPY: p.s[0] = a.in0; p.o[0] = a.out0; break;
+        case OP_P1: p.s[0] = a.in0; p.o[0] = a.out0; p.o[1] = a.out1; break;
+        case OP_P3: p.s[0] = a.in0; p.s[1] = a.in1; p.o[0] = a.out0; p.o[1] = a.out1; break;
+    }
+    return p;
+}
+
+template <class P>
+bool col_pipe_eligible(const P& p, int n, int nlines) {
+    if (nlines % 32 != 0 || n < 256) return false;
+    for (int f = 0; f < P::NS; ++f) if (!aligned16(p.s[f])) return false;
+    return true;
+}
+
+template <int M, class P, bool kFinal>
+cudaError_t cols_pipe_launch(const LineParams<float>& lp, const P& op, int nlines, int tiles, ColScratch<float>* cs,
+                             unsigned long long* red, cudaStream_t st) {
+    constexpr int ROWS = kColR + 2 * (kMaxM / 2);
+    const size_t smem = static_cast<size_t>(2) * P::NS * ROWS * 32 * sizeof(float);
+    auto kern = cols_pipe_kernel<M, P, kFinal>;
+    static int limit = smem_optin(kern);
+    if (limit < 0 || smem > static_cast<size_t>(limit)) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kColWY, smem);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int items = (nlines / 32) * tiles;
+    int grid = sms * per_sm;
+    if (grid > items) grid = items;
+    kern<<<grid, 32 * kColWY, smem, st>>>(lp, op, nlines, static_cast<long long>(nlines), tiles, cs->aggL, cs->aggR,
+                                          cs->carL, cs->carR, red);
+    return cudaGetLastError();
+}
+
+template <int M, class P>
+cudaError_t cols_pipe(const LineParams<float>& lp, const P& op, int nlines, ColScratch<float>* cs,
+                      unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof, int kind) {
+    const int n = lp.n;
+    const int tiles = (n + kColR - 1) / kColR;
+    if (cs == nullptr || cs->capacity_lines < nlines || cs->capacity_fields < P::NF || cs->tiles < tiles)
+        return cudaErrorInvalidValue;
+    prof_begin(prof, 8 + kind, st);
+    cudaError_t e = cols_pipe_launch<M, P, false>(lp, op, nlines, tiles, cs, red, st);
+    prof_end(prof, st);
+    if (e != cudaSuccess) return e;
+    const int total = nlines * P::NF;
+    prof_begin(prof, 16, st);
+    cols_carry_kernel<float><<<(total + 127) / 128, 128, 0, st>>>(lp, nlines, P::NF, tiles, kColR, cs->aggL, cs->aggR,
+                                                                 cs->carL, cs->carR);
+    prof_end(prof, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    prof_begin(prof, 17 + kind, st);
+    e = cols_pipe_launch<M, P, true>(lp, op, nlines, tiles, cs, red, st);
+    prof_end(prof, st);
+    if (launches) *launches += 2;
+    return e;
+}
+
 template <typename T, class Op>
 cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int nx, int ny, ColScratch<T>* cs,
                      unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof, int kind) {
@@ -230,6 +303,17 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
             }
         }
     } else {
+        if constexpr (std::is_same<T, float>::value && !std::is_same<typename ColPipeOf<Op>::type, void>::value) {
+            using P = typename ColPipeOf<Op>::type;
+            const P pop = col_pipe_build<P>(kind, a);
+            if (col_pipe_eligible(pop, lp.n, nlines)) {
+                switch (lp.M) {
+                    case 2: return cols_pipe<2>(lp, pop, nlines, cs, red, st, launches, prof, kind);
+                    case 4: return cols_pipe<4>(lp, pop, nlines, cs, red, st, launches, prof, kind);
+                    case 6: return cols_pipe<6>(lp, pop, nlines, cs, red, st, launches, prof, kind);
+                }
+            }
+        }
         if constexpr ((Op::kAxes & 2) != 0) {
             switch (lp.M) {
                 case 2: return cols<T, 2>(lp, op, nlines, cs, red, st, launches, prof, kind);

@@ -474,3 +474,48 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 __device__ __forceinline__ int swz(int c) { return c ^ ((c >> 3) & 7); }
 
 }  // namespace molt
+
+namespace molt {
+
+// Column passes in pointwise form (pipelined FP32 column kernels).
+// pass 1 (y, inner c): staged w; sweep G(w), w; outputs T = H G, S = H w
+template <typename T>
+struct PipeP1 {
+    static constexpr int NS = 1, NA = 0, NF = 2, NO = 2;
+    static constexpr bool kReduce = false;
+    const T* s[NS];
+    const T* a[1];
+    T* o[NO];
+    T g2, g1, beta;
+    __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const {
+        f[0] = g_lag(sv[0], g2, g1);
+        f[1] = sv[0];
+    }
+    __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&)[NS], const T (&)[1], T (&ov)[NO],
+                                             RedAcc<T>&) const {
+        ov[0] = h[0];
+        ov[1] = h[1];
+    }
+};
+
+// pass 3 (y, outer c): staged P, U; outputs Q1 = H P, Q2 = H U
+template <typename T>
+struct PipeP3 {
+    static constexpr int NS = 2, NA = 0, NF = 2, NO = 2;
+    static constexpr bool kReduce = false;
+    const T* s[NS];
+    const T* a[1];
+    T* o[NO];
+    T g2, g1, beta;
+    __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const {
+        f[0] = sv[0];
+        f[1] = sv[1];
+    }
+    __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&)[NS], const T (&)[1], T (&ov)[NO],
+                                             RedAcc<T>&) const {
+        ov[0] = h[0];
+        ov[1] = h[1];
+    }
+};
+
+}  // namespace molt

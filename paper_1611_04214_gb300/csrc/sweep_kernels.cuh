@@ -583,6 +583,278 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const Op op, int 
 }
 
 // =========================================================================================
+// Columns, FP32, persistent and pipelined.  A work item is one tile of R = 128 rows of a strip
+// of 32 columns (each staged row is one 128-byte segment per field); items are visited
+// strip-fastest so that concurrent blocks read adjacent segments of the same rows.  The rows
+// [r0 - 3, r0 + R + 3) of the next item's staged fields arrive by cp.async while the current
+// item is processed.  kFinal = false: tile aggregates (phase A); kFinal = true: the tile's
+// results from the carries of the scan kernel (phase C).
+// Phase A uses that a tile aggregate of J = (stencil applied to f) is the stencil weights
+// applied to M+1 shifted recurrences of f: with window w[i] = f at start - M/2 + i,
+//   sum_k d^{K-1-k} J^L_k = sum_o wl_o S_o,  S_0 = sum_k d^{K-1-k} w[k],
+//                                            S_{o+1} = d S_o - d^K w[o] + w[K+o];
+//   sum_k d^k J^R_k      = sum_o wr_o R_o,  R_M = sum_k d^k w[k+M],
+//                                            R_o = w[o] + d (R_{o+1} - d^{K-1} w[K+o]).
+// Requires nlines % 32 == 0, n >= 256, 16-byte aligned rows.
+// =========================================================================================
+template <int M, class Op, bool kFinal>
+__global__ void __launch_bounds__(256, 2)
+cols_pipe_kernel(const __grid_constant__ LineParams<float> lp, const Op op, int nlines, long long ld, int tiles,
+                 float* __restrict__ aggL, float* __restrict__ aggR, const float* __restrict__ carL,
+                 const float* __restrict__ carR, unsigned long long* red_slots) {
+    using T = float;
+    constexpr int KY = 16, WY = 8, R = KY * WY, HR = kMaxM / 2, ROWS = R + 2 * HR, H = M / 2;
+    constexpr int NS = Op::NS, NF = Op::NF, NO = Op::NO;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float* sm = reinterpret_cast<float*>(smraw);   // [2][NS][ROWS][32]
+    __shared__ T sD[WY][32];
+    __shared__ T sL[NF][WY][32];
+    __shared__ T sR[NF][WY][32];
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int n = lp.n, N = lp.N, jb = lp.N - H + 1;
+    const bool periodic = lp.bc == BC_PERIODIC;
+    const T d = lp.d;
+    const int nstrips = nlines >> 5;
+    const int items = nstrips * tiles;
+    T DK = T(1);
+#pragma unroll
+    for (int k = 0; k < KY - 1; ++k) DK *= d;
+    const T DK1 = DK;          // d^{KY-1}
+    DK *= d;                   // d^{KY}
+
+    auto buf = [&](int sb, int f) { return sm + (static_cast<size_t>(sb) * NS + f) * ROWS * 32; };
+    auto issue = [&](int itm, int sb) {
+        const int strip = itm % nstrips, tile = itm / nstrips;
+        const int r0 = tile * R - HR;
+#pragma unroll
+        for (int f = 0; f < NS; ++f) {
+            const T* base = op.s[f] + strip * 32;
+            float* dst = buf(sb, f);
+            for (int idx = threadIdx.x; idx < ROWS * 8; idx += blockDim.x) {
+                const int rr = idx >> 3, ch = idx & 7;
+                const int row = fold_pos(r0 + rr, n, periodic);
+                cp_async16(dst + rr * 32 + ch * 4, base + row * ld + ch * 4);
+            }
+        }
+    };
+
+    RedAcc<T> red{T(0), T(0)};
+    int item = blockIdx.x;
+    if (item < items) issue(item, 0);
+    cp_async_commit();
+    for (int it = 0; item < items; ++it, item += gridDim.x) {
+        const int sb = it & 1;
+        cp_async_wait<0>();
+        __syncthreads();
+        const int nxt = item + gridDim.x;
+        if (nxt < items) issue(nxt, sb ^ 1);
+        cp_async_commit();
+
+        const int strip = item % nstrips, tile = item / nstrips;
+        const int line = strip * 32 + lane;
+        const int r0 = tile * R - HR;
+        const int start = tile * R + wy * KY;
+        int cnt = n - start;
+        cnt = cnt < 0 ? 0 : (cnt > KY ? KY : cnt);
+        // window of swept values: win[q][i] at position start - H + i
+        T win[NF][KY + M];
+#pragma unroll
+        for (int i = 0; i < KY + M; ++i) {
+            const int rr = wy * KY + HR - H + i;
+            T sv[NS], fv[NF];
+#pragma unroll
+            for (int f = 0; f < NS; ++f) sv[f] = buf(sb, f)[rr * 32 + lane];
+            op.prologue(sv, fv);
+#pragma unroll
+            for (int q = 0; q < NF; ++q) win[q][i] = fv[q];
+        }
+        T D = T(1);
+#pragma unroll
+        for (int k = 0; k < KY; ++k)
+            if (k < cnt) D *= d;
+        const bool interior = (cnt == KY) && (periodic || (start >= H && start + KY - 1 <= N - H));
+        // wall values injected at the end nodes in phase C (from the scan kernel), 0 otherwise
+        T injL[NF], injR[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            injL[q] = injR[q] = T(0);
+            if (kFinal && !periodic) {
+                const size_t o = (static_cast<size_t>(q) * tiles + tile) * nlines + line;
+                if (tile == 0) injL[q] = carL[o];
+                if (tile == tiles - 1) injR[q] = carR[o];
+            }
+        }
+        auto at = [&](int p, int q) {
+            const int rr = p - r0;
+            T sv[NS], fv[NF];
+            if (rr >= 0 && rr < ROWS) {
+#pragma unroll
+                for (int f = 0; f < NS; ++f) sv[f] = buf(sb, f)[rr * 32 + lane];
+            } else {
+#pragma unroll
+                for (int f = 0; f < NS; ++f) sv[f] = op.s[f][static_cast<long long>(p) * ld + line];
+            }
+            op.prologue(sv, fv);
+            return fv[q];
+        };
+        // J^L / J^R at chunk position k (j = start + k), wall stencils and injections included
+        auto jl = [&](int q, int k) {
+            const int j = start + k;
+            T a = T(0);
+            if (!periodic && j < H) {
+                if (j == 0) return injL[q];
+                for (int o = 0; o <= M; ++o) a = fma(lp.wlA[j - 1][o], at(o, q), a);
+            } else if (!periodic && j >= jb) {
+                for (int o = 0; o <= M; ++o) a = fma(lp.wlB[j - jb][o], at(N - M + o, q), a);
+            } else {
+#pragma unroll
+                for (int o = 0; o <= M; ++o) a = fma(lp.wl[o], win[q][k + o], a);
+            }
+            return a;
+        };
+        auto jr = [&](int q, int k) {
+            const int j = start + k;
+            T a = T(0);
+            if (!periodic && j < H) {
+                for (int o = 0; o <= M; ++o) a = fma(lp.wrA[j][o], at(o, q), a);
+            } else if (!periodic && j >= jb) {
+                if (j == N) return injR[q];
+                for (int o = 0; o <= M; ++o) a = fma(lp.wrB[j - jb][o], at(N - M + o, q), a);
+            } else {
+#pragma unroll
+                for (int o = 0; o <= M; ++o) a = fma(lp.wr[o], win[q][k + o], a);
+            }
+            return a;
+        };
+
+        // ---- chunk aggregates ----
+        T aL[NF], aR[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            if (interior) {
+                T S = T(0);
+#pragma unroll
+                for (int k = 0; k < KY; ++k) S = fma(d, S, win[q][k]);
+                T a = lp.wl[0] * S;
+#pragma unroll
+                for (int o = 0; o < M; ++o) {
+                    S = fma(d, S, fma(-DK, win[q][o], win[q][KY + o]));
+                    a = fma(lp.wl[o + 1], S, a);
+                }
+                T Rr = T(0);
+#pragma unroll
+                for (int k = KY - 1; k >= 0; --k) Rr = fma(d, Rr, win[q][k + M]);
+                T b = lp.wr[M] * Rr;
+#pragma unroll
+                for (int o = M - 1; o >= 0; --o) {
+                    Rr = fma(d, fma(-DK1, win[q][KY + o], Rr), win[q][o]);
+                    b = fma(lp.wr[o], Rr, b);
+                }
+                aL[q] = a;
+                aR[q] = b;
+            } else {
+                T a = T(0), b = T(0);
+#pragma unroll
+                for (int k = 0; k < KY; ++k)
+                    if (k < cnt) a = fma(d, a, jl(q, k));
+#pragma unroll
+                for (int k = KY - 1; k >= 0; --k)
+                    if (k < cnt) b = fma(d, b, jr(q, k));
+                aL[q] = a;
+                aR[q] = b;
+            }
+        }
+        sD[wy][lane] = D;
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            sL[q][wy][lane] = aL[q];
+            sR[q][wy][lane] = aR[q];
+        }
+        __syncthreads();
+        if constexpr (!kFinal) {
+            if (wy == 0) {
+#pragma unroll
+                for (int q = 0; q < NF; ++q) {
+                    T a = T(0), b = T(0);
+#pragma unroll
+                    for (int i = 0; i < WY; ++i) a = fma(a, sD[i][lane], sL[q][i][lane]);
+#pragma unroll
+                    for (int i = WY - 1; i >= 0; --i) b = fma(b, sD[i][lane], sR[q][i][lane]);
+                    const size_t o = (static_cast<size_t>(q) * tiles + tile) * nlines + line;
+                    aggL[o] = a;
+                    aggR[o] = b;
+                }
+            }
+        } else {
+            T out[NF][KY];
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                const size_t o = (static_cast<size_t>(q) * tiles + tile) * nlines + line;
+                T cl = (!periodic && tile == 0) ? T(0) : carL[o];
+                T cr = (!periodic && tile == tiles - 1) ? T(0) : carR[o];
+#pragma unroll
+                for (int i = 0; i < WY; ++i)
+                    if (i < wy) cl = fma(cl, sD[i][lane], sL[q][i][lane]);
+#pragma unroll
+                for (int i = WY - 1; i >= 0; --i)
+                    if (i > wy) cr = fma(cr, sD[i][lane], sR[q][i][lane]);
+                // second pass: P^R backward, then P^L forward added (Eq. IL / IR from the carries)
+                T p = cr;
+                if (interior) {
+#pragma unroll
+                    for (int k = KY - 1; k >= 0; --k) {
+                        T a = T(0);
+#pragma unroll
+                        for (int o2 = 0; o2 <= M; ++o2) a = fma(lp.wr[o2], win[q][k + o2], a);
+                        p = fma(d, p, a);
+                        out[q][k] = p;
+                    }
+                    T s2 = cl;
+#pragma unroll
+                    for (int k = 0; k < KY; ++k) {
+                        T a = T(0);
+#pragma unroll
+                        for (int o2 = 0; o2 <= M; ++o2) a = fma(lp.wl[o2], win[q][k + o2], a);
+                        s2 = fma(d, s2, a);
+                        out[q][k] += s2;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = KY - 1; k >= 0; --k)
+                        if (k < cnt) {
+                            p = fma(d, p, jr(q, k));
+                            out[q][k] = p;
+                        }
+                    T s2 = cl;
+#pragma unroll
+                    for (int k = 0; k < KY; ++k)
+                        if (k < cnt) {
+                            s2 = fma(d, s2, jl(q, k));
+                            out[q][k] += s2;
+                        }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < KY; ++k) {
+                if (k < cnt) {
+                    const int row_local = wy * KY + HR + k;
+                    T h[NF], sv[NS], av[1] = {T(0)}, ov[NO];
+#pragma unroll
+                    for (int q = 0; q < NF; ++q) h[q] = out[q][k];
+#pragma unroll
+                    for (int f = 0; f < NS; ++f) sv[f] = buf(sb, f)[row_local * 32 + lane];
+                    op.epilogue(h, sv, av, ov, red);
+#pragma unroll
+                    for (int o = 0; o < NO; ++o) op.o[o][static_cast<long long>(start + k) * ld + line] = ov[o];
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+    if (Op::kReduce) block_reduce_store<T>(red, red_slots);
+}
+
+// =========================================================================================
 // Columns.  Block = 32 lanes (32 adjacent columns, so every access is a 128 B row segment in
 // FP32) x WY warps; a tile is R = WY * KY positions of those columns.  Phase A reduces each
 // tile to its two segments, phase B scans the tile segments down each column (FP64) and
@@ -660,9 +932,10 @@ cols_agg_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nline
     }
 }
 
-// One thread per (field, column): scan the tile segments in FP64, solve the boundary system,
-// write the carry entering each tile (or, for walls, the B value injected at the end node).
-// Decays are products of two constants (full tile, last tile), never per-tile exponentials.
+// One thread per (field, column): scan the tile segments, solve the boundary system in FP64,
+// and write the carry entering each tile (or, for walls, the B value injected at the end node).
+// The tile recurrences run in the kernel precision (FP64 throughput on this part is a small
+// fraction of FP32), with the decays as products of two constants (full tile, last tile).
 template <typename T>
 __global__ void cols_carry_kernel(const __grid_constant__ LineParams<T> lp, int nlines, int nf, int tiles,
                                   int R, const T* __restrict__ aggL, const T* __restrict__ aggR,
@@ -671,53 +944,53 @@ __global__ void cols_carry_kernel(const __grid_constant__ LineParams<T> lp, int 
     if (idx >= nlines * nf) return;
     const int q = idx / nlines, line = idx % nlines;
     const int n = lp.n;
-    const double nu = static_cast<double>(lp.nu);
+    const T nu = lp.nu;
     const int last_rows = n - (tiles - 1) * R;
-    const double Dfull = exp(-nu * R);
-    const double Dlast = exp(-nu * last_rows);
-    const double einv = exp(nu);          // d^{-1}: shifts a power by one node
+    const T Dfull = dev_exp(-nu * T(R));
+    const T Dlast = dev_exp(-nu * T(last_rows));
+    const T einv = dev_exp(nu);           // d^{-1}: shifts a power by one node
     const size_t b0 = static_cast<size_t>(q) * tiles * nlines + line;
     auto dec = [&](int t) { return t == tiles - 1 ? Dlast : Dfull; };
-    double E = 0.0;
+    T E = T(0);
 #pragma unroll 8
-    for (int t = 0; t < tiles; ++t) E = E * dec(t) + static_cast<double>(aggL[b0 + static_cast<size_t>(t) * nlines]);
-    const double IN = E;
-    E = 0.0;
+    for (int t = 0; t < tiles; ++t) E = fma(E, dec(t), aggL[b0 + static_cast<size_t>(t) * nlines]);
+    const double IN = static_cast<double>(E);
+    E = T(0);
 #pragma unroll 8
-    for (int t = tiles - 1; t >= 0; --t) E = E * dec(t) + static_cast<double>(aggR[b0 + static_cast<size_t>(t) * nlines]);
-    const double I0 = E;
+    for (int t = tiles - 1; t >= 0; --t) E = fma(E, dec(t), aggR[b0 + static_cast<size_t>(t) * nlines]);
+    const double I0 = static_cast<double>(E);
     const bool periodic = lp.bc == BC_PERIODIC;
-    double XL, XR;
+    T XL, XR;
     if (periodic) {
-        XL = IN * lp.inv1mmu;
-        XR = I0 * lp.inv1mmu;
+        XL = static_cast<T>(IN * lp.inv1mmu);
+        XR = static_cast<T>(I0 * lp.inv1mmu);
     } else {
-        XL = lp.bAA * I0 + lp.bAB * IN;   // B_a
-        XR = lp.bBA * I0 + lp.bBB * IN;   // B_b
+        XL = static_cast<T>(lp.bAA * I0 + lp.bAB * IN);   // B_a
+        XR = static_cast<T>(lp.bBA * I0 + lp.bBB * IN);   // B_b
     }
     // forward: carry entering tile t = E_t + d^{s_t} XL (periodic) or E_t + d^{s_t - 1} B_a
-    E = 0.0;
-    double pw = 1.0;                        // d^{s_t}
+    E = T(0);
+    T pw = T(1);                           // d^{s_t}
 #pragma unroll 8
     for (int t = 0; t < tiles; ++t) {
-        double c;
-        if (periodic) c = E + pw * XL;
-        else c = (t == 0) ? XL : E + pw * einv * XL;
-        carL[b0 + static_cast<size_t>(t) * nlines] = static_cast<T>(c);
-        E = E * dec(t) + static_cast<double>(aggL[b0 + static_cast<size_t>(t) * nlines]);
+        T c;
+        if (periodic) c = fma(pw, XL, E);
+        else c = (t == 0) ? XL : fma(pw * einv, XL, E);
+        carL[b0 + static_cast<size_t>(t) * nlines] = c;
+        E = fma(E, dec(t), aggL[b0 + static_cast<size_t>(t) * nlines]);
         pw *= dec(t);
     }
     // backward: carry entering tile t from the right = E_t + d^{n-1-e_t} XR (periodic) or
     // E_t + d^{n-2-e_t} B_b, with e_t the tile's last position
-    E = 0.0;
-    double qw = 1.0;                        // d^{n-1-e_t}
+    E = T(0);
+    T qw = T(1);                           // d^{n-1-e_t}
 #pragma unroll 8
     for (int t = tiles - 1; t >= 0; --t) {
-        double c;
-        if (periodic) c = E + qw * XR;
-        else c = (t == tiles - 1) ? XR : E + qw * einv * XR;
-        carR[b0 + static_cast<size_t>(t) * nlines] = static_cast<T>(c);
-        E = E * dec(t) + static_cast<double>(aggR[b0 + static_cast<size_t>(t) * nlines]);
+        T c;
+        if (periodic) c = fma(qw, XR, E);
+        else c = (t == tiles - 1) ? XR : fma(qw * einv, XR, E);
+        carR[b0 + static_cast<size_t>(t) * nlines] = c;
+        E = fma(E, dec(t), aggR[b0 + static_cast<size_t>(t) * nlines]);
         qw *= dec(t);
     }
 }

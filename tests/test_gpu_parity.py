@@ -159,6 +159,41 @@ def test_pipelined_rows_match_oracle(bc, M, nlines, nu):
 
 
 @pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+@pytest.mark.parametrize("M", [2, 4, 6])
+@pytest.mark.parametrize("n", [300, 1000])
+@pytest.mark.parametrize("nu", [0.05, 2.0])
+def test_pipelined_columns_match_oracle(bc, M, n, nu):
+    # FP32 columns of length >= 256 over a multiple of 32 lines take the pipelined column
+    # kernels; 300 leaves a ragged last tile of 44 rows, 1000 spans 8 tiles.
+    nx = 96
+    h = spacing(n, 2 * np.pi, bc == "periodic")
+    c = (h / nu) ** 2
+    f = uniform_noise((n, nx), 1.0, seed=M + n, mean=1.0)
+    with _solver(nx=nx, ny=n, bc=bc, quad_order=M, precision="fp32", eps=0.1) as s:
+        fin = _dev(f, "fp32")
+        out = torch.empty_like(fin)
+        s.helmholtz_apply(1, c, fin, out)
+        got = _host(out)
+    ref = helmholtz_inverse(f.astype(np.float32).astype(np.float64), c, h, bc, M, axis=0)
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-6
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+def test_pipelined_columns_in_2d_steps(bc):
+    # 288 x 96: the column passes of the iteration run through the pipelined column kernels.
+    from paper_1611_04214_gb300.inputs import paper_ic_2d
+    ny, nx = 288, 96
+    u0 = paper_ic_2d(nx, ny, periodic=(bc == "periodic"))
+    if bc == "dirichlet":
+        u0[0, :] = u0[-1, :] = -1
+        u0[:, 0] = u0[:, -1] = -1
+    rho = []
+    got, ref, _, _ = _run_both(nx, ny, bc, 0.18, 4, 1e-10, 3000, "bdf2", 0.01, 2, "fp32", u0, rho)
+    err, bar = np.abs(got - ref).max(), _fp32_bar(ref, bc, rho[0])
+    assert err <= bar, (err, bar, rho)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
 @pytest.mark.parametrize("scheme", ["be", "sdirk2"])
 def test_pipelined_rows_in_2d_steps(bc, scheme):
     # 2D FP32 steps on a 40 x 1024 grid run their row passes through the pipelined kernel.
