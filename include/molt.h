@@ -147,6 +147,22 @@ molt_status molt_helmholtz_apply(molt_solver* solver, int axis, double c, const 
  * factor 1/2 of Eq. IL.  No device work. */
 molt_status molt_quadrature_weights(double nu, int M, const int* offsets, int side, double* weights);
 
+/* FP32 column sweep that allocates nothing (no counterpart in the paper; a deployment aid).
+ * For callers that cannot call cudaMalloc - code under a memory manager that owns all device
+ * memory, or in a latency-critical loop where an allocation could synchronize the device.
+ * Applies H_c along y (every column) of the ny-by-nx FP32 field in_dev, writing out_dev (both
+ * caller-owned device buffers, row-major [ny][nx], distinct).  The grid convention, bc and
+ * quadrature order are those of molt_grid_create / molt_params, with Ly the column length.
+ * The scan's scratch is a 4 MiB file-scope device array, held by every GPU that loads the
+ * library until the process exits; grids need ceil(ny/128) * nx <= 262144, otherwise
+ * MOLT_ERR_ARG.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share
+ * the array: each call writes the
+ * scratch before reading it, and calls that overlap on the GPU race on it.  Errors are reported
+ * by molt_last_error(NULL). */
+molt_status molt_helmholtz_columns_noalloc(int nx, int ny, double Ly, int bc, int quad_order, double c,
+                                           const float* in_dev, float* out_dev, void* stream);
+
 /* Last error message of `solver` (or of the last failed create/ABI call when NULL). */
 const char* molt_last_error(const molt_solver* solver);
 

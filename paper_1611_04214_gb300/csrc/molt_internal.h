@@ -50,6 +50,9 @@ bool build_line_params(double c, double h, int n, int M, int bc, LineParams<doub
 template <typename T>
 LineParams<T> cast_line_params(const LineParams<double>& p);
 
+// Host: record the message molt_last_error(NULL) returns (entry points without a solver).
+void set_abi_error(const char* message);
+
 // Host: local quadrature weights of Sec. 3.2 for one stencil (factor 1/2 included).
 bool quadrature_weights(double nu, int M, const int* offsets, int side, double* w);
 

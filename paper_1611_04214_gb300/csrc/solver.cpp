@@ -494,6 +494,8 @@ molt_status set_global_error(molt_status s, const char* m) {
 
 }  // namespace
 
+void molt::set_abi_error(const char* message) { g_last_error = message ? message : ""; }
+
 extern "C" {
 
 molt_status molt_grid_create(molt_grid** grid, int dim, int nx, int ny, double Lx, double Ly, int bc) {

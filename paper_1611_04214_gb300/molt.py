@@ -24,6 +24,7 @@ EXPORTS = [
     "molt_set_params", "molt_set_bc", "molt_reset_history", "molt_step", "molt_run_host",
     "molt_energy", "molt_mass", "molt_helmholtz_apply", "molt_quadrature_weights",
     "molt_last_error", "molt_kernel_launches", "molt_profile_enable", "molt_profile_collect",
+    "molt_helmholtz_columns_noalloc",
 ]
 PROFILE_SLOTS = 32
 PASS_NAMES = ["H", "pass1", "pass2", "pass3", "pass4", "pass1d_a", "pass1d_b", ""]
@@ -80,6 +81,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_kernel_launches": ([P], ctypes.c_longlong),
         "molt_profile_enable": ([P, I], I),
         "molt_profile_collect": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)], I),
+        "molt_helmholtz_columns_noalloc": ([I, I, D, I, I, D, VP, VP, VP], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -105,6 +107,18 @@ def molt_quadrature_weights(nu: float, M: int, offsets, side: str):
     out = (ctypes.c_double * (M + 1))()
     _check(lib.molt_quadrature_weights(float(nu), int(M), offs, 0 if side == "L" else 1, out))
     return list(out)
+
+
+def molt_helmholtz_columns_noalloc(nx: int, ny: int, Ly: float, bc: str, quad_order: int, c: float, inp, out,
+                                   stream=None):
+    """The allocation-free FP32 column sweep (see include/molt.h) on contiguous CUDA float32 tensors."""
+    lib = load_library()
+    for t in (inp, out):
+        if not t.is_cuda or t.dtype.itemsize != 4 or not t.is_contiguous() or t.numel() != nx * ny:
+            raise ValueError("expected contiguous CUDA float32 tensors of ny x nx elements")
+    _check(lib.molt_helmholtz_columns_noalloc(int(nx), int(ny), float(Ly), BC[bc], int(quad_order), float(c),
+                                              ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                              _stream_handle(stream)))
 
 
 def _stream_handle(stream):
