@@ -326,17 +326,58 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
 }
 
 // ---- pointwise and reductions ----
+// out = c0 x0 + c1 x1 + c2 x2 + c3 x3 + c4 in the field precision (FP64 arithmetic on an FP32
+// field would make this pass ALU-bound on a part with a small FP64 rate).
 template <typename T>
-__global__ void lincomb_kernel(T* out, long long n, const T* x0, double c0, const T* x1, double c1, const T* x2,
-                               double c2, const T* x3, double c3, double c4) {
+__device__ __forceinline__ T lin_elem(const T* x0, T c0, const T* x1, T c1, const T* x2, T c2, const T* x3, T c3,
+                                      T c4, long long i) {
+    if (x0 && x1 && c1 == -c0 && !x2 && !x3) return fma(c0, x0[i] - x1[i], c4);   // scaled difference
+    T acc = c4;
+    if (x0) acc = fma(c0, x0[i], acc);
+    if (x1) acc = fma(c1, x1[i], acc);
+    if (x2) acc = fma(c2, x2[i], acc);
+    if (x3) acc = fma(c3, x3[i], acc);
+    return acc;
+}
+
+template <typename T>
+__global__ void lincomb_kernel(T* out, long long n, const T* x0, T c0, const T* x1, T c1, const T* x2, T c2,
+                               const T* x3, T c3, T c4) {
     const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n; i += stride) {
-        double acc = c4;
-        if (x0) acc += c0 * static_cast<double>(x0[i]);
-        if (x1) acc += c1 * static_cast<double>(x1[i]);
-        if (x2) acc += c2 * static_cast<double>(x2[i]);
-        if (x3) acc += c3 * static_cast<double>(x3[i]);
-        out[i] = static_cast<T>(acc);
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n; i += stride)
+        out[i] = lin_elem(x0, c0, x1, c1, x2, c2, x3, c3, c4, i);
+}
+
+// FP32 with every pointer 16-byte aligned and n % 4 == 0: four elements per thread and access.
+static __global__ void lincomb4_kernel(float* out, long long n4, const float* x0, float c0, const float* x1, float c1,
+                                const float* x2, float c2, const float* x3, float c3, float c4) {
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n4; i += stride) {
+        float4 acc = make_float4(c4, c4, c4, c4);
+        if (x1 && c1 == -c0 && !x2 && !x3) {
+            // scaled difference c0 (x0 - x1): difference first (exact for nearby values), then scale
+            const float4 a = reinterpret_cast<const float4*>(x0)[i];
+            const float4 b = reinterpret_cast<const float4*>(x1)[i];
+            acc.x = fmaf(c0, a.x - b.x, c4);
+            acc.y = fmaf(c0, a.y - b.y, c4);
+            acc.z = fmaf(c0, a.z - b.z, c4);
+            acc.w = fmaf(c0, a.w - b.w, c4);
+            reinterpret_cast<float4*>(out)[i] = acc;
+            continue;
+        }
+        auto add = [&](const float* x, float c) {
+            if (!x) return;
+            const float4 v = reinterpret_cast<const float4*>(x)[i];
+            acc.x = fmaf(c, v.x, acc.x);
+            acc.y = fmaf(c, v.y, acc.y);
+            acc.z = fmaf(c, v.z, acc.z);
+            acc.w = fmaf(c, v.w, acc.w);
+        };
+        add(x0, c0);
+        add(x1, c1);
+        add(x2, c2);
+        add(x3, c3);
+        reinterpret_cast<float4*>(out)[i] = acc;
     }
 }
 
@@ -426,11 +467,25 @@ int max_row_length(int nf) {
 template <typename T>
 cudaError_t lincomb(T* out, long long n, const T* x0, double c0, const T* x1, double c1, const T* x2, double c2,
                     const T* x3, double c3, double c4, cudaStream_t st, long long* launches) {
+    if (launches) *launches += 1;
+    if constexpr (std::is_same<T, float>::value) {
+        auto al = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+        if (n % 4 == 0 && al(out) && al(x0) && al(x1) && al(x2) && al(x3)) {
+            long long blocks = (n / 4 + 255) / 256;
+            if (blocks > 152 * 8) blocks = 152 * 8;
+            if (blocks < 1) blocks = 1;
+            detail::lincomb4_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(
+                out, n / 4, x0, static_cast<float>(c0), x1, static_cast<float>(c1), x2, static_cast<float>(c2), x3,
+                static_cast<float>(c3), static_cast<float>(c4));
+            return cudaGetLastError();
+        }
+    }
     long long blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    detail::lincomb_kernel<T><<<static_cast<int>(blocks), 256, 0, st>>>(out, n, x0, c0, x1, c1, x2, c2, x3, c3, c4);
-    if (launches) *launches += 1;
+    detail::lincomb_kernel<T><<<static_cast<int>(blocks), 256, 0, st>>>(
+        out, n, x0, static_cast<T>(c0), x1, static_cast<T>(c1), x2, static_cast<T>(c2), x3, static_cast<T>(c3),
+        static_cast<T>(c4));
     return cudaGetLastError();
 }
 

@@ -494,10 +494,11 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const Op op, int 
                     s_scan[lane][2 + NF + q] = exB[q];
                 }
             }
-            if (lane == 0) {
-                // one FP64 2x2 boundary solve per line (Eq. homogeneous and analogues)
+            // one FP64 2x2 boundary solve per line and field (Eq. homogeneous and analogues);
+            // lane q solves field q
 #pragma unroll
-                for (int q = 0; q < NF; ++q) {
+            for (int q = 0; q < NF; ++q) {
+                if (lane == q) {
                     const double I0 = static_cast<double>(totB[q]);
                     const double IN = static_cast<double>(totF[q]);
                     double a, b;
@@ -834,19 +835,24 @@ cols_pipe_kernel(const __grid_constant__ LineParams<float> lp, const Op op, int 
                         }
                 }
             }
+            T* ob[NO];
+#pragma unroll
+            for (int o = 0; o < NO; ++o) ob[o] = op.o[o] + static_cast<long long>(start) * ld + line;
+            const float* sbase = buf(sb, 0) + (wy * KY + HR) * 32 + lane;
 #pragma unroll
             for (int k = 0; k < KY; ++k) {
                 if (k < cnt) {
-                    const int row_local = wy * KY + HR + k;
                     T h[NF], sv[NS], av[1] = {T(0)}, ov[NO];
 #pragma unroll
                     for (int q = 0; q < NF; ++q) h[q] = out[q][k];
 #pragma unroll
-                    for (int f = 0; f < NS; ++f) sv[f] = buf(sb, f)[row_local * 32 + lane];
+                    for (int f = 0; f < NS; ++f) sv[f] = sbase[static_cast<size_t>(f) * ROWS * 32 + k * 32];
                     op.epilogue(h, sv, av, ov, red);
 #pragma unroll
-                    for (int o = 0; o < NO; ++o) op.o[o][static_cast<long long>(start + k) * ld + line] = ov[o];
+                    for (int o = 0; o < NO; ++o) *ob[o] = ov[o];
                 }
+#pragma unroll
+                for (int o = 0; o < NO; ++o) ob[o] += ld;
             }
         }
     }
