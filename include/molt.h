@@ -85,7 +85,7 @@ molt_status molt_grid_create(molt_grid** grid, int dim, int nx, int ny, double L
 void molt_grid_destroy(molt_grid* grid);
 
 /* Create a solver on the current CUDA device for `grid` with parameters `p` (copied).
- * Allocates the device workspace (about 12 fields of the grid's size).
+ * Allocates the device workspace (15 fields of the grid's size).
  * Errors: MOLT_ERR_ARG (eps <= 0, M not in {2,4,6}, tol <= 0, max_iter < 1,
  * line shorter than M+2, or x lines longer than the row kernels support: 16384 nodes),
  * MOLT_ERR_OOM, MOLT_ERR_CUDA.  2D time steps additionally need nx <= 8192
@@ -98,6 +98,19 @@ molt_status molt_set_params(molt_solver* solver, const molt_params* p);
 
 /* Change the boundary condition of both directions.  Clears the time history. */
 molt_status molt_set_bc(molt_solver* solver, int bc);
+
+/* How a stage's fixed-point loop is driven.
+ * MOLT_EXEC_GRAPH (default): the loop is a CUDA graph with a conditional WHILE node whose
+ *   body launches one iteration and a one-thread check kernel that applies the stopping rule on
+ *   the device; the host reads the loop state back once per stage.  Graphs are built on first
+ *   use per stage coefficient and reused while parameters, boundary condition and dt are
+ *   unchanged.  If a graph cannot be built, the host-driven loop runs instead (counted by
+ *   molt_graph_fallbacks).
+ * MOLT_EXEC_HOST_LOOP: the host launches each iteration and reads the residual back after it
+ *   (also used while profiling is enabled). */
+typedef enum { MOLT_EXEC_HOST_LOOP = 0, MOLT_EXEC_GRAPH = 1 } molt_execution;
+molt_status molt_set_execution(molt_solver* solver, int mode);
+long long molt_graph_fallbacks(const molt_solver* solver);
 
 /* Forget the time history (BDF2 previous level, SDC2 level-[0] state). */
 molt_status molt_reset_history(molt_solver* solver);

@@ -43,10 +43,10 @@ template <typename T> inline OpP4<T> build(const OpArgs<T>& a, OpP4<T>*) {
     o.shift = a.shift; return o;
 }
 template <typename T> inline Op1a<T> build(const OpArgs<T>& a, Op1a<T>*) {
-    Op1a<T> o; o.r = a.in0; o.w = a.in1; o.e_out = a.out0; o.g2 = a.g2; o.g1 = a.g1; o.beta = a.beta; return o;
+    Op1a<T> o; o.w = a.in0; o.e_out = a.out0; o.g2 = a.g2; o.g1 = a.g1; o.beta = a.beta; return o;
 }
 template <typename T> inline Op1b<T> build(const OpArgs<T>& a, Op1b<T>*) {
-    Op1b<T> o; o.e_in = a.in0; o.w = a.out0; o.shift = a.shift; return o;
+    Op1b<T> o; o.e_in = a.in0; o.y_in = a.in1; o.w = a.out0; o.shift = a.shift; return o;
 }
 
 // Opt the kernel into the largest dynamic shared memory the device allows next to its static
@@ -164,8 +164,8 @@ P pipe_build(int kind, const OpArgs<float>& a) {
         case OP_COPY: p.s[0] = a.in0; p.o[0] = a.out0; break;
         case OP_P2: p.s[0] = a.in0; p.s[1] = a.in1; p.s[2] = a.in2; p.o[0] = a.out0; p.o[1] = a.out1; break;
         case OP_P4: p.s[0] = a.in0; p.s[1] = a.in2; p.a[0] = a.out0; p.a[1] = a.in3; p.a[2] = a.in1; p.o[0] = a.out0; break;
-        case OP_1A: p.s[0] = a.in0; p.s[1] = a.in1; p.o[0] = a.out0; break;
-        case OP_1B: p.s[0] = a.in0; p.a[0] = a.out0; p.o[0] = a.out0; break;
+        case OP_1A: p.s[0] = a.in0; p.o[0] = a.out0; break;
+        case OP_1B: p.s[0] = a.in0; p.a[0] = a.out0; p.a[1] = a.in1; p.o[0] = a.out0; break;
     }
     return p;
 }
@@ -489,6 +489,28 @@ cudaError_t lincomb(T* out, long long n, const T* x0, double c0, const T* x1, do
     return cudaGetLastError();
 }
 
+namespace detail {
+template <typename T>
+__global__ void cubic_kernel(T* out, long long n, const T* x, T a2, T a1) {
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+        const T v = x[i];
+        out[i] = v * fma(v, v + a2, a1);
+    }
+}
+}  // namespace detail
+
+template <typename T>
+cudaError_t cubic(T* out, long long n, const T* x, double a2, double a1, cudaStream_t st, long long* launches) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    detail::cubic_kernel<T><<<static_cast<int>(blocks), 256, 0, st>>>(out, n, x, static_cast<T>(a2),
+                                                                      static_cast<T>(a1));
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t energy_mass(const T* u, int nx, int ny, int bc, double hx, double hy, double eps, int which,
                         double* partials, double* result, cudaStream_t st, long long* launches) {
@@ -511,4 +533,5 @@ cudaError_t energy_mass(const T* u, int nx, int ny, int bc, double hx, double hy
     template cudaError_t molt::lincomb<T>(T*, long long, const T*, double, const T*, double, const T*, double,  \
                                           const T*, double, double, cudaStream_t, long long*);                  \
     template cudaError_t molt::energy_mass<T>(const T*, int, int, int, double, double, double, int, double*,    \
-                                              double*, cudaStream_t, long long*);
+                                              double*, cudaStream_t, long long*);                               \
+    template cudaError_t molt::cubic<T>(T*, long long, const T*, double, double, cudaStream_t, long long*);

@@ -126,6 +126,29 @@ template <typename T>
 cudaError_t lincomb(T* out, long long n, const T* x0, double c0, const T* x1, double c1, const T* x2,
                     double c2, const T* x3, double c3, double c4, cudaStream_t st, long long* launches);
 
+// Device-side state of one fixed-point stage loop (graph execution mode).
+struct LoopState {
+    int k;            // iterations done
+    int stall;        // iterations without a new residual minimum
+    int done;         // loop finished
+    int converged;    // finished by the tolerance (or at FP32 precision)
+    double best;      // smallest residual so far
+    double res;       // last residual max |w_new - w|
+    double tol_used;  // tolerance applied at the last check
+};
+
+// Reset the loop state and the residual slots (one thread).
+cudaError_t loop_init(LoopState* ls, unsigned long long* red, cudaStream_t st);
+// Read the residual slots, apply the stopping rule of the host loop (tolerance, FP32 floor of
+// 2 ulp of max|w|, stall at the FP32 noise floor, iteration cap), clear the slots and set the
+// conditional of the enclosing WHILE node: 1 = iterate again, 0 = stop.
+cudaError_t loop_check(cudaGraphConditionalHandle h, LoopState* ls, unsigned long long* red, double tol,
+                       int max_iter, int fp32, cudaStream_t st);
+
+// out = x (x (x + a2) + a1), n elements (the pointwise cubic f of Eq. CahnHilliard_v).
+template <typename T>
+cudaError_t cubic(T* out, long long n, const T* x, double a2, double a1, cudaStream_t st, long long* launches);
+
 // FP64 energy / mass partial sums: per-block partials into `partials` (>= reduce_blocks()),
 // then a single-block fixed-order sum into `result`.
 template <typename T>

@@ -145,6 +145,8 @@ struct molt_solver {
     std::string err;
     long long launches = 0;
     molt::Prof prof;
+    int exec_mode = MOLT_EXEC_GRAPH;
+    long long graph_fallbacks = 0;
     // history
     bool have_prev = false;
     double dt_prev = 0.0;
@@ -156,6 +158,7 @@ struct molt_solver {
     virtual molt_status reduce(const void* u, int which, double* out, cudaStream_t st) = 0;
     virtual molt_status apply(int axis, double c, const void* in, void* out, cudaStream_t st) = 0;
     virtual molt_status init() = 0;
+    virtual void drop_graphs() = 0;
 };
 
 namespace {
@@ -166,6 +169,7 @@ struct Solver final : molt_solver {
     T *w = nullptr, *wn = nullptr, *wprev = nullptr, *r = nullptr, *Y = nullptr;
     T *f1 = nullptr, *f2 = nullptr, *f3 = nullptr, *f4 = nullptr, *f5 = nullptr, *f6 = nullptr;
     T *k0 = nullptr, *k1 = nullptr, *ubuf = nullptr;
+    T *sdc_w0 = nullptr, *sdc_F0 = nullptr;   // SDC2: level-[0] state and its F
     molt::ColScratch<T> cs{};
     unsigned long long* red = nullptr;       // device [2]
     unsigned long long* red_host = nullptr;  // pinned [2]
@@ -179,6 +183,9 @@ struct Solver final : molt_solver {
     T shift() const { return bc == molt::BC_DIRICHLET ? T(0) : T(1); }
 
     ~Solver() override {
+        drop_graphs();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (ls_host) cudaFreeHost(ls_host);
         for (void* a : allocs) cudaFree(a);
         if (red_host) cudaFreeHost(red_host);
         if (result_host) cudaFreeHost(result_host);
@@ -204,7 +211,7 @@ struct Solver final : molt_solver {
 
     molt_status init() override {
         const size_t n = count();
-        T** fields[] = {&w, &wn, &wprev, &r, &Y, &f1, &f2, &f3, &f4, &f5, &f6, &k0, &k1};
+        T** fields[] = {&w, &wn, &wprev, &r, &Y, &f1, &f2, &f3, &f4, &f5, &f6, &k0, &k1, &sdc_w0, &sdc_F0};
         for (T** f : fields)
             if (!alloc(f, n)) return fail(MOLT_ERR_OOM, "device workspace allocation failed");
         const int nlines = g.nx;
@@ -216,8 +223,10 @@ struct Solver final : molt_solver {
         if (!alloc(&cs.aggL, sc) || !alloc(&cs.aggR, sc) || !alloc(&cs.carL, sc) || !alloc(&cs.carR, sc) ||
             !alloc(&red, 2) || !alloc(&partials, static_cast<size_t>(molt::reduce_blocks())) || !alloc(&result, 1))
             return fail(MOLT_ERR_OOM, "device scratch allocation failed");
+        if (!alloc(&ls, 1)) return fail(MOLT_ERR_OOM, "device loop state allocation failed");
         if (cudaMallocHost(&red_host, 2 * sizeof(unsigned long long)) != cudaSuccess ||
-            cudaMallocHost(&result_host, sizeof(double)) != cudaSuccess)
+            cudaMallocHost(&result_host, sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&ls_host, sizeof(molt::LoopState)) != cudaSuccess)
             return fail(MOLT_ERR_OOM, "pinned host allocation failed");
         return MOLT_OK;
     }
@@ -253,24 +262,203 @@ struct Solver final : molt_solver {
                                 &launches);
     }
 
-    // Solve v - tau F(v) = r for w (in: first guess, out: last iterate), r in stored form.
-    molt_status stage(double tau, const T* rhs, cudaStream_t st, int* iters, double* res_out, double* tol_out) {
-        const StageParams sp = stage_params(tau, p.eps);
+    // out = M_c^{-1} in = H_x H_y in (2D) or H_x in (1D); uses f1 as scratch in 2D.
+    cudaError_t mm_inv(double c, const T* in, T* out, cudaStream_t st) {
+        molt::LineParams<T> lx, ly;
+        if (!line_params(c, 0, &lx)) return cudaErrorInvalidValue;
+        if (g.dim == 1) return copy_sweep(0, lx, in, out, st);
+        if (!line_params(c, 1, &ly)) return cudaErrorInvalidValue;
+        cudaError_t e = copy_sweep(1, ly, in, f1, st);
+        if (e != cudaSuccess) return e;
+        return copy_sweep(0, lx, f1, out, st);
+    }
+
+    // out = E_c in with E = M^{-1} - I + D_x D_y, i.e. 2 H_x H_y - H_x - H_y in 2D and H - I in 1D
+    // (the operator through which M^{-1} acts on c Lap, Remark Laplacian); scratch f1, f2, f3.
+    cudaError_t e_op(double c, const T* in, T* out, cudaStream_t st) {
+        molt::LineParams<T> lx, ly;
+        if (!line_params(c, 0, &lx)) return cudaErrorInvalidValue;
+        cudaError_t e;
+        if (g.dim == 1) {
+            if ((e = copy_sweep(0, lx, in, f1, st)) != cudaSuccess) return e;
+            return lin(out, f1, 1.0, in, -1.0, nullptr, 0, nullptr, 0, 0, st);
+        }
+        if (!line_params(c, 1, &ly)) return cudaErrorInvalidValue;
+        if ((e = copy_sweep(1, ly, in, f1, st)) != cudaSuccess) return e;      // H_y
+        if ((e = copy_sweep(0, lx, f1, f2, st)) != cudaSuccess) return e;      // H_x H_y
+        if ((e = copy_sweep(0, lx, in, f3, st)) != cudaSuccess) return e;      // H_x
+        return lin(out, f2, 2.0, f3, -1.0, f1, -1.0, nullptr, 0, 0, st);
+    }
+
+    // out = M_o^{-1} M_i^{-1} F(v) for v stored in w_in, without derivatives (Remark Laplacian /
+    // biLaplacian): -(eps^2/(c_i c_o)) E_o E_i v + (1/c_i) M_o^{-1} E_i f(v-1).  E kills constants
+    // on periodic / Neumann grids, so E_i v = E_i w there; f(v-1) = w^3 - w for w = v - 1 and
+    // v^3 - 3v^2 + 2v for w = v.  Scratch: f1..f6.
+    cudaError_t inverse_of_F(const StageParams& sp, const T* w_in, T* out, cudaStream_t st) {
+        cudaError_t e;
+        if ((e = e_op(sp.c_in, w_in, f4, st)) != cudaSuccess) return e;        // E_i v
+        if ((e = e_op(sp.c_out, f4, f5, st)) != cudaSuccess) return e;         // E_o E_i v
+        const bool shifted = shift() == T(1);
+        if ((e = molt::cubic<T>(f6, static_cast<long long>(count()), w_in, shifted ? 0.0 : -3.0,
+                                shifted ? -1.0 : 2.0, st, &launches)) != cudaSuccess)
+            return e;                                                           // f(v-1)
+        if ((e = e_op(sp.c_in, f6, f4, st)) != cudaSuccess) return e;         // E_i f
+        if ((e = mm_inv(sp.c_out, f4, f6, st)) != cudaSuccess) return e;      // M_o^{-1} E_i f
+        return lin(out, f5, -(p.eps * p.eps) / (sp.c_in * sp.c_out), f6, 1.0 / sp.c_in, nullptr, 0, nullptr, 0, 0,
+                   st);
+    }
+
+    // Everything one fixed-point iteration of a stage launches (line parameters by value).
+    struct Passes {
         molt::LineParams<T> lix, lox, liy, loy;
-        if (!line_params(sp.c_in, 0, &lix) || !line_params(sp.c_out, 0, &lox)) return MOLT_ERR_ARG;
-        const bool two_d = g.dim == 2;
-        if (two_d && (!line_params(sp.c_in, 1, &liy) || !line_params(sp.c_out, 1, &loy))) return MOLT_ERR_ARG;
-        const T s = shift();
-        const T g2 = s == T(1) ? T(0) : T(-3);
-        const T g1 = s == T(1) ? static_cast<T>(sp.lam - 3.0) : static_cast<T>(sp.lam);
-        const T beta = static_cast<T>(sp.beta);
+        T g2, g1, beta, s;
+        bool two_d;
+    };
+
+    bool make_passes(const StageParams& sp, Passes* ps) {
+        ps->two_d = g.dim == 2;
+        if (!line_params(sp.c_in, 0, &ps->lix) || !line_params(sp.c_out, 0, &ps->lox)) return false;
+        if (ps->two_d && (!line_params(sp.c_in, 1, &ps->liy) || !line_params(sp.c_out, 1, &ps->loy))) return false;
+        ps->s = shift();
+        ps->g2 = ps->s == T(1) ? T(0) : T(-3);
+        ps->g1 = ps->s == T(1) ? static_cast<T>(sp.lam - 3.0) : static_cast<T>(sp.lam);
+        ps->beta = static_cast<T>(sp.beta);
+        return true;
+    }
+
+    // One iteration: 2D passes 1-4 (column, row, column, row) or the two 1D row passes.  The
+    // last pass accumulates the residual into `red`.
+    cudaError_t launch_iteration(const Passes& ps, cudaStream_t st) {
+        cudaError_t e;
+        if (ps.two_d) {
+            molt::OpArgs<T> a1;
+            a1.in0 = w; a1.out0 = f1; a1.out1 = f2; a1.g2 = ps.g2; a1.g1 = ps.g1;
+            if ((e = sweep(1, ps.liy, molt::OP_P1, a1, st)) != cudaSuccess) return e;
+            molt::OpArgs<T> a2;
+            a2.in0 = w; a2.in1 = f1; a2.in2 = f2; a2.out0 = f3; a2.out1 = f4;
+            a2.g2 = ps.g2; a2.g1 = ps.g1; a2.beta = ps.beta;
+            if ((e = sweep(0, ps.lix, molt::OP_P2, a2, st)) != cudaSuccess) return e;
+            molt::OpArgs<T> a3;
+            a3.in0 = f3; a3.in1 = f4; a3.out0 = f5; a3.out1 = f6;
+            if ((e = sweep(1, ps.loy, molt::OP_P3, a3, st)) != cudaSuccess) return e;
+            molt::OpArgs<T> a4;
+            a4.in0 = f5; a4.in1 = f6; a4.in2 = f4; a4.in3 = Y; a4.out0 = w; a4.shift = ps.s;
+            return sweep(0, ps.lox, molt::OP_P4, a4, st);
+        }
+        molt::OpArgs<T> aa;
+        aa.in0 = w; aa.out0 = f1; aa.g2 = ps.g2; aa.g1 = ps.g1; aa.beta = ps.beta;
+        if ((e = sweep(0, ps.lix, molt::OP_1A, aa, st)) != cudaSuccess) return e;
+        molt::OpArgs<T> ab;
+        ab.in0 = f1; ab.in1 = Y; ab.out0 = w; ab.shift = ps.s;
+        return sweep(0, ps.lox, molt::OP_1B, ab, st);
+    }
+
+    // Executable graphs of the stage loop, one per stage coefficient tau: a conditional WHILE
+    // node whose body is one iteration followed by the device-side stopping check.
+    struct LoopGraph {
+        bool valid = false;
+        double tau = 0.0;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        long long kernels_per_iter = 0;
+    };
+    static constexpr int kGraphSlots = 4;
+    LoopGraph graphs[kGraphSlots];
+    int next_graph = 0;
+    cudaStream_t cap_stream = nullptr;
+    molt::LoopState* ls = nullptr;
+    molt::LoopState* ls_host = nullptr;
+
+    void drop_graphs() override {
+        for (LoopGraph& lg : graphs) {
+            if (lg.exec) cudaGraphExecDestroy(lg.exec);
+            if (lg.graph) cudaGraphDestroy(lg.graph);
+            lg = LoopGraph();
+        }
+    }
+
+    LoopGraph* loop_graph(double tau, const Passes& ps) {
+        for (LoopGraph& lg : graphs)
+            if (lg.valid && lg.tau == tau) return &lg;
+        LoopGraph& lg = graphs[next_graph];
+        next_graph = (next_graph + 1) % kGraphSlots;
+        if (lg.exec) cudaGraphExecDestroy(lg.exec);
+        if (lg.graph) cudaGraphDestroy(lg.graph);
+        lg = LoopGraph();
+        if (!cap_stream && cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        cudaGraph_t graph = nullptr;
+        if (cudaGraphCreate(&graph, 0) != cudaSuccess) return nullptr;
+        cudaGraphConditionalHandle h;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        cudaGraphNode_t node;
+        bool ok = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+        if (ok) {
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) == cudaSuccess;
+        }
+        const long long before = launches;
+        if (ok) {
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            ok = cudaStreamBeginCaptureToGraph(cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
+                 cudaSuccess;
+            if (ok) {
+                const bool launched =
+                    launch_iteration(ps, cap_stream) == cudaSuccess &&
+                    molt::loop_check(h, ls, red, p.tol, p.max_iter, fp32() ? 1 : 0, cap_stream) == cudaSuccess;
+                cudaGraph_t captured = nullptr;
+                ok = cudaStreamEndCapture(cap_stream, &captured) == cudaSuccess && launched;
+            }
+        }
+        lg.kernels_per_iter = launches - before + 1;
+        launches = before;
+        cudaGraphExec_t exec = nullptr;
+        if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            if (exec) cudaGraphExecDestroy(exec);
+            cudaGraphDestroy(graph);
+            return nullptr;
+        }
+        lg.valid = true;
+        lg.tau = tau;
+        lg.graph = graph;
+        lg.exec = exec;
+        return &lg;
+    }
+
+    // Solve v - tau F(v) = r for w (in: first guess, out: last iterate), r in stored form.
+    // With y_given, the field Y already holds M_o^{-1} M_i^{-1} r and rhs is not read.
+    molt_status stage(double tau, const T* rhs, cudaStream_t st, int* iters, double* res_out, double* tol_out,
+                      bool y_given = false) {
+        const StageParams sp = stage_params(tau, p.eps);
+        Passes ps;
+        if (!make_passes(sp, &ps)) return MOLT_ERR_ARG;
         cudaError_t e = cudaSuccess;
-        if (two_d) {
+        if (!y_given) {
             // Y = M_o^{-1} M_i^{-1} r
-            if ((e = copy_sweep(1, liy, rhs, f1, st)) != cudaSuccess) return cuda_fail(e, "sweep");
-            if ((e = copy_sweep(0, lix, f1, f2, st)) != cudaSuccess) return cuda_fail(e, "sweep");
-            if ((e = copy_sweep(1, loy, f2, f1, st)) != cudaSuccess) return cuda_fail(e, "sweep");
-            if ((e = copy_sweep(0, lox, f1, Y, st)) != cudaSuccess) return cuda_fail(e, "sweep");
+            if ((e = mm_inv(sp.c_in, rhs, f2, st)) != cudaSuccess) return cuda_fail(e, "rhs inverse");
+            if ((e = mm_inv(sp.c_out, f2, Y, st)) != cudaSuccess) return cuda_fail(e, "rhs inverse");
+        }
+        if (exec_mode == MOLT_EXEC_GRAPH && !prof.on) {
+            LoopGraph* lg = loop_graph(tau, ps);
+            if (lg) {
+                // the whole loop on the device; one read-back of the loop state per stage
+                if ((e = molt::loop_init(ls, red, st)) != cudaSuccess) return cuda_fail(e, "loop init");
+                if ((e = cudaGraphLaunch(lg->exec, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
+                if ((e = cudaMemcpyAsync(ls_host, ls, sizeof(molt::LoopState), cudaMemcpyDeviceToHost, st)) !=
+                    cudaSuccess)
+                    return cuda_fail(e, "loop state copy");
+                if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream sync");
+                launches += 1 + static_cast<long long>(ls_host->k) * lg->kernels_per_iter;
+                *iters = ls_host->k;
+                *res_out = ls_host->res;
+                *tol_out = ls_host->tol_used;
+                return ls_host->converged ? MOLT_OK : MOLT_ERR_NOT_CONVERGED;
+            }
+            graph_fallbacks += 1;     // graph construction failed: run the host-driven loop
         }
         double res = INFINITY, tol_used = p.tol, best = INFINITY;
         int k = 0, stall = 0;
@@ -278,28 +466,7 @@ struct Solver final : molt_solver {
         for (k = 1; k <= p.max_iter; ++k) {
             if ((e = cudaMemsetAsync(red, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
                 return cuda_fail(e, "memset");
-            if (two_d) {
-                molt::OpArgs<T> a1;
-                a1.in0 = w; a1.out0 = f1; a1.out1 = f2; a1.g2 = g2; a1.g1 = g1;
-                if ((e = sweep(1, liy, molt::OP_P1, a1, st)) != cudaSuccess) return cuda_fail(e, "pass 1");
-                molt::OpArgs<T> a2;
-                a2.in0 = w; a2.in1 = f1; a2.in2 = f2; a2.out0 = f3; a2.out1 = f4;
-                a2.g2 = g2; a2.g1 = g1; a2.beta = beta;
-                if ((e = sweep(0, lix, molt::OP_P2, a2, st)) != cudaSuccess) return cuda_fail(e, "pass 2");
-                molt::OpArgs<T> a3;
-                a3.in0 = f3; a3.in1 = f4; a3.out0 = f5; a3.out1 = f6;
-                if ((e = sweep(1, loy, molt::OP_P3, a3, st)) != cudaSuccess) return cuda_fail(e, "pass 3");
-                molt::OpArgs<T> a4;
-                a4.in0 = f5; a4.in1 = f6; a4.in2 = f4; a4.in3 = Y; a4.out0 = w; a4.shift = s;
-                if ((e = sweep(0, lox, molt::OP_P4, a4, st)) != cudaSuccess) return cuda_fail(e, "pass 4");
-            } else {
-                molt::OpArgs<T> aa;
-                aa.in0 = rhs; aa.in1 = w; aa.out0 = f1; aa.g2 = g2; aa.g1 = g1; aa.beta = beta;
-                if ((e = sweep(0, lix, molt::OP_1A, aa, st)) != cudaSuccess) return cuda_fail(e, "pass a");
-                molt::OpArgs<T> ab;
-                ab.in0 = f1; ab.out0 = w; ab.shift = s;
-                if ((e = sweep(0, lox, molt::OP_1B, ab, st)) != cudaSuccess) return cuda_fail(e, "pass b");
-            }
+            if ((e = launch_iteration(ps, st)) != cudaSuccess) return cuda_fail(e, "iteration");
             if ((e = cudaMemcpyAsync(red_host, red, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) !=
                 cudaSuccess)
                 return cuda_fail(e, "residual copy");
@@ -310,8 +477,7 @@ struct Solver final : molt_solver {
             res = dmax;
             if (!std::isfinite(res)) break;
             // FP32 fields cannot resolve changes below a few units in the last place of the
-            // stored variable: the tolerance is floored at 2 ulp of max|w|, and an iteration that
-            // has reached 64 ulp and stopped improving for 8 steps is at FP32 precision.
+            // stored variable: the tolerance is floored at 2 ulp of max|w| (see the stall rule below).
             const double ulp = std::ldexp(1.0, -24) * wmax;
             tol_used = fp32() ? std::max(p.tol, 2.0 * ulp) : p.tol;
             if (res < tol_used) {
@@ -372,6 +538,50 @@ struct Solver final : molt_solver {
         return worst;
     }
 
+    // SDC2 (Sec. 4.3, Eq. IDC_BE_j with the trapezoid rule, Eq. SDC_fixed): the level-[0] BE
+    // trajectory and the level-[1] correction advance together.  Level [1] solves
+    //   v1_{n+1} - dt F(v1_{n+1}) = v1_n - (dt/2)(F0_{n+1} - F0_n),
+    // with F0_{n+1} = (v0_{n+1} - v0_n)/dt from the BE identity and, at a (re)start, F0_n taken
+    // inside the inverse (inverse_of_F).  Level [1] starts from the level-[0] value.
+    molt_status sdc2(double dt, cudaStream_t st, molt_step_info* info) {
+        const bool start = !have_sdc || dt_prev != dt;
+        const StageParams sp = stage_params(dt, p.eps);
+        const T* v0n = start ? wn : sdc_w0;
+        cudaError_t e;
+        if ((e = lin(w, v0n, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
+            return cuda_fail(e, "sdc guess");
+        int it;
+        double res, tu;
+        molt_status worst = MOLT_OK;
+        molt_status ms = stage(dt, v0n, st, &it, &res, &tu);                  // level [0]: BE
+        if (ms != MOLT_OK && ms != MOLT_ERR_NOT_CONVERGED) return ms;
+        if (ms != MOLT_OK) worst = ms;
+        record(info, 0, it, res, tu);
+        if ((e = lin(k0, w, 1.0 / dt, v0n, -1.0 / dt, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
+            return cuda_fail(e, "sdc F");                                      // F0_{n+1}
+        if ((e = lin(k1, w, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
+            return cuda_fail(e, "sdc state");                                  // v0_{n+1}
+        if (start) {
+            if ((e = lin(r, wn, 1.0, k0, -0.5 * dt, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess ||
+                (e = mm_inv(sp.c_in, r, f2, st)) != cudaSuccess || (e = mm_inv(sp.c_out, f2, Y, st)) != cudaSuccess ||
+                (e = inverse_of_F(sp, v0n, sdc_F0, st)) != cudaSuccess ||
+                (e = lin(Y, Y, 1.0, sdc_F0, 0.5 * dt, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
+                return cuda_fail(e, "sdc rhs");
+        } else {
+            if ((e = lin(r, wn, 1.0, k0, -0.5 * dt, sdc_F0, 0.5 * dt, nullptr, 0, 0, st)) != cudaSuccess ||
+                (e = mm_inv(sp.c_in, r, f2, st)) != cudaSuccess || (e = mm_inv(sp.c_out, f2, Y, st)) != cudaSuccess)
+                return cuda_fail(e, "sdc rhs");
+        }
+        ms = stage(dt, nullptr, st, &it, &res, &tu, true);                     // level [1]
+        if (ms != MOLT_OK && ms != MOLT_ERR_NOT_CONVERGED) return ms;
+        if (ms != MOLT_OK) worst = ms;
+        record(info, 1, it, res, tu);
+        std::swap(sdc_w0, k1);
+        std::swap(sdc_F0, k0);
+        have_sdc = true;
+        return worst;
+    }
+
     molt_status step(void* u_void, double dt, int scheme, cudaStream_t st, molt_step_info* info) override {
         T* u = static_cast<T*>(u_void);
         if (info) std::memset(info, 0, sizeof(*info));
@@ -414,9 +624,13 @@ struct Solver final : molt_solver {
                 ms = sdirk(dt, A, 3, st, info, 0);
                 break;
             }
+            case MOLT_SDC2:
+                ms = sdc2(dt, st, info);
+                break;
             default:
                 return fail(MOLT_ERR_UNSUPPORTED, "scheme not supported by this build");
         }
+        if (scheme != MOLT_SDC2) have_sdc = false;
         if (ms != MOLT_OK && ms != MOLT_ERR_NOT_CONVERGED) return ms;
         // history for BDF2: previous level
         std::swap(wprev, wn);
@@ -550,6 +764,7 @@ molt_status molt_set_params(molt_solver* s, const molt_params* p) {
     s->p = *p;
     s->have_prev = false;
     s->have_sdc = false;
+    s->drop_graphs();
     return MOLT_OK;
 }
 
@@ -560,8 +775,18 @@ molt_status molt_set_bc(molt_solver* s, int bc) {
     s->g.bc = bc;
     s->have_prev = false;
     s->have_sdc = false;
+    s->drop_graphs();
     return MOLT_OK;
 }
+
+molt_status molt_set_execution(molt_solver* s, int mode) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    if (mode != MOLT_EXEC_HOST_LOOP && mode != MOLT_EXEC_GRAPH) { s->err = "unknown execution mode"; return MOLT_ERR_ARG; }
+    s->exec_mode = mode;
+    return MOLT_OK;
+}
+
+long long molt_graph_fallbacks(const molt_solver* s) { return s ? s->graph_fallbacks : 0; }
 
 molt_status molt_reset_history(molt_solver* s) {
     if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");

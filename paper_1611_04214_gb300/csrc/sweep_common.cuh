@@ -285,20 +285,18 @@ struct OpP4 : OpBase<T> {
     }
 };
 
-// 1D pass a (inner c): E = H_i[r + beta G(w)] - beta G(w).
+// 1D pass a (inner c): E = H_i[beta G(w)] - beta G(w).
 template <typename T>
 struct Op1a : OpBase<T> {
     static constexpr int NF = 1;
     static constexpr int NA = 1;
     static constexpr int kAxes = 1;
     static constexpr bool kReduce = false;
-    const T* r;
     const T* w;
     T* e_out;
     T g2, g1, beta;
     __device__ __forceinline__ void load(int line, int pos, T (&f)[1]) const {
-        const size_t i = this->at(line, pos);
-        f[0] = fma(beta, g_lag(w[i], g2, g1), r[i]);
+        f[0] = beta * g_lag(w[this->at(line, pos)], g2, g1);
     }
     __device__ __forceinline__ void fetch(int line, int pos, T (&a)[NA]) const { a[0] = w[this->at(line, pos)]; }
     __device__ __forceinline__ void put(int line, int pos, const T (&h)[1], const T (&a)[NA], RedAcc<T>&) const {
@@ -306,22 +304,28 @@ struct Op1a : OpBase<T> {
     }
 };
 
-// 1D pass b (outer c): w_new = H_o E over w, with the residual.
+// 1D pass b (outer c): w_new = Y + H_o E over w, with the residual.
 template <typename T>
 struct Op1b : OpBase<T> {
     static constexpr int NF = 1;
-    static constexpr int NA = 1;
+    static constexpr int NA = 2;
     static constexpr int kAxes = 1;
     static constexpr bool kReduce = true;
     const T* e_in;
+    const T* y_in;
     T* w;
     T shift;
     __device__ __forceinline__ void load(int line, int pos, T (&f)[1]) const { f[0] = e_in[this->at(line, pos)]; }
-    __device__ __forceinline__ void fetch(int line, int pos, T (&a)[NA]) const { a[0] = w[this->at(line, pos)]; }
+    __device__ __forceinline__ void fetch(int line, int pos, T (&a)[NA]) const {
+        const size_t i = this->at(line, pos);
+        a[0] = w[i];
+        a[1] = y_in[i];
+    }
     __device__ __forceinline__ void put(int line, int pos, const T (&h)[1], const T (&a)[NA], RedAcc<T>& r) const {
-        w[this->at(line, pos)] = h[0];
-        r.dmax = fmax(r.dmax, fabs(h[0] - a[0]));
-        r.vmax = fmax(r.vmax, fabs(h[0]));
+        const T nw = a[1] + h[0];
+        w[this->at(line, pos)] = nw;
+        r.dmax = fmax(r.dmax, fabs(nw - a[0]));
+        r.vmax = fmax(r.vmax, fabs(nw));
     }
 };
 
@@ -423,28 +427,28 @@ struct PipeP4 {
     }
 };
 
-// 1D pass a: staged r, w; output E = H_i[r + beta G(w)] - beta G(w)
+// 1D pass a: staged w; output E = H_i[beta G(w)] - beta G(w)
 template <typename T>
 struct Pipe1a {
-    static constexpr int NS = 2, NA = 0, NF = 1, NO = 1;
+    static constexpr int NS = 1, NA = 0, NF = 1, NO = 1;
     static constexpr bool kReduce = false;
     const T* s[NS];
     const T* a[1];
     T* o[NO];
     T g2, g1, beta;
     __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const {
-        f[0] = fma(beta, g_lag(sv[1], g2, g1), sv[0]);
+        f[0] = beta * g_lag(sv[0], g2, g1);
     }
     __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&sv)[NS], const T (&)[1], T (&ov)[NO],
                                              RedAcc<T>&) const {
-        ov[0] = h[0] - beta * g_lag(sv[1], g2, g1);
+        ov[0] = h[0] - beta * g_lag(sv[0], g2, g1);
     }
 };
 
-// 1D pass b: staged E; auxiliary w; output w_new = H_o E (over w)
+// 1D pass b: staged E; auxiliary w, Y; output w_new = Y + H_o E (over w)
 template <typename T>
 struct Pipe1b {
-    static constexpr int NS = 1, NA = 1, NF = 1, NO = 1;
+    static constexpr int NS = 1, NA = 2, NF = 1, NO = 1;
     static constexpr bool kReduce = true;
     const T* s[NS];
     const T* a[NA];
@@ -453,9 +457,10 @@ struct Pipe1b {
     __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const { f[0] = sv[0]; }
     __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&)[NS], const T (&av)[NA], T (&ov)[NO],
                                              RedAcc<T>& r) const {
-        ov[0] = h[0];
-        r.dmax = fmax(r.dmax, fabs(h[0] - av[0]));
-        r.vmax = fmax(r.vmax, fabs(h[0]));
+        const T nw = av[1] + h[0];
+        ov[0] = nw;
+        r.dmax = fmax(r.dmax, fabs(nw - av[0]));
+        r.vmax = fmax(r.vmax, fabs(nw));
     }
 };
 

@@ -24,8 +24,9 @@ EXPORTS = [
     "molt_set_params", "molt_set_bc", "molt_reset_history", "molt_step", "molt_run_host",
     "molt_energy", "molt_mass", "molt_helmholtz_apply", "molt_quadrature_weights",
     "molt_last_error", "molt_kernel_launches", "molt_profile_enable", "molt_profile_collect",
-    "molt_helmholtz_columns_noalloc",
+    "molt_helmholtz_columns_noalloc", "molt_set_execution", "molt_graph_fallbacks",
 ]
+EXECUTION = {"host_loop": 0, "graph": 1}
 PROFILE_SLOTS = 32
 PASS_NAMES = ["H", "pass1", "pass2", "pass3", "pass4", "pass1d_a", "pass1d_b", ""]
 
@@ -82,6 +83,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_profile_enable": ([P, I], I),
         "molt_profile_collect": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)], I),
         "molt_helmholtz_columns_noalloc": ([I, I, D, I, I, D, VP, VP, VP], I),
+        "molt_set_execution": ([P, I], I),
+        "molt_graph_fallbacks": ([P], ctypes.c_longlong),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -208,6 +211,13 @@ class Solver:
     def set_bc(self, bc: str):
         _check(self._lib.molt_set_bc(self._h, BC[bc]), self._h)
         self.bc = bc
+
+    def set_execution(self, mode: str):
+        """'graph' (device-driven stage loops, the default) or 'host_loop'."""
+        _check(self._lib.molt_set_execution(self._h, EXECUTION[mode]), self._h)
+
+    def graph_fallbacks(self) -> int:
+        return int(self._lib.molt_graph_fallbacks(self._h))
 
     def reset_history(self):
         _check(self._lib.molt_reset_history(self._h), self._h)

@@ -263,7 +263,7 @@ def _fp32_bar(ref, bc, rho):
     return max(1e-6 * np.abs(ref + 1).max(), 8 * 2.0 ** -24 * np.abs(w).max() / max(1e-3, 1 - rho))
 
 
-@pytest.mark.parametrize("scheme", ["be", "bdf2", "sdirk2", "sdirk3"])
+@pytest.mark.parametrize("scheme", ["be", "bdf2", "sdirk2", "sdirk3", "sdc2"])
 @pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
 def test_steps_2d_fp64_match_oracle(scheme, bc):
     ny, nx = 72, 96
@@ -305,11 +305,16 @@ def test_1d_neumann_be_matches_oracle(precision):
         assert all(abs(a[0] - b[0]) <= 1 for a, b in zip(ig, ir))
 
 
-def test_1d_periodic_paper_ic_sdirk2():
+@pytest.mark.parametrize("scheme", ["be", "bdf2", "sdirk2", "sdirk3", "sdc2"])
+@pytest.mark.parametrize("dt", [0.025, 0.05])      # square and factorization regimes for SDC2 / BE
+def test_1d_periodic_paper_ic(scheme, dt):
+    # The setting of the paper's refinement tables (M = 6, eps = 0.18, 512 nodes), four steps.
     n = 512
     u0 = paper_ic_1d(n)[None, :]
-    got, ref, _, _ = _run_both(n, 1, "periodic", 0.18, 6, 1e-12, 2000, "sdirk2", 0.025, 4, "fp64", u0)
+    got, ref, ig, ir = _run_both(n, 1, "periodic", 0.18, 6, 1e-12, 3000, scheme, dt, 4, "fp64", u0)
     assert np.abs(got - ref).max() < 1e-10
+    for a, b in zip(ig, ir):
+        assert all(abs(x - y) <= 1 for x, y in zip(a, b)), (ig, ir)
 
 
 def test_run_host_matches_device_path():
@@ -346,3 +351,40 @@ def test_not_converged_and_bad_arguments():
             s.helmholtz_apply(0, -0.01, ud, out)
     with pytest.raises(MoltError):
         _solver(nx=nx, ny=ny, quad_order=3)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("dims,bc,scheme", [((48, 64), "neumann", "sdirk3"), ((300, 96), "periodic", "bdf2"),
+                                            ((1, 256), "neumann", "sdc2"), ((40, 1024), "dirichlet", "be")])
+def test_graph_loop_equals_host_loop(precision, dims, bc, scheme):
+    # The device-driven loop (conditional WHILE graph) launches the same kernels in the same order
+    # as the host-driven loop and applies the same stopping rule, so results are bit-identical.
+    ny, nx = dims
+    u0 = uniform_noise((ny, nx), 0.05, seed=21, mean=0.1)
+    if bc == "dirichlet":
+        u0[0, :] = u0[-1, :] = -1
+        u0[:, 0] = u0[:, -1] = -1
+    results = {}
+    for mode in ("host_loop", "graph"):
+        with _solver(nx=nx, ny=ny, bc=bc, precision=precision, eps=0.1, tol=1e-9, max_iter=400) as s:
+            s.set_execution(mode)
+            u = _dev(u0, precision)
+            iters = [s.step(u, 2e-3, scheme).iters for _ in range(3)]
+            results[mode] = (_host(u), iters, s.graph_fallbacks())
+    assert results["graph"][2] == 0
+    assert results["graph"][1] == results["host_loop"][1]
+    assert np.array_equal(results["graph"][0], results["host_loop"][0])
+
+
+def test_graph_loop_iteration_cap():
+    from paper_1611_04214_gb300.molt import NotConverged
+    ny, nx = 32, 40
+    u0 = uniform_noise((ny, nx), 0.05, seed=1)
+    with _solver(nx=nx, ny=ny, bc="neumann", precision="fp64", eps=0.1, tol=1e-14, max_iter=3) as s:
+        s.set_execution("graph")
+        ud = _dev(u0, "fp64")
+        with pytest.raises(NotConverged):
+            s.step(ud, 1e-3, "be")
+        info = s.step(ud, 1e-3, "be", raise_on_nonconvergence=False)
+        assert info.status == -2 and info.iters == [3]
+        assert s.graph_fallbacks() == 0
