@@ -171,6 +171,41 @@ def _config(args):
             "initial_state": "0.1 + 0.05 N(0,1), SplitMix64 seed 0", "replicas": args.gpus}
 
 
+def fp64_comparison(args, u0, steps: int = 2):
+    """The FP32 path against the plain FP64 single-instance GPU path on the same workload: same
+    initial state, the same steps and fixed-point iterations; device time per step and the largest
+    difference of the fields (absolute, and relative to max|u + 1|)."""
+    import numpy as np
+    import torch
+
+    from paper_1611_04214_gb300.molt import Solver
+    n = WORKLOAD["n"]
+    out = {}
+    fields = {}
+    for prec in ("fp32", "fp64"):
+        s = Solver(nx=n, ny=n, bc=WORKLOAD["bc"], eps=WORKLOAD["eps"], quad_order=WORKLOAD["M"], precision=prec,
+                   tol=1e-6, max_iter=args.iters, Lx=WORKLOAD["L"], Ly=WORKLOAD["L"])
+        u = torch.tensor(u0, dtype=s.dtype, device="cuda")
+        if prec == "fp64":
+            u.copy_(torch.tensor(u0, dtype=torch.float32, device="cuda").double())   # same rounded start
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            s.step(u, WORKLOAD["dt"], WORKLOAD["scheme"], raise_on_nonconvergence=False)
+        e1.record()
+        torch.cuda.synchronize()
+        out[f"{prec}_ms_per_step"] = e0.elapsed_time(e1) / steps
+        fields[prec] = u.double()
+        s.close()
+    diff = (fields["fp32"] - fields["fp64"]).abs().max().item()
+    scale = (fields["fp64"] + 1).abs().max().item()
+    out.update({"steps": steps, "speedup_fp32": out["fp64_ms_per_step"] / out["fp32_ms_per_step"],
+                "max_abs_diff": diff, "max_rel_diff_v": diff / scale})
+    del fields
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -263,6 +298,21 @@ def run_ours(args, rank, world, dist):
             cpu = {"value": p / s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": "one SDIRK3 step of a 512x512 periodic patch of the workload (same h, eps, dt, "
                              f"{args.iters} fixed-point iterations per stage), numpy/scipy FP64, one thread"}
+        # the product default: stage loops as device-driven graphs (no profiling events)
+        solver.set_execution("graph")
+        ug = torch.tensor(u0, dtype=dtype, device="cuda")
+        for _ in range(1):
+            solver.step(ug, WORKLOAD["dt"], WORKLOAD["scheme"], raise_on_nonconvergence=False)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            solver.step(ug, WORKLOAD["dt"], WORKLOAD["scheme"], raise_on_nonconvergence=False)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = g0.elapsed_time(g1) / args.steps
+        del ug
+        fp64 = fp64_comparison(args, u0) if (args.precision == "fp32" and not args.skip_fp64) else None
         last = infos[-1]
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                   "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -271,7 +321,7 @@ def run_ours(args, rank, world, dist):
                   "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(),
                   "ch_steps_per_s": args.steps / (ms * 1e-3), "iters_per_stage": last.iters,
                   "final_residual": last.residual, "hbm_frac_step_algorithmic": hbm_frac_step,
-                  "kernels": kernels}
+                  "ms_per_step_graph_mode": graph_ms, "fp32_vs_fp64": fp64, "kernels": kernels}
     solver.close()
     return result
 
@@ -284,6 +334,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--iters", type=int, default=10, help="fixed-point iterations per stage")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--skip-fp64", action="store_true", help="skip the FP64-path comparison")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
