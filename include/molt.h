@@ -182,6 +182,13 @@ const char* molt_last_error(const molt_solver* solver);
 /* Number of kernels this solver has launched so far (all entry points), for reporting. */
 long long molt_kernel_launches(const molt_solver* solver);
 
+/* Diagnostics (no counterpart in the paper): number of FP32 column-sweep kernels launched with
+ * tensor-memory-accelerator tile loads since the library was loaded, over all solvers and
+ * entry points.  Eligible column sweeps (FP32, lines a multiple of 32, length >= 256, 16-byte
+ * aligned fields) use these kernels unless the environment variable MOLT_COLS_TMA is "0" when
+ * the sweep is launched or captured; both kernel families give bit-identical results. */
+long long molt_column_tma_launches(void);
+
 /* Diagnostic timing (not part of the method; off by default).  While enabled, every sweep
  * kernel launch is bracketed by two CUDA events on its stream. */
 molt_status molt_profile_enable(molt_solver* solver, int enable);

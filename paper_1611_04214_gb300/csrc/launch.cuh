@@ -5,8 +5,11 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
 #include <type_traits>
 
+#include "cols_tma.cuh"
 #include "molt_internal.h"
 #include "sweep_kernels.cuh"
 
@@ -276,6 +279,109 @@ cudaError_t cols_pipe(const LineParams<float>& lp, const P& op, int nlines, ColS
     return e;
 }
 
+// ---- FP32 columns with TMA tile loads (cols_tma.cuh) ----
+// The driver's tensor-map encoder, looked up once through the runtime (no link against libcuda).
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// TMA column kernels are the default for eligible FP32 column sweeps; MOLT_COLS_TMA=0 in the
+// environment at launch (or graph capture) time selects the cp.async kernels instead.  Both
+// evaluate the same operations in the same order, so their results agree bit for bit.
+inline bool cols_tma_enabled() {
+    const char* v = std::getenv("MOLT_COLS_TMA");
+    return !(v && v[0] == '0');
+}
+
+// One map per staged field: an n x nlines row-major FP32 array, box of 32 columns x rows rows.
+template <class P>
+bool col_tma_maps(const P& op, int nlines, int n, int rows, ColMaps* maps) {
+    std::memset(maps, 0, sizeof(*maps));
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    for (int f = 0; f < P::NS; ++f) {
+        const cuuint64_t dims[2] = {static_cast<cuuint64_t>(nlines), static_cast<cuuint64_t>(n)};
+        const cuuint64_t strides[1] = {static_cast<cuuint64_t>(nlines) * sizeof(float)};
+        const cuuint32_t box[2] = {32u, static_cast<cuuint32_t>(rows)};
+        const cuuint32_t estr[2] = {1u, 1u};
+        if (enc(&maps->m[f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(op.s[f]), dims, strides, box,
+                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+inline PackedStencil packed_stencil(const LineParams<float>& lp) {
+    PackedStencil p;
+    std::memset(&p, 0, sizeof(p));
+    for (int o = 0; o < kMaxStencil; ++o) {
+        unsigned bl, br;
+        std::memcpy(&bl, &lp.wl[o], 4);
+        std::memcpy(&br, &lp.wr[o], 4);
+        p.wl[o] = (static_cast<unsigned long long>(bl) << 32) | bl;
+        p.wr[o] = (static_cast<unsigned long long>(br) << 32) | br;
+    }
+    return p;
+}
+
+template <int M, class P, bool kFinal>
+cudaError_t cols_tma_launch(const LineParams<float>& lp, const ColMaps& maps, const PackedStencil& pw, const P& op,
+                            int nlines, int tiles, ColScratch<float>* cs, unsigned long long* red, cudaStream_t st) {
+    constexpr int ROWS = kColR + M;
+    const size_t smem = static_cast<size_t>(3) * P::NS * ROWS * 32 * sizeof(float) + 128;
+    auto kern = cols_tma_kernel<M, P, kFinal>;
+    static int limit = smem_optin(kern);
+    if (limit < 0 || smem > static_cast<size_t>(limit)) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kColWY, smem);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int items = (nlines / 32) * tiles;
+    int grid = sms * per_sm;
+    if (grid > items) grid = items;
+    kern<<<grid, 32 * kColWY, smem, st>>>(lp, maps, pw, op, nlines, static_cast<long long>(nlines), tiles, cs->aggL,
+                                          cs->aggR, cs->carL, cs->carR, cs->status, red);
+    count_tma_launch();
+    return cudaGetLastError();
+}
+
+template <int M, class P>
+cudaError_t cols_tma(const LineParams<float>& lp, const ColMaps& maps, const P& op, int nlines, ColScratch<float>* cs,
+                     unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof, int kind) {
+    const int n = lp.n;
+    const int tiles = (n + kColR - 1) / kColR;
+    if (cs == nullptr || cs->capacity_lines < nlines || cs->capacity_fields < P::NF || cs->tiles < tiles)
+        return cudaErrorInvalidValue;
+    const PackedStencil pw = packed_stencil(lp);
+    prof_begin(prof, 8 + kind, st);
+    cudaError_t e = cols_tma_launch<M, P, false>(lp, maps, pw, op, nlines, tiles, cs, red, st);
+    prof_end(prof, st);
+    if (e != cudaSuccess) return e;
+    const int total = nlines * P::NF;
+    prof_begin(prof, 16, st);
+    cols_carry_kernel<float><<<(total + 127) / 128, 128, 0, st>>>(lp, nlines, P::NF, tiles, kColR, cs->aggL, cs->aggR,
+                                                                 cs->carL, cs->carR);
+    prof_end(prof, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    prof_begin(prof, 17 + kind, st);
+    e = cols_tma_launch<M, P, true>(lp, maps, pw, op, nlines, tiles, cs, red, st);
+    prof_end(prof, st);
+    if (launches) *launches += 2;
+    return e;
+}
+
 template <typename T, class Op>
 cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int nx, int ny, ColScratch<T>* cs,
                      unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof, int kind) {
@@ -307,6 +413,14 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
             using P = typename ColPipeOf<Op>::type;
             const P pop = col_pipe_build<P>(kind, a);
             if (col_pipe_eligible(pop, lp.n, nlines)) {
+                ColMaps maps;
+                if (cols_tma_enabled() && col_tma_maps(pop, nlines, lp.n, kColR + lp.M, &maps)) {
+                    switch (lp.M) {
+                        case 2: return cols_tma<2>(lp, maps, pop, nlines, cs, red, st, launches, prof, kind);
+                        case 4: return cols_tma<4>(lp, maps, pop, nlines, cs, red, st, launches, prof, kind);
+                        case 6: return cols_tma<6>(lp, maps, pop, nlines, cs, red, st, launches, prof, kind);
+                    }
+                }
                 switch (lp.M) {
                     case 2: return cols_pipe<2>(lp, pop, nlines, cs, red, st, launches, prof, kind);
                     case 4: return cols_pipe<4>(lp, pop, nlines, cs, red, st, launches, prof, kind);

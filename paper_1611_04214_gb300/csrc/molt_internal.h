@@ -53,6 +53,9 @@ LineParams<T> cast_line_params(const LineParams<double>& p);
 // Host: record the message molt_last_error(NULL) returns (entry points without a solver).
 void set_abi_error(const char* message);
 
+// Host: count one column kernel launched with TMA tile loads (molt_column_tma_launches).
+void count_tma_launch();
+
 // Host: local quadrature weights of Sec. 3.2 for one stencil (factor 1/2 included).
 bool quadrature_weights(double nu, int M, const int* offsets, int side, double* w);
 
@@ -66,6 +69,7 @@ struct ColScratch {
     int tiles;
     int capacity_lines;   // nlines the buffers were sized for
     int capacity_fields;
+    unsigned* status = nullptr;   // device word: bits set by kernels whose bounded waits ran out
 };
 
 }  // namespace molt

@@ -18,6 +18,7 @@
 //   which is, term by term, Y + M_o^{-1}[beta (M_i^{-1}G - G + D_ix D_iy G)]
 //   + (D_ox D_oy + D_ix D_iy - D_ox D_oy D_ix D_iy) w  (Sec. 5.1 with c_o != c_i).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -39,6 +40,7 @@ struct molt_grid {
 namespace {
 
 thread_local std::string g_last_error = "";
+std::atomic<long long> g_tma_launches{0};
 
 constexpr double kEta2 = 0.29289321881345247560;   // 1 - sqrt(2)/2 (Sec. 4.2)
 
@@ -173,6 +175,8 @@ struct Solver final : molt_solver {
     molt::ColScratch<T> cs{};
     unsigned long long* red = nullptr;       // device [2]
     unsigned long long* red_host = nullptr;  // pinned [2]
+    unsigned* wait_status = nullptr;         // device [1]: set by kernels whose bounded waits ran out
+    unsigned* wait_status_host = nullptr;    // pinned [1]
     double* partials = nullptr;              // device [reduce_blocks]
     double* result = nullptr;                // device [1]
     double* result_host = nullptr;           // pinned [1]
@@ -189,11 +193,18 @@ struct Solver final : molt_solver {
         for (void* a : allocs) cudaFree(a);
         if (red_host) cudaFreeHost(red_host);
         if (result_host) cudaFreeHost(result_host);
+        if (wait_status_host) cudaFreeHost(wait_status_host);
     }
 
     molt_status fail(molt_status s, const std::string& m) {
         err = m;
         return s;
+    }
+    // A column kernel's copy did not complete within its time limit; its outputs are invalid.
+    // The status stays set, so every later step of this solver reports the same error.
+    molt_status wait_timeout() {
+        err = "a device-side wait for a tile copy ran out of time; results of this step are invalid";
+        return MOLT_ERR_CUDA;
     }
     molt_status cuda_fail(cudaError_t e, const char* where) {
         err = std::string(where) + ": " + cudaGetErrorString(e);
@@ -224,10 +235,16 @@ struct Solver final : molt_solver {
             !alloc(&red, 2) || !alloc(&partials, static_cast<size_t>(molt::reduce_blocks())) || !alloc(&result, 1))
             return fail(MOLT_ERR_OOM, "device scratch allocation failed");
         if (!alloc(&ls, 1)) return fail(MOLT_ERR_OOM, "device loop state allocation failed");
+        if (!alloc(&wait_status, 1)) return fail(MOLT_ERR_OOM, "device status allocation failed");
+        if (cudaMemset(wait_status, 0, sizeof(unsigned)) != cudaSuccess)
+            return fail(MOLT_ERR_CUDA, "device status initialisation failed");
+        cs.status = wait_status;
         if (cudaMallocHost(&red_host, 2 * sizeof(unsigned long long)) != cudaSuccess ||
             cudaMallocHost(&result_host, sizeof(double)) != cudaSuccess ||
-            cudaMallocHost(&ls_host, sizeof(molt::LoopState)) != cudaSuccess)
+            cudaMallocHost(&ls_host, sizeof(molt::LoopState)) != cudaSuccess ||
+            cudaMallocHost(&wait_status_host, sizeof(unsigned)) != cudaSuccess)
             return fail(MOLT_ERR_OOM, "pinned host allocation failed");
+        *wait_status_host = 0;
         return MOLT_OK;
     }
 
@@ -451,7 +468,11 @@ struct Solver final : molt_solver {
                 if ((e = cudaMemcpyAsync(ls_host, ls, sizeof(molt::LoopState), cudaMemcpyDeviceToHost, st)) !=
                     cudaSuccess)
                     return cuda_fail(e, "loop state copy");
+                if ((e = cudaMemcpyAsync(wait_status_host, wait_status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                         st)) != cudaSuccess)
+                    return cuda_fail(e, "status copy");
                 if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream sync");
+                if (*wait_status_host) return wait_timeout();
                 launches += 1 + static_cast<long long>(ls_host->k) * lg->kernels_per_iter;
                 *iters = ls_host->k;
                 *res_out = ls_host->res;
@@ -470,7 +491,11 @@ struct Solver final : molt_solver {
             if ((e = cudaMemcpyAsync(red_host, red, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) !=
                 cudaSuccess)
                 return cuda_fail(e, "residual copy");
+            if ((e = cudaMemcpyAsync(wait_status_host, wait_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess)
+                return cuda_fail(e, "status copy");
             if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream sync");
+            if (*wait_status_host) return wait_timeout();
             double dmax, wmax;
             std::memcpy(&dmax, &red_host[0], sizeof(double));
             std::memcpy(&wmax, &red_host[1], sizeof(double));
@@ -709,6 +734,7 @@ molt_status set_global_error(molt_status s, const char* m) {
 }  // namespace
 
 void molt::set_abi_error(const char* message) { g_last_error = message ? message : ""; }
+void molt::count_tma_launch() { g_tma_launches.fetch_add(1); }
 
 extern "C" {
 
@@ -843,6 +869,8 @@ const char* molt_last_error(const molt_solver* s) {
 }
 
 long long molt_kernel_launches(const molt_solver* s) { return s ? s->launches : 0; }
+
+long long molt_column_tma_launches(void) { return g_tma_launches.load(); }
 
 molt_status molt_profile_enable(molt_solver* s, int enable) {
     if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");

@@ -25,6 +25,7 @@ EXPORTS = [
     "molt_energy", "molt_mass", "molt_helmholtz_apply", "molt_quadrature_weights",
     "molt_last_error", "molt_kernel_launches", "molt_profile_enable", "molt_profile_collect",
     "molt_helmholtz_columns_noalloc", "molt_set_execution", "molt_graph_fallbacks",
+    "molt_column_tma_launches",
 ]
 EXECUTION = {"host_loop": 0, "graph": 1}
 PROFILE_SLOTS = 32
@@ -85,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_helmholtz_columns_noalloc": ([I, I, D, I, I, D, VP, VP, VP], I),
         "molt_set_execution": ([P, I], I),
         "molt_graph_fallbacks": ([P], ctypes.c_longlong),
+        "molt_column_tma_launches": ([], ctypes.c_longlong),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -122,6 +124,11 @@ def molt_helmholtz_columns_noalloc(nx: int, ny: int, Ly: float, bc: str, quad_or
     _check(lib.molt_helmholtz_columns_noalloc(int(nx), int(ny), float(Ly), BC[bc], int(quad_order), float(c),
                                               ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                               _stream_handle(stream)))
+
+
+def molt_column_tma_launches() -> int:
+    """Column-sweep kernels launched with TMA tile loads since the library was loaded (diagnostics)."""
+    return int(load_library().molt_column_tma_launches())
 
 
 def _stream_handle(stream):
