@@ -176,6 +176,50 @@ molt_status molt_quadrature_weights(double nu, int M, const int* offsets, int si
 molt_status molt_helmholtz_columns_noalloc(int nx, int ny, double Ly, int bc, int quad_order, double c,
                                            const float* in_dev, float* out_dev, void* stream);
 
+/* ---- Batched instances ----------------------------------------------------------------
+ * Many independent 2D problems, each with its own grid size, eps and time step, stepped
+ * together in FP32.  Every instance follows Sec. 2-5 exactly as molt_step does (stage
+ * coefficients of Sec. 2.2 / 2.3 from its own tau and eps, the 2D fixed-point iteration of
+ * Sec. 5, the stopping rule documented at molt_params).  Each pass of the stage solve is one
+ * launch over all instances.  Errors of the batch calls are reported by molt_last_error(NULL). */
+typedef struct molt_batch molt_batch;
+
+typedef struct {
+    int nx, ny;      /* grid nodes of the instance, each in [quad_order + 2, 1024] */
+    double Lx, Ly;   /* domain lengths (> 0) */
+    double eps;      /* interface parameter (> 0) */
+} molt_instance;
+
+/* Create a batch of `count` >= 1 instances sharing the boundary condition, the quadrature
+ * order M (2, 4 or 6), the fixed-point tolerance and max_iter.  The batch owns its device
+ * workspace (ten packed fields plus scan scratch).  A packed field stores the instances back to
+ * back: instance i occupies ny_i * nx_i floats, row-major with x fastest, from
+ * molt_batch_offsets()[i].  Errors: MOLT_ERR_ARG, MOLT_ERR_OOM, MOLT_ERR_CUDA. */
+molt_status molt_batch_create(molt_batch** batch, int count, const molt_instance* instances, molt_bc bc,
+                              int quad_order, double tol, int max_iter);
+molt_status molt_batch_destroy(molt_batch* batch);
+
+/* Floats in one packed field (sum of ny_i * nx_i); 0 for NULL. */
+long long molt_batch_points(const molt_batch* batch);
+
+/* Offsets (in floats) of the `count` instances in a packed field. */
+molt_status molt_batch_offsets(const molt_batch* batch, long long* offsets);
+
+/* Graph (default) or host-driven stage loop; both give bit-identical fields. */
+molt_status molt_batch_set_execution(molt_batch* batch, molt_execution mode);
+
+/* One time step of every instance, in place on the packed device field u_dev (FP32, u of the
+ * paper).  dt: host array of `count` steps (> 0).  scheme: MOLT_BE or MOLT_BDF2 (BDF2 starts
+ * with one BE step, again whenever any dt changes).  The step's stage (rhs inverse and the
+ * fixed-point loop) runs as one CUDA graph with a conditional WHILE node; each instance stops
+ * on its own rule and skips later iterations.  iters / residual / status: host arrays of
+ * `count` entries (each may be NULL) receiving each instance's iterations, last residual
+ * max|w_new - w| and MOLT_OK or MOLT_ERR_NOT_CONVERGED.  Returns MOLT_ERR_NOT_CONVERGED when any
+ * instance reached max_iter (the fields hold the last iterates), MOLT_ERR_UNSUPPORTED for other
+ * schemes, MOLT_ERR_ARG, MOLT_ERR_CUDA. */
+molt_status molt_batch_step(molt_batch* batch, float* u_dev, const double* dt, molt_scheme scheme, void* stream,
+                            int* iters, double* residual, int* status);
+
 /* Last error message of `solver` (or of the last failed create/ABI call when NULL). */
 const char* molt_last_error(const molt_solver* solver);
 

@@ -56,6 +56,18 @@ void set_abi_error(const char* message);
 // Host: count one column kernel launched with TMA tile loads (molt_column_tma_launches).
 void count_tma_launch();
 
+// Host: coefficients of the stage equation v - tau F(v) = r (Sec. 2.2 factorization when
+// tau >= eps^2, Sec. 2.3 completed square otherwise): the two Helmholtz parameters (inner = the
+// larger), beta = tau / c_in and lambda = 2 - (c1 + c2) / tau of the lagged term G.
+struct StageParams {
+    bool factor;
+    double c_in, c_out, beta, lam;
+};
+StageParams stage_params(double tau, double eps);
+
+// Host: node spacing of a line of n stored nodes over a length L (periodic: L / n).
+double grid_h(int n, double L, int bc);
+
 // Host: local quadrature weights of Sec. 3.2 for one stencil (factor 1/2 included).
 bool quadrature_weights(double nu, int M, const int* offsets, int side, double* w);
 

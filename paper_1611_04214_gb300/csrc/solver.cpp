@@ -56,12 +56,9 @@ double alexander_eta() {
     return 0.5 * (lo + hi);
 }
 
-struct StageParams {
-    bool factor;
-    double c_in, c_out, beta, lam;
-};
+}  // namespace
 
-StageParams stage_params(double tau, double eps) {
+molt::StageParams molt::stage_params(double tau, double eps) {
     StageParams sp;
     double c1, c2;
     if (tau >= eps * eps) {
@@ -80,7 +77,13 @@ StageParams stage_params(double tau, double eps) {
     return sp;
 }
 
-double grid_h(int n, double L, int bc) { return bc == molt::BC_PERIODIC ? L / n : L / (n - 1); }
+double molt::grid_h(int n, double L, int bc) { return bc == molt::BC_PERIODIC ? L / n : L / (n - 1); }
+
+namespace {
+
+using molt::StageParams;
+using molt::grid_h;
+using molt::stage_params;
 
 }  // namespace
 

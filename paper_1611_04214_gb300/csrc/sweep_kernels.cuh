@@ -12,14 +12,13 @@ namespace molt {
 // Shared layout: [line in block][field][position + position/32] (the pad keeps the chunked
 // per-thread reads free of bank conflicts).
 // =========================================================================================
+// Body of one block: lines line0 .. line0 + lpb - 1 of nlines; sm = the block's dynamic shared
+// memory (lpb * NF * pitch values).  Shared by rows_kernel and the batched row kernel.
 template <typename T, int M, int K, class Op>
-__global__ void __launch_bounds__(1024)
-rows_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, int tl_log2, int lpb,
-            int pitch, unsigned long long* red_slots) {
+__device__ __forceinline__ void rows_body(const LineParams<T>& lp, const Op& op, int nlines, int tl_log2, int lpb,
+                                          int pitch, int line0, T* sm, unsigned long long* red_slots) {
     constexpr int NF = Op::NF;
     constexpr int H = M / 2;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T* sm = reinterpret_cast<T*>(smraw);
     __shared__ T s_scan[32][2 + 2 * NF];   // per-warp segments: D_f, D_b, A_f[NF], A_b[NF]
     __shared__ T s_tot[32][2 * NF];        // per-line totals (lines spanning several warps)
     __shared__ T s_bnd[128][2 * NF];       // per-line carries / B values from the FP64 solve
@@ -30,7 +29,6 @@ rows_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, i
     const int tid = threadIdx.x;
     const int lib = tid >> tl_log2;
     const int t = tid & (TL - 1);
-    const int line0 = blockIdx.x * lpb;
 
     // ---- stage the block's lines (prologue): batches of U independent loads per thread ----
     constexpr int U = 8;
@@ -294,6 +292,15 @@ rows_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, i
         }
     }
     if (Op::kReduce) block_reduce_store<T>(red, red_slots);
+}
+
+template <typename T, int M, int K, class Op>
+__global__ void __launch_bounds__(1024)
+rows_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, int tl_log2, int lpb,
+            int pitch, unsigned long long* red_slots) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    rows_body<T, M, K, Op>(lp, op, nlines, tl_log2, lpb, pitch, static_cast<int>(blockIdx.x) * lpb,
+                           reinterpret_cast<T*>(smraw), red_slots);
 }
 
 // =========================================================================================
@@ -895,17 +902,17 @@ __device__ __forceinline__ void col_chunk(const LineParams<T>& lp, const Op& op,
     }
 }
 
+// Body of one block (32 x WY threads): tile `tile` of the strip of 32 lines from strip*32.
 template <typename T, int M, int KY, int WY, class Op>
-__global__ void __launch_bounds__(32 * WY)
-cols_agg_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, T* aggL, T* aggR, int tiles) {
+__device__ __forceinline__ void cols_agg_body(const LineParams<T>& lp, const Op& op, int nlines, T* aggL, T* aggR,
+                                              int tiles, int strip, int tile) {
     constexpr int NF = Op::NF;
     constexpr int R = WY * KY;
     __shared__ T sD[WY][32];
     __shared__ T sL[NF][WY][32];
     __shared__ T sR[NF][WY][32];
     const int lane = threadIdx.x, wy = threadIdx.y;
-    const int line = blockIdx.x * 32 + lane;
-    const int tile = blockIdx.y;
+    const int line = strip * 32 + lane;
     const int start = tile * R + wy * KY;
     int cnt = lp.n - start;
     cnt = cnt < 0 ? 0 : (cnt > KY ? KY : cnt);
@@ -938,15 +945,20 @@ cols_agg_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nline
     }
 }
 
+template <typename T, int M, int KY, int WY, class Op>
+__global__ void __launch_bounds__(32 * WY)
+cols_agg_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, T* aggL, T* aggR, int tiles) {
+    cols_agg_body<T, M, KY, WY, Op>(lp, op, nlines, aggL, aggR, tiles, blockIdx.x, blockIdx.y);
+}
+
 // One thread per (field, column): scan the tile segments, solve the boundary system in FP64,
 // and write the carry entering each tile (or, for walls, the B value injected at the end node).
 // The tile recurrences run in the kernel precision (FP64 throughput on this part is a small
 // fraction of FP32), with the decays as products of two constants (full tile, last tile).
 template <typename T>
-__global__ void cols_carry_kernel(const __grid_constant__ LineParams<T> lp, int nlines, int nf, int tiles,
-                                  int R, const T* __restrict__ aggL, const T* __restrict__ aggR,
-                                  T* __restrict__ carL, T* __restrict__ carR) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void carry_body(const LineParams<T>& lp, int nlines, int nf, int tiles, int R,
+                                          const T* __restrict__ aggL, const T* __restrict__ aggR,
+                                          T* __restrict__ carL, T* __restrict__ carR, int idx) {
     if (idx >= nlines * nf) return;
     const int q = idx / nlines, line = idx % nlines;
     const int n = lp.n;
@@ -1001,18 +1013,24 @@ __global__ void cols_carry_kernel(const __grid_constant__ LineParams<T> lp, int 
     }
 }
 
+template <typename T>
+__global__ void cols_carry_kernel(const __grid_constant__ LineParams<T> lp, int nlines, int nf, int tiles,
+                                  int R, const T* __restrict__ aggL, const T* __restrict__ aggR,
+                                  T* __restrict__ carL, T* __restrict__ carR) {
+    carry_body<T>(lp, nlines, nf, tiles, R, aggL, aggR, carL, carR, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 template <typename T, int M, int KY, int WY, class Op>
-__global__ void __launch_bounds__(32 * WY)
-cols_final_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, const T* carL,
-                  const T* carR, int tiles, unsigned long long* red_slots) {
+__device__ __forceinline__ void cols_final_body(const LineParams<T>& lp, const Op& op, int nlines, const T* carL,
+                                                const T* carR, int tiles, int strip, int tile,
+                                                unsigned long long* red_slots) {
     constexpr int NF = Op::NF;
     constexpr int R = WY * KY;
     __shared__ T sD[WY][32];
     __shared__ T sL[NF][WY][32];
     __shared__ T sR[NF][WY][32];
     const int lane = threadIdx.x, wy = threadIdx.y;
-    const int line = blockIdx.x * 32 + lane;
-    const int tile = blockIdx.y;
+    const int line = strip * 32 + lane;
     const int n = lp.n;
     const bool periodic = lp.bc == BC_PERIODIC;
     const int start = tile * R + wy * KY;
@@ -1080,6 +1098,13 @@ cols_final_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nli
         }
     }
     if (Op::kReduce) block_reduce_store<T>(red, red_slots);
+}
+
+template <typename T, int M, int KY, int WY, class Op>
+__global__ void __launch_bounds__(32 * WY)
+cols_final_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, const T* carL,
+                  const T* carR, int tiles, unsigned long long* red_slots) {
+    cols_final_body<T, M, KY, WY, Op>(lp, op, nlines, carL, carR, tiles, blockIdx.x, blockIdx.y, red_slots);
 }
 
 }  // namespace molt

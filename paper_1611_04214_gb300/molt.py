@@ -25,7 +25,8 @@ EXPORTS = [
     "molt_energy", "molt_mass", "molt_helmholtz_apply", "molt_quadrature_weights",
     "molt_last_error", "molt_kernel_launches", "molt_profile_enable", "molt_profile_collect",
     "molt_helmholtz_columns_noalloc", "molt_set_execution", "molt_graph_fallbacks",
-    "molt_column_tma_launches",
+    "molt_column_tma_launches", "molt_batch_create", "molt_batch_destroy", "molt_batch_points",
+    "molt_batch_offsets", "molt_batch_set_execution", "molt_batch_step",
 ]
 EXECUTION = {"host_loop": 0, "graph": 1}
 PROFILE_SLOTS = 32
@@ -87,6 +88,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_set_execution": ([P, I], I),
         "molt_graph_fallbacks": ([P], ctypes.c_longlong),
         "molt_column_tma_launches": ([], ctypes.c_longlong),
+        "molt_batch_create": ([ctypes.POINTER(VP), I, VP, I, I, D, I], I),
+        "molt_batch_destroy": ([VP], I),
+        "molt_batch_points": ([VP], ctypes.c_longlong),
+        "molt_batch_offsets": ([VP, ctypes.POINTER(ctypes.c_longlong)], I),
+        "molt_batch_set_execution": ([VP, I], I),
+        "molt_batch_step": ([VP, VP, ctypes.POINTER(D), I, VP, ctypes.POINTER(I), ctypes.POINTER(D),
+                             ctypes.POINTER(I)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -292,3 +300,86 @@ class Solver:
                 name = f"cols_final_{PASS_NAMES[slot - 17]}"
             out[name] = (ms[slot], int(cnt[slot]))
         return out
+
+
+class _Instance(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("Lx", ctypes.c_double), ("Ly", ctypes.c_double),
+                ("eps", ctypes.c_double)]
+
+
+@dataclass
+class BatchStepInfo:
+    status: int
+    iters: list
+    residual: list
+    instance_status: list
+
+
+class Batch:
+    """Independent 2D FP32 instances stepped together (molt_batch_*): one packed device field holds
+    every instance back to back; `offsets[i]` is where instance i (ny_i x nx_i, x fastest) starts."""
+
+    def __init__(self, instances, bc: str = "neumann", quad_order: int = 4, tol: float = 1e-6,
+                 max_iter: int = 200):
+        """instances: sequence of (nx, ny, Lx, Ly, eps)."""
+        lib = load_library()
+        self._lib = lib
+        self.count = len(instances)
+        arr = (_Instance * self.count)(*[_Instance(int(a), int(b), float(c), float(d), float(e))
+                                         for (a, b, c, d, e) in instances])
+        self.shapes = [(int(b), int(a)) for (a, b, _, _, _) in instances]
+        h = ctypes.c_void_p()
+        _check(lib.molt_batch_create(ctypes.byref(h), self.count, ctypes.cast(arr, ctypes.c_void_p), BC[bc],
+                                     int(quad_order), float(tol), int(max_iter)))
+        self._h = h
+        self.points = int(lib.molt_batch_points(h))
+        offs = (ctypes.c_longlong * self.count)()
+        _check(lib.molt_batch_offsets(h, offs))
+        self.offsets = [int(o) for o in offs]
+
+    def set_execution(self, mode: str):
+        _check(self._lib.molt_batch_set_execution(self._h, EXECUTION[mode]))
+
+    def pack(self, fields):
+        """Host arrays (one per instance, shape (ny, nx)) -> one packed float32 numpy array."""
+        import numpy as np
+        out = np.empty(self.points, dtype=np.float32)
+        for (ny, nx), o, f in zip(self.shapes, self.offsets, fields):
+            out[o:o + ny * nx] = np.asarray(f, dtype=np.float32).reshape(-1)
+        return out
+
+    def unpack(self, packed):
+        """Packed array (numpy or CPU tensor) -> list of (ny, nx) arrays."""
+        return [packed[o:o + ny * nx].reshape(ny, nx) for (ny, nx), o in zip(self.shapes, self.offsets)]
+
+    def step(self, u, dt, scheme: str = "be", stream=None, raise_on_nonconvergence: bool = True) -> BatchStepInfo:
+        """One step of every instance in place on the packed CUDA float32 tensor u; dt: per instance."""
+        if not u.is_cuda or u.dtype.itemsize != 4 or not u.is_contiguous() or u.numel() != self.points:
+            raise ValueError("expected the packed contiguous CUDA float32 field of the batch")
+        dts = (ctypes.c_double * self.count)(*[float(x) for x in dt])
+        it = (ctypes.c_int * self.count)()
+        res = (ctypes.c_double * self.count)()
+        sts = (ctypes.c_int * self.count)()
+        status = self._lib.molt_batch_step(self._h, ctypes.c_void_p(u.data_ptr()), dts, SCHEME[scheme],
+                                           _stream_handle(stream), it, res, sts)
+        info = BatchStepInfo(status, list(it), list(res), list(sts))
+        if status != MOLT_OK and (status != MOLT_ERR_NOT_CONVERGED or raise_on_nonconvergence):
+            _check(status, None)
+        return info
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.molt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,135 @@
+"""GPU: batched instances (molt_batch_*) against the single-instance solver and the oracle.
+
+For instances whose rows are shorter than 1024 nodes and whose columns are shorter than 256, the
+single-instance solver runs the same general row / column block bodies, the same stopping rule
+and the same pointwise kernels as the batched passes, so every instance of a batch must match a
+single-instance run of the same problem bit for bit, iteration counts included.  The oracle
+bounds both with the FP32 fixed-point bar of test_gpu_parity.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle.solver import OracleSolver, Problem  # noqa: E402
+from paper_1611_04214_gb300.inputs import uniform_noise  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_04214_gb300 import build
+    build.build_library()
+
+
+# (nx, ny, Lx, Ly, eps, dt): square and factorization regimes, uneven sizes and aspect ratios
+INSTANCES = [
+    (40, 56, 2 * np.pi, 2 * np.pi, 0.10, 2e-3),
+    (96, 72, 3.0, 2.0, 0.06, 1e-3),
+    (48, 128, 2 * np.pi, 4.0, 0.15, 5e-3),
+    (33, 40, 1.5, 1.9, 0.08, 8e-4),
+    (64, 24, 2.0, 1.0, 0.05, 3e-3),      # tau >= eps^2: factorization regime
+]
+
+
+def _initial(bc, seed, nx, ny):
+    u = uniform_noise((ny, nx), 0.05, seed=seed, mean=0.0)
+    if bc == "dirichlet":
+        u[0, :] = u[-1, :] = -1
+        u[:, 0] = u[:, -1] = -1
+    return u.astype(np.float32)
+
+
+def _run_batch(bc, scheme, steps, mode="graph", tol=1e-6, max_iter=300):
+    from paper_1611_04214_gb300.molt import Batch
+    inst = [(nx, ny, Lx, Ly, eps) for (nx, ny, Lx, Ly, eps, _) in INSTANCES]
+    dts = [dt for (*_, dt) in INSTANCES]
+    with Batch(inst, bc=bc, quad_order=4, tol=tol, max_iter=max_iter) as b:
+        b.set_execution(mode)
+        u0 = [_initial(bc, 10 + i, nx, ny) for i, (nx, ny, *_rest) in enumerate(INSTANCES)]
+        u = torch.tensor(b.pack(u0), device="cuda")
+        infos = [b.step(u, dts, scheme, raise_on_nonconvergence=False) for _ in range(steps)]
+        torch.cuda.synchronize()
+        out = b.unpack(u.cpu().numpy())
+    return u0, out, infos
+
+
+def _run_single(bc, scheme, steps, i, u0, tol=1e-6, max_iter=300):
+    from paper_1611_04214_gb300.molt import Solver
+    nx, ny, Lx, Ly, eps, dt = INSTANCES[i]
+    with Solver(nx=nx, ny=ny, Lx=Lx, Ly=Ly, bc=bc, eps=eps, quad_order=4, precision="fp32", tol=tol,
+                max_iter=max_iter) as s:
+        u = torch.tensor(u0, device="cuda")
+        infos = [s.step(u, dt, scheme, raise_on_nonconvergence=False) for _ in range(steps)]
+        torch.cuda.synchronize()
+        return u.cpu().numpy(), [inf.iters[0] for inf in infos], [inf.status for inf in infos]
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+@pytest.mark.parametrize("scheme,steps", [("be", 2), ("bdf2", 3)])
+def test_batch_equals_single_instance_bitwise(bc, scheme, steps):
+    u0, out, infos = _run_batch(bc, scheme, steps)
+    for i in range(len(INSTANCES)):
+        ref, iters, status = _run_single(bc, scheme, steps, i, u0[i])
+        assert [inf.iters[i] for inf in infos] == iters, (i, iters)
+        assert [inf.instance_status[i] for inf in infos] == status, (i, status)
+        assert np.array_equal(out[i], ref), (i, np.abs(out[i] - ref).max())
+
+
+@pytest.mark.parametrize("bc", ["neumann", "dirichlet"])
+def test_batch_graph_equals_host_loop(bc):
+    _, a, ia = _run_batch(bc, "bdf2", 3, mode="graph")
+    _, b, ib = _run_batch(bc, "bdf2", 3, mode="host_loop")
+    assert [x.iters for x in ia] == [x.iters for x in ib]
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def _posteriori_bar(ref, bc, rho, residuals):
+    """Error bound of a converged FP32 step sequence against the FP64 fixed points.  For a
+    contraction with factor rho, an iterate whose last change was res lies within
+    (rho res + delta) / (1 - rho) of the fixed point, delta the rounding of one evaluation of the
+    map (a few ulp of max|w|, w = u or u + 1 on Dirichlet grids); the steps' errors add up.
+    Never below the 1e-6 relative target on v = u + 1."""
+    w = ref if bc != "dirichlet" else ref + 1
+    ulp = 2.0 ** -24 * np.abs(w).max()
+    bound = sum((rho * r + 8 * ulp) / max(1e-3, 1 - rho) for r in residuals)
+    return max(1e-6 * np.abs(ref + 1).max(), bound)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+def test_batch_matches_oracle(bc):
+    u0, out, infos = _run_batch(bc, "be", 2, tol=1e-10, max_iter=3000)
+    for i in (0, 3, 4):
+        nx, ny, Lx, Ly, eps, dt = INSTANCES[i]
+        prob = Problem(nx=nx, ny=ny, Lx=Lx, Ly=Ly, bc=bc, eps=eps, M=4, tol=1e-11, max_iter=3000)
+        o = OracleSolver(prob)
+        u = u0[i].astype(np.float64)
+        rho = 0.0
+        for _ in range(2):
+            u, info = o.step(u, dt, "be")
+            rho = max(rho, info.contraction)
+        err = np.abs(out[i] - u).max()
+        bar = _posteriori_bar(u, bc, rho, [inf.residual[i] for inf in infos])
+        assert err <= bar, (i, err, bar, rho, [inf.residual[i] for inf in infos])
+
+
+def test_batch_arguments_and_status():
+    from paper_1611_04214_gb300.molt import Batch, MoltError, NotConverged
+    with pytest.raises(MoltError):
+        Batch([(2048, 64, 1.0, 1.0, 0.1)])
+    with pytest.raises(MoltError):
+        Batch([(64, 64, 1.0, 1.0, -0.1)])
+    with Batch([(64, 48, 2.0, 2.0, 0.05), (40, 40, 2.0, 2.0, 0.1)], bc="neumann", tol=1e-12, max_iter=3) as b:
+        u = torch.tensor(b.pack([_initial("neumann", 1, 64, 48), _initial("neumann", 2, 40, 40)]), device="cuda")
+        with pytest.raises(MoltError):
+            b.step(u, [1e-3, 1e-3], "sdirk3")
+        with pytest.raises(MoltError):
+            b.step(u, [1e-3, -1.0], "be")
+        with pytest.raises(NotConverged):
+            b.step(u, [1e-3, 1e-3], "be")
+        info = b.step(u, [1e-3, 1e-3], "be", raise_on_nonconvergence=False)
+        assert info.iters == [3, 3] and all(s != 0 for s in info.instance_status)
