@@ -207,6 +207,94 @@ def fp64_comparison(args, u0, steps: int = 2):
     return out
 
 
+BATCH = dict(name="batch512_neumann_be", count=512, sides=(128, 256, 384, 512, 768, 1024), eps=(0.02, 0.1),
+             dt=(1e-5, 1e-3), bc="neumann", scheme="be", M=4, tol=1e-6, amp=0.05, seed=0)
+
+
+def batched_leg(args, sample: int = 16):
+    """The batched workload: 512 independent 2D instances (sides uniform over {128..1024}, eps
+    uniform in [0.02, 0.1], dt uniform in [1e-5, 1e-3], Neumann, u0 = 0.05 U[-1,1] per instance)
+    advanced by one batched BE step per call, FP32.  Throughput in line-sweep points per second
+    over the whole batch; then the first `sample` instances against the plain FP64 single-instance
+    GPU path from the same rounded start: device time and field difference after one step."""
+    import numpy as np
+    import torch
+
+    from paper_1611_04214_gb300.inputs import uniform_noise
+    from paper_1611_04214_gb300.molt import Batch, Solver
+    rng = np.random.default_rng(BATCH["seed"])
+    n = BATCH["count"]
+    sides = rng.choice(BATCH["sides"], size=n)
+    eps = rng.uniform(*BATCH["eps"], size=n)
+    dts = rng.uniform(*BATCH["dt"], size=n)
+    L = 2 * np.pi
+    u0 = [uniform_noise((int(s), int(s)), BATCH["amp"], seed=i).astype(np.float32) for i, s in enumerate(sides)]
+
+    def sweep_points(iters, idx):
+        return float(sum((SWEEPS_RHS + SWEEPS_ITER * k) * float(sides[i]) ** 2 for k, i in zip(iters, idx)))
+
+    out = {"workload": BATCH["name"], "instances": n, "points": int(sum(int(s) ** 2 for s in sides)),
+           "fixed_point": {"tol": BATCH["tol"], "max_iter": args.batch_iters}}
+    with Batch([(int(s), int(s), L, L, float(e)) for s, e in zip(sides, eps)], bc=BATCH["bc"], quad_order=BATCH["M"],
+               tol=BATCH["tol"], max_iter=args.batch_iters) as b:
+        u = torch.tensor(b.pack(u0), device="cuda")
+        b.step(u, dts, "be", raise_on_nonconvergence=False)          # warm-up (builds the graph)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps, pts, infos = 3, 0.0, []
+        e0.record()
+        for _ in range(steps):
+            info = b.step(u, dts, "be", raise_on_nonconvergence=False)
+            infos.append(info)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        pts = sum(sweep_points(inf.iters, range(n)) for inf in infos) / steps
+        it = np.array(infos[-1].iters)
+        out.update({"ms_per_step": ms, "gpts_per_s": pts / (ms * 1e-3) / 1e9,
+                    "instance_steps_per_s": n / (ms * 1e-3),
+                    "iters_min_median_max": [int(it.min()), float(np.median(it)), int(it.max())],
+                    "instances_converged": int(sum(1 for s_ in infos[-1].instance_status if s_ == 0))})
+        del u
+    # the FP64 single-instance GPU path on the first `sample` instances, one at a time
+    idx = list(range(sample))
+    with Batch([(int(sides[i]), int(sides[i]), L, L, float(eps[i])) for i in idx], bc=BATCH["bc"],
+               quad_order=BATCH["M"], tol=BATCH["tol"], max_iter=args.batch_iters) as b:
+        u = torch.tensor(b.pack([u0[i] for i in idx]), device="cuda")
+        b.step(u, dts[:sample], "be", raise_on_nonconvergence=False)     # warm-up
+        u = torch.tensor(b.pack([u0[i] for i in idx]), device="cuda")
+        torch.cuda.synchronize()
+        e0.record()
+        binfo = b.step(u, dts[:sample], "be", raise_on_nonconvergence=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1)
+        got = b.unpack(u.cpu().numpy())
+        del u
+    ms64, diff, scale = 0.0, 0.0, 0.0
+    for j, i in enumerate(idx):
+        s_ = int(sides[i])
+        with Solver(nx=s_, ny=s_, Lx=L, Ly=L, bc=BATCH["bc"], eps=float(eps[i]), quad_order=BATCH["M"],
+                    precision="fp64", tol=BATCH["tol"], max_iter=args.batch_iters) as s64:
+            v = torch.tensor(u0[i].astype(np.float64), device="cuda")
+            s64.step(v.clone(), float(dts[i]), "be", raise_on_nonconvergence=False)   # warm-up
+            torch.cuda.synchronize()
+            e0.record()
+            s64.step(v, float(dts[i]), "be", raise_on_nonconvergence=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms64 += e0.elapsed_time(e1)
+            ref = v.cpu().numpy()
+        diff = max(diff, float(np.abs(got[j] - ref).max()))
+        scale = max(scale, float(np.abs(ref + 1).max()))
+    out["vs_fp64_single_instance"] = {
+        "instances": sample, "fp32_batched_ms": ms32, "fp64_single_ms_sum": ms64, "speedup": ms64 / ms32,
+        "max_abs_diff": diff, "max_rel_diff_v": diff / scale,
+        "iters_fp32_batched": binfo.iters}
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -314,6 +402,7 @@ def run_ours(args, rank, world, dist):
         graph_ms = g0.elapsed_time(g1) / args.steps
         del ug
         fp64 = fp64_comparison(args, u0) if (args.precision == "fp32" and not args.skip_fp64) else None
+        batched = None if args.skip_batch else batched_leg(args)
         last = infos[-1]
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                   "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -322,7 +411,8 @@ def run_ours(args, rank, world, dist):
                   "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(),
                   "ch_steps_per_s": args.steps / (ms * 1e-3), "iters_per_stage": last.iters,
                   "final_residual": last.residual, "hbm_frac_step_algorithmic": hbm_frac_step,
-                  "ms_per_step_graph_mode": graph_ms, "fp32_vs_fp64": fp64, "kernels": kernels}
+                  "ms_per_step_graph_mode": graph_ms, "fp32_vs_fp64": fp64, "batched": batched,
+                  "kernels": kernels}
     solver.close()
     return result
 
@@ -336,6 +426,8 @@ def main():
     ap.add_argument("--iters", type=int, default=10, help="fixed-point iterations per stage")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--skip-fp64", action="store_true", help="skip the FP64-path comparison")
+    ap.add_argument("--skip-batch", action="store_true", help="skip the batched-instances leg")
+    ap.add_argument("--batch-iters", type=int, default=40, help="fixed-point iteration cap of the batched leg")
     ap.add_argument("--grid", type=int, default=WORKLOAD["n"],
                     help="grid points per side (default: the 8192^2 workload; smaller sizes are for profiling)")
     args = ap.parse_args()
