@@ -19,52 +19,6 @@
 
 namespace molt {
 
-// ---- packed FP32 pairs -------------------------------------------------------------------
-template <int NF> struct Lanes;
-template <> struct Lanes<1> {
-    using V = float;
-    using W = float;
-    static __device__ __forceinline__ V splat(float a) { return a; }
-    static __device__ __forceinline__ V fma(V a, V b, V c) { return fmaf(a, b, c); }
-    static __device__ __forceinline__ V add(V a, V b) { return a + b; }
-    static __device__ __forceinline__ V zero() { return 0.0f; }
-    static __device__ __forceinline__ float get(V v, int) { return v; }
-    template <int K> static __device__ __forceinline__ V make(const float (&f)[K]) { return f[0]; }
-};
-template <> struct Lanes<2> {
-    using V = unsigned long long;   // low half: field 0, high half: field 1
-    using W = unsigned long long;
-    static __device__ __forceinline__ V pack(float lo, float hi) {
-        V r;
-        asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-        return r;
-    }
-    static __device__ __forceinline__ V splat(float a) { return pack(a, a); }
-    static __device__ __forceinline__ V fma(V a, V b, V c) {
-        V r;
-        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-        return r;
-    }
-    static __device__ __forceinline__ V add(V a, V b) {
-        V r;
-        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-        return r;
-    }
-    static __device__ __forceinline__ V zero() { return 0ull; }
-    static __device__ __forceinline__ float get(V v, int q) {
-        float lo, hi;
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-        return q ? hi : lo;
-    }
-    template <int K> static __device__ __forceinline__ V make(const float (&f)[K]) { return pack(f[0], f[1]); }
-};
-
-// Interior stencil weights duplicated into both halves of a 64-bit word (host-built).
-struct PackedStencil {
-    unsigned long long wl[kMaxStencil];
-    unsigned long long wr[kMaxStencil];
-};
-
 // One 2D tensor map per staged field (at most two).
 struct ColMaps {
     CUtensorMap m[2];

@@ -149,6 +149,20 @@ cudaError_t cols(const LineParams<T>& lp, const Op& op, int nlines, ColScratch<T
     return cudaGetLastError();
 }
 
+// Interior weights duplicated into both halves of a 64-bit word (packed FP32x2 stencil steps).
+inline PackedStencil packed_stencil(const LineParams<float>& lp) {
+    PackedStencil p;
+    std::memset(&p, 0, sizeof(p));
+    for (int o = 0; o < kMaxStencil; ++o) {
+        unsigned bl, br;
+        std::memcpy(&bl, &lp.wl[o], 4);
+        std::memcpy(&br, &lp.wr[o], 4);
+        p.wl[o] = (static_cast<unsigned long long>(bl) << 32) | bl;
+        p.wr[o] = (static_cast<unsigned long long>(br) << 32) | br;
+    }
+    return p;
+}
+
 // ---- pipelined FP32 rows: pointwise op for each row pass ----
 template <class Op> struct PipeOf { using type = void; };
 template <> struct PipeOf<OpCopy<float>> { using type = PipeCopy<float>; };
@@ -201,7 +215,8 @@ cudaError_t rows_pipe(const LineParams<float>& lp, const P& op, int nlines, unsi
     int grid = sms * per_sm;
     if (grid > nlines) grid = nlines;
     prof_begin(prof, kind, st);
-    kern<<<grid, TL, smem, st>>>(lp, op, nlines, static_cast<long long>(n), red);
+    const PackedStencil pw = packed_stencil(lp);
+    kern<<<grid, TL, smem, st>>>(lp, pw, op, nlines, static_cast<long long>(n), red);
     prof_end(prof, st);
     return cudaGetLastError();
 }
@@ -265,10 +280,10 @@ cudaError_t cols_pipe(const LineParams<float>& lp, const P& op, int nlines, ColS
     cudaError_t e = cols_pipe_launch<M, P, false>(lp, op, nlines, tiles, cs, red, st);
     prof_end(prof, st);
     if (e != cudaSuccess) return e;
-    const int total = nlines * P::NF;
+    const int strips = (nlines + 31) / 32;
     prof_begin(prof, 16, st);
-    cols_carry_kernel<float><<<(total + 127) / 128, 128, 0, st>>>(lp, nlines, P::NF, tiles, kColR, cs->aggL, cs->aggR,
-                                                                 cs->carL, cs->carR);
+    cols_carry_split_kernel<float><<<P::NF * strips, dim3(32, 8), 0, st>>>(lp, nlines, P::NF, tiles, kColR, cs->aggL,
+                                                                          cs->aggR, cs->carL, cs->carR);
     prof_end(prof, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -321,18 +336,6 @@ bool col_tma_maps(const P& op, int nlines, int n, int rows, ColMaps* maps) {
     return true;
 }
 
-inline PackedStencil packed_stencil(const LineParams<float>& lp) {
-    PackedStencil p;
-    std::memset(&p, 0, sizeof(p));
-    for (int o = 0; o < kMaxStencil; ++o) {
-        unsigned bl, br;
-        std::memcpy(&bl, &lp.wl[o], 4);
-        std::memcpy(&br, &lp.wr[o], 4);
-        p.wl[o] = (static_cast<unsigned long long>(bl) << 32) | bl;
-        p.wr[o] = (static_cast<unsigned long long>(br) << 32) | br;
-    }
-    return p;
-}
 
 template <int M, class P, bool kFinal>
 cudaError_t cols_tma_launch(const LineParams<float>& lp, const ColMaps& maps, const PackedStencil& pw, const P& op,
@@ -368,10 +371,10 @@ cudaError_t cols_tma(const LineParams<float>& lp, const ColMaps& maps, const P& 
     cudaError_t e = cols_tma_launch<M, P, false>(lp, maps, pw, op, nlines, tiles, cs, red, st);
     prof_end(prof, st);
     if (e != cudaSuccess) return e;
-    const int total = nlines * P::NF;
+    const int strips = (nlines + 31) / 32;
     prof_begin(prof, 16, st);
-    cols_carry_kernel<float><<<(total + 127) / 128, 128, 0, st>>>(lp, nlines, P::NF, tiles, kColR, cs->aggL, cs->aggR,
-                                                                 cs->carL, cs->carR);
+    cols_carry_split_kernel<float><<<P::NF * strips, dim3(32, 8), 0, st>>>(lp, nlines, P::NF, tiles, kColR, cs->aggL,
+                                                                          cs->aggR, cs->carL, cs->carR);
     prof_end(prof, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -324,17 +324,21 @@ __device__ __forceinline__ void set4(float4& v, int e, float x) {
 
 template <int M, class Op>
 __global__ void __launch_bounds__(512, 1)
-rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const Op op, int nlines, long long ld,
-                 unsigned long long* red_slots) {
+rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_constant__ PackedStencil pw, const Op op,
+                 int nlines, long long ld, unsigned long long* red_slots) {
     using T = float;
     constexpr int K = 16, V = 4, KC = K / V, H = M / 2, WC = KC + 2;
     constexpr int NS = Op::NS, NA = Op::NA, NF = Op::NF, NO = Op::NO;
+    // two swept fields (pass 2): their stencil and recurrence steps run as fma.rn.f32x2 pairs
+    constexpr bool kPack = NF == 2;
+    using PL = Lanes<2>;
     extern __shared__ __align__(128) unsigned char smraw[];
     float4* sm = reinterpret_cast<float4*>(smraw);
     __shared__ T s_scan[16][2 + 2 * NF];   // per-warp segments: D_f, D_b, A_f[NF], A_b[NF]
     __shared__ T s_bnd[2 * NF];            // carries / B values of the line (FP64 solve)
 
     const int n = lp.n;
+    const int N = lp.N, jb = N - H + 1;
     const int nch = n / V;
     const int TL = blockDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wpl = TL >> 5;
@@ -398,21 +402,78 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const Op op, int 
                 for (int q = 0; q < NF; ++q) fw[q][j * V + e] = fv[q];
             }
         }
-        T JL[NF][K], JR[NF][K], aL[NF], aR[NF];
+        T JL[kPack ? 1 : NF][K], JR[kPack ? 1 : NF][K], aL[NF], aR[NF];
+        unsigned long long JL2[kPack ? K : 1], JR2[kPack ? K : 1];   // packed J (then outputs)
+        auto at_field = [&](int p, int q) {
+            T sv[NS], fv[NF];
 #pragma unroll
-        for (int q = 0; q < NF; ++q) {
-            T win[K + M];
+            for (int f = 0; f < NS; ++f) sv[f] = reinterpret_cast<const T*>(stage_buf(sb, f) + swz(p / V))[p % V];
+            op.prologue(sv, fv);
+            return fv[q];
+        };
+        if constexpr (kPack) {
+            unsigned long long win2[K + M];
 #pragma unroll
-            for (int i = 0; i < K + M; ++i) win[i] = fw[q][V - H + i];
-            auto at = [&](int p) {
-                T sv[NS], fv[NF];
+            for (int i = 0; i < K + M; ++i) win2[i] = PL::pack(fw[0][V - H + i], fw[1][V - H + i]);
 #pragma unroll
-                for (int f = 0; f < NS; ++f) sv[f] = reinterpret_cast<const T*>(stage_buf(sb, f) + swz(p / V))[p % V];
-                op.prologue(sv, fv);
-                return fv[q];
-            };
-            local_integrals<T, M, K>(lp, start, K, win, at, JL[q], JR[q]);
-            chunk_aggregates<T, K>(d, K, JL[q], JR[q], aL[q], aR[q]);
+            for (int k = 0; k < K; ++k) {
+                unsigned long long jl = PL::fma(pw.wl[0], win2[k], PL::zero());
+                unsigned long long jr = PL::fma(pw.wr[0], win2[k], PL::zero());
+#pragma unroll
+                for (int o = 1; o <= M; ++o) {
+                    jl = PL::fma(pw.wl[o], win2[k + o], jl);
+                    jr = PL::fma(pw.wr[o], win2[k + o], jr);
+                }
+                JL2[k] = jl;
+                JR2[k] = jr;
+            }
+            if (!periodic && (start < H || start + K - 1 >= jb)) {
+                // chunks touching a wall: the shifted wall stencils, field by field (as local_integrals)
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int j = start + k;
+                    if (j >= H && j < jb) continue;
+                    T jl[2] = {T(0), T(0)}, jr[2] = {T(0), T(0)};
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+                        for (int o = 0; o <= M; ++o) {
+                            if (j < H) {
+                                const T v = at_field(o, q);
+                                if (j >= 1) jl[q] = fma(lp.wlA[j - 1][o], v, jl[q]);
+                                jr[q] = fma(lp.wrA[j][o], v, jr[q]);
+                            } else {
+                                const T v = at_field(N - M + o, q);
+                                jl[q] = fma(lp.wlB[j - jb][o], v, jl[q]);
+                                if (j < N) jr[q] = fma(lp.wrB[j - jb][o], v, jr[q]);
+                            }
+                        }
+                    }
+                    JL2[k] = PL::pack(jl[0], jl[1]);
+                    JR2[k] = PL::pack(jr[0], jr[1]);
+                }
+            }
+            const unsigned long long d2 = PL::splat(d);
+            unsigned long long a = PL::zero(), b = PL::zero();
+#pragma unroll
+            for (int k = 0; k < K; ++k) a = PL::fma(d2, a, JL2[k]);
+#pragma unroll
+            for (int k = K - 1; k >= 0; --k) b = PL::fma(d2, b, JR2[k]);
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                aL[q] = PL::get(a, q);
+                aR[q] = PL::get(b, q);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                T win[K + M];
+#pragma unroll
+                for (int i = 0; i < K + M; ++i) win[i] = fw[q][V - H + i];
+                auto at = [&](int p) { return at_field(p, q); };
+                local_integrals<T, M, K>(lp, start, K, win, at, JL[q], JR[q]);
+                chunk_aggregates<T, K>(d, K, JL[q], JR[q], aL[q], aR[q]);
+            }
         }
 
         // ---- scan of the chunk segments: shuffles inside each warp ----
@@ -530,29 +591,38 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const Op op, int 
             xl[q] = s_bnd[q];
             xr[q] = s_bnd[NF + q];
         }
+        const bool wallL = !periodic && start == 0, wallR = !periodic && start + K == n;
+        T cl[NF], cr[NF];
 #pragma unroll
         for (int q = 0; q < NF; ++q) {
             const T ax = fma(pF[q], Dxf, Axf[q]);
             const T bx = fma(pB[q], Dxb, Axb[q]);
-            T cl, cr;
-            if (periodic) {
-                cl = fma(pl, xl[q], ax);
-                cr = fma(pr, xr[q], bx);
-            } else {
-                if (start == 0) {
-                    JL[q][0] += xl[q];                    // P^L_0 = B_a
-                    cl = T(0);
-                } else {
-                    cl = fma(pl, xl[q], ax);
-                }
-                if (start + K == n) {
-                    JR[q][K - 1] += xr[q];                // P^R_N = B_b
-                    cr = T(0);
-                } else {
-                    cr = fma(pr, xr[q], bx);
-                }
+            cl[q] = wallL ? T(0) : fma(pl, xl[q], ax);   // at a wall, P^L_0 = B_a is injected instead
+            cr[q] = wallR ? T(0) : fma(pr, xr[q], bx);   // ... and P^R_N = B_b
+        }
+        if constexpr (kPack) {
+            if (wallL) JL2[0] = PL::add(JL2[0], PL::pack(xl[0], xl[1]));
+            if (wallR) JR2[K - 1] = PL::add(JR2[K - 1], PL::pack(xr[0], xr[1]));
+            const unsigned long long d2 = PL::splat(d);
+            unsigned long long p = PL::pack(cr[0], cr[1]);
+#pragma unroll
+            for (int k = K - 1; k >= 0; --k) {
+                p = PL::fma(d2, p, JR2[k]);
+                JR2[k] = p;
             }
-            chunk_finish<T, K>(d, K, cl, cr, JL[q], JR[q]);
+            unsigned long long qq = PL::pack(cl[0], cl[1]);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                qq = PL::fma(d2, qq, JL2[k]);
+                JR2[k] = PL::add(JR2[k], qq);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                if (wallL) JL[q][0] += xl[q];
+                if (wallR) JR[q][K - 1] += xr[q];
+                chunk_finish<T, K>(d, K, cl[q], cr[q], JL[q], JR[q]);
+            }
         }
 
         // ---- epilogue on this thread's own chunks ----
@@ -572,7 +642,10 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const Op op, int 
             for (int e = 0; e < V; ++e) {
                 T h[NF], sv[NS], av[NA > 0 ? NA : 1], ov[NO];
 #pragma unroll
-                for (int q = 0; q < NF; ++q) h[q] = JR[q][kc * V + e];
+                for (int q = 0; q < NF; ++q) {
+                    if constexpr (kPack) h[q] = PL::get(JR2[kc * V + e], q);
+                    else h[q] = JR[q][kc * V + e];
+                }
 #pragma unroll
                 for (int f = 0; f < NS; ++f) sv[f] = comp4(sraw[f], e);
 #pragma unroll
@@ -1018,6 +1091,99 @@ __global__ void cols_carry_kernel(const __grid_constant__ LineParams<T> lp, int 
                                   int R, const T* __restrict__ aggL, const T* __restrict__ aggR,
                                   T* __restrict__ carL, T* __restrict__ carR) {
     carry_body<T>(lp, nlines, nf, tiles, R, aggL, aggR, carL, carR, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// The same carries with each column's tiles split over 8 warps.  Block = 32 columns (lanes) x
+// 8 warps of one field; warp w scans tiles [w*tpw, (w+1)*tpw).  The warp segments (decay D,
+// aggregate E) compose through shared memory, (D1, E1) then (D2, E2) = (D1 D2, E1 D2 + E2),
+// giving each warp the segment entering its tiles and every warp the line totals I_N, I_0 for
+// the FP64 boundary solve; each warp then writes the carries of its own tiles.  Coalesced over
+// the 32 columns and 8x shorter dependency chains than one thread per column.
+template <typename T>
+__global__ void __launch_bounds__(256)
+cols_carry_split_kernel(const __grid_constant__ LineParams<T> lp, int nlines, int nf, int tiles, int R,
+                        const T* __restrict__ aggL, const T* __restrict__ aggR, T* __restrict__ carL,
+                        T* __restrict__ carR) {
+    constexpr int WS = 8;
+    __shared__ T sD[WS][32], sEf[WS][32], sEb[WS][32];
+    const int lane = threadIdx.x, wy = threadIdx.y;
+    const int strips = (nlines + 31) / 32;
+    const int q = blockIdx.x / strips;
+    const int line = (blockIdx.x % strips) * 32 + lane;
+    const bool live = line < nlines && q < nf;
+    const int n = lp.n;
+    const T nu = lp.nu;
+    const int last_rows = n - (tiles - 1) * R;
+    const T Dfull = dev_exp(-nu * T(R));
+    const T Dlast = dev_exp(-nu * T(last_rows));
+    const T einv = dev_exp(nu);           // d^{-1}: shifts a power by one node
+    auto dec = [&](int t) { return t == tiles - 1 ? Dlast : Dfull; };
+    const int tpw = (tiles + WS - 1) / WS;
+    const int t0 = min(wy * tpw, tiles), t1 = min(t0 + tpw, tiles);
+    const size_t b0 = static_cast<size_t>(q) * tiles * nlines + line;
+    T D = T(1), Ef = T(0), Eb = T(0);
+    if (live) {
+        for (int t = t0; t < t1; ++t) {
+            Ef = fma(Ef, dec(t), aggL[b0 + static_cast<size_t>(t) * nlines]);
+            D *= dec(t);
+        }
+        for (int t = t1 - 1; t >= t0; --t) Eb = fma(Eb, dec(t), aggR[b0 + static_cast<size_t>(t) * nlines]);
+    }
+    sD[wy][lane] = D;
+    sEf[wy][lane] = Ef;
+    sEb[wy][lane] = Eb;
+    __syncthreads();
+    if (!live) return;
+    // forward: segment entering this warp (E_in, decay P_in) and the total I_N
+    T IN = T(0), P = T(1), Ein = T(0), Pin = T(1);
+#pragma unroll
+    for (int w = 0; w < WS; ++w) {
+        if (w == wy) {
+            Ein = IN;
+            Pin = P;
+        }
+        IN = fma(IN, sD[w][lane], sEf[w][lane]);
+        P *= sD[w][lane];
+    }
+    // backward: from the top, entering this warp from the right, and the total I_0
+    T I0 = T(0), Q = T(1), Bin = T(0), Qin = T(1);
+#pragma unroll
+    for (int w = WS - 1; w >= 0; --w) {
+        if (w == wy) {
+            Bin = I0;
+            Qin = Q;
+        }
+        I0 = fma(I0, sD[w][lane], sEb[w][lane]);
+        Q *= sD[w][lane];
+    }
+    const bool periodic = lp.bc == BC_PERIODIC;
+    T XL, XR;
+    if (periodic) {
+        XL = static_cast<T>(static_cast<double>(IN) * lp.inv1mmu);
+        XR = static_cast<T>(static_cast<double>(I0) * lp.inv1mmu);
+    } else {
+        XL = static_cast<T>(lp.bAA * static_cast<double>(I0) + lp.bAB * static_cast<double>(IN));   // B_a
+        XR = static_cast<T>(lp.bBA * static_cast<double>(I0) + lp.bBB * static_cast<double>(IN));   // B_b
+    }
+    T E = Ein, pw = Pin;
+    for (int t = t0; t < t1; ++t) {
+        T c;
+        if (periodic) c = fma(pw, XL, E);
+        else c = (t == 0) ? XL : fma(pw * einv, XL, E);
+        carL[b0 + static_cast<size_t>(t) * nlines] = c;
+        E = fma(E, dec(t), aggL[b0 + static_cast<size_t>(t) * nlines]);
+        pw *= dec(t);
+    }
+    E = Bin;
+    T qw = Qin;
+    for (int t = t1 - 1; t >= t0; --t) {
+        T c;
+        if (periodic) c = fma(qw, XR, E);
+        else c = (t == tiles - 1) ? XR : fma(qw * einv, XR, E);
+        carR[b0 + static_cast<size_t>(t) * nlines] = c;
+        E = fma(E, dec(t), aggR[b0 + static_cast<size_t>(t) * nlines]);
+        qw *= dec(t);
+    }
 }
 
 template <typename T, int M, int KY, int WY, class Op>
