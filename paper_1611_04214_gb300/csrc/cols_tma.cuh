@@ -4,7 +4,7 @@
 // laid out for sm_103a:
 //   * a work item is one tile of R = 128 rows of a strip of 32 columns; one elected thread loads
 //     the tile plus its stencil halo (R + M rows x 128 bytes per staged field) with one 2D
-//     cp.async.bulk.tensor per field, completing on an mbarrier; three stages are in flight;
+//     cp.async.bulk.tensor per field, completing on an mbarrier; 3 or 4 tiles are in flight;
 //   * the two swept fields of a node (G(w) and w in pass 1, P and U in pass 3) share one 64-bit
 //     register pair and every recurrence / stencil step is one fma.rn.f32x2;
 //   * every mbarrier wait is bounded in time; a wait that runs out marks the block, the block
@@ -72,12 +72,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 // Status bit a kernel sets when one of its waits ran out of time.
 constexpr unsigned kStatusWaitTimeout = 1u;
 
+// Tiles in flight per block: 4 for one staged field, 3 for two (two blocks per SM either way).
+__host__ __device__ constexpr int tma_col_stages(int ns) { return ns == 1 ? 4 : 3; }
+
 // =========================================================================================
 // The kernel.  Block = 8 warps; warp wy owns rows [wy*16, wy*16 + 16) of the tile, lane = column.
 // Shared stage s holds, per staged field, rows r0 .. r0 + R + M - 1 (r0 = tile*R - M/2) of the
 // strip; rows outside [0, n) arrive zero-filled and, on periodic lines, are read wrapped from
-// global memory instead.  The buffer of item it-1 is refilled (item it+2) right after the block
-// barrier of item it, when no thread can still read it.
+// global memory instead.  The buffer of item it-1 is refilled (item it+STAGES-1) right after the block
+// barrier of item it, when no thread can still read it (STAGES = 3 or 4 tiles in flight).
 // kFinal = false: tile aggregates; kFinal = true: tile results from the scan's carries.
 // Requires nlines % 32 == 0 and n >= 256 (at least two tiles).
 // =========================================================================================
@@ -89,7 +92,7 @@ cols_tma_kernel(const __grid_constant__ LineParams<float> lp, const __grid_const
                 const float* __restrict__ carR, unsigned* status, unsigned long long* red_slots) {
     using T = float;
     constexpr int KY = 16, WY = 8, R = KY * WY, H = M / 2, ROWS = R + M;
-    constexpr int NS = Op::NS, NF = Op::NF, NO = Op::NO, STAGES = 3;
+    constexpr int NS = Op::NS, NF = Op::NF, NO = Op::NO, STAGES = tma_col_stages(Op::NS);
     constexpr unsigned kStageBytes = NS * ROWS * 32 * sizeof(float);
     using Ln = Lanes<NF>;
     using V = typename Ln::V;
@@ -142,8 +145,9 @@ cols_tma_kernel(const __grid_constant__ LineParams<float> lp, const __grid_const
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (blockIdx.x < items) issue(blockIdx.x, 0);
-        if (blockIdx.x + gridDim.x < items) issue(blockIdx.x + gridDim.x, 1);
+#pragma unroll
+        for (int j = 0; j < STAGES - 1; ++j)
+            if (blockIdx.x + j * gridDim.x < items) issue(blockIdx.x + j * gridDim.x, j);
     }
 
     RedAcc<T> red{T(0), T(0)};
@@ -161,6 +165,19 @@ cols_tma_kernel(const __grid_constant__ LineParams<float> lp, const __grid_const
         int cnt = n - start;
         cnt = cnt < 0 ? 0 : (cnt > KY ? KY : cnt);
         const float* sb = stage(s, 0) + (wy * KY) * 32 + lane;
+        const bool last = tile == tiles - 1;
+        // final phase: the tile's carries, loaded first so that their latency hides behind the
+        // window and the chunk aggregates
+        T c0[NF], c1[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            c0[q] = c1[q] = T(0);
+            if constexpr (kFinal) {
+                const size_t o = (static_cast<size_t>(q) * tiles + tile) * nlines + line;
+                if (periodic || tile != 0) c0[q] = carL[o];
+                if (periodic || !last) c1[q] = carR[o];
+            }
+        }
 
         // window of swept values: win[i] at position start - H + i (smem row wy*KY + i)
         V win[KY + M];
@@ -290,9 +307,9 @@ cols_tma_kernel(const __grid_constant__ LineParams<float> lp, const __grid_const
         // every thread is done with the stage of item it-1: refill it; agree on timeouts
         failed = __syncthreads_or(!arrived) != 0;
         if (failed) break;
-        if (threadIdx.x == 0 && item + 2 * gridDim.x < items) issue(item + 2 * gridDim.x, (it + 2) % STAGES);
+        if (threadIdx.x == 0 && item + (STAGES - 1) * gridDim.x < items)
+            issue(item + (STAGES - 1) * gridDim.x, (it + STAGES - 1) % STAGES);
 
-        const bool last = tile == tiles - 1;
         if constexpr (!kFinal) {
             if (wy == 0) {
                 V a = Ln::zero(), b = Ln::zero();
@@ -313,13 +330,6 @@ cols_tma_kernel(const __grid_constant__ LineParams<float> lp, const __grid_const
                 }
             }
         } else {
-            T c0[NF], c1[NF];
-#pragma unroll
-            for (int q = 0; q < NF; ++q) {
-                const size_t o = (static_cast<size_t>(q) * tiles + tile) * nlines + line;
-                c0[q] = (!periodic && tile == 0) ? T(0) : carL[o];
-                c1[q] = (!periodic && last) ? T(0) : carR[o];
-            }
             V cl = Ln::make(c0), cr = Ln::make(c1);
             if (!last) {
                 for (int i = 0; i < wy; ++i) cl = Ln::fma(cl, DKv, sL[pb][i][lane]);
@@ -402,10 +412,10 @@ cols_tma_kernel(const __grid_constant__ LineParams<float> lp, const __grid_const
         }
     }
     if (failed) {
-        // stop here; let the copies this block still has in flight (item it and, if issued,
-        // item it+1) land, each wait bounded, before exiting
+        // stop here; let the copies this block still has in flight (items it .. it+STAGES-2,
+        // those that were issued) land, each wait bounded, before exiting
         if (threadIdx.x == 0) {
-            for (int j = 0; j <= 1; ++j) {
+            for (int j = 0; j <= STAGES - 2; ++j) {
                 const int itm = blockIdx.x + (it + j) * gridDim.x;
                 if (itm < items) mbar_wait(&full[(it + j) % STAGES], static_cast<unsigned>(((it + j) / STAGES) & 1));
             }

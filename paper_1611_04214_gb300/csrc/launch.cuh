@@ -341,7 +341,7 @@ template <int M, class P, bool kFinal>
 cudaError_t cols_tma_launch(const LineParams<float>& lp, const ColMaps& maps, const PackedStencil& pw, const P& op,
                             int nlines, int tiles, ColScratch<float>* cs, unsigned long long* red, cudaStream_t st) {
     constexpr int ROWS = kColR + M;
-    const size_t smem = static_cast<size_t>(3) * P::NS * ROWS * 32 * sizeof(float) + 128;
+    const size_t smem = static_cast<size_t>(tma_col_stages(P::NS)) * P::NS * ROWS * 32 * sizeof(float) + 128;
     auto kern = cols_tma_kernel<M, P, kFinal>;
     static int limit = smem_optin(kern);
     if (limit < 0 || smem > static_cast<size_t>(limit)) return cudaErrorInvalidValue;
