@@ -295,6 +295,47 @@ def batched_leg(args, sample: int = 16):
     return out
 
 
+def sweep_microbench(reps: int = 10):
+    """Single H_c applications (one line sweep of a whole field, Sec. 3.2) through
+    molt_helmholtz_apply: along x and along y, the three boundary conditions, M = 4, nu = h/sqrt(c)
+    = 0.08, on 8192^2 and 16384^2 FP32 fields and one 8192^2 FP64 case; input U[0, 2].  Every field
+    exceeds the L2, so no flush is needed.  Algorithmic bytes: read once + write once per point."""
+    import torch
+
+    from paper_1611_04214_gb300.molt import Solver
+    peak, _ = _peaks()
+    cases = [(8192, "fp32", bc, axis) for bc in ("periodic", "neumann", "dirichlet") for axis in (0, 1)]
+    cases += [(16384, "fp32", "periodic", 0), (16384, "fp32", "periodic", 1), (8192, "fp64", "periodic", 0),
+              (8192, "fp64", "periodic", 1)]
+    out = []
+    for n, prec, bc, axis in cases:
+        L = 2 * 3.141592653589793
+        h = L / n if bc == "periodic" else L / (n - 1)
+        c = (h / 0.08) ** 2
+        dtype = torch.float32 if prec == "fp32" else torch.float64
+        g = torch.Generator(device="cuda").manual_seed(1)
+        fin = torch.rand((n, n), generator=g, device="cuda", dtype=dtype) * 2
+        fout = torch.empty_like(fin)
+        with Solver(nx=n, ny=n, bc=bc, quad_order=4, precision=prec, eps=0.02) as s:
+            for _ in range(2):
+                s.helmholtz_apply(axis, c, fin, fout)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                s.helmholtz_apply(axis, c, fin, fout)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+        elem = 4 if prec == "fp32" else 8
+        gbs = 2 * elem * n * n / (ms * 1e-3) / 1e9
+        out.append({"n": n, "precision": prec, "bc": bc, "axis": "x" if axis == 0 else "y", "ms": ms,
+                    "gpts_per_s": n * n / (ms * 1e-3) / 1e9, "gbs_algorithmic": gbs, "frac_of_peak": gbs / peak})
+        del fin, fout
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -403,6 +444,7 @@ def run_ours(args, rank, world, dist):
         del ug
         fp64 = fp64_comparison(args, u0) if (args.precision == "fp32" and not args.skip_fp64) else None
         batched = None if args.skip_batch else batched_leg(args)
+        sweeps_mb = None if args.skip_sweeps else sweep_microbench()
         last = infos[-1]
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                   "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -412,7 +454,7 @@ def run_ours(args, rank, world, dist):
                   "ch_steps_per_s": args.steps / (ms * 1e-3), "iters_per_stage": last.iters,
                   "final_residual": last.residual, "hbm_frac_step_algorithmic": hbm_frac_step,
                   "ms_per_step_graph_mode": graph_ms, "fp32_vs_fp64": fp64, "batched": batched,
-                  "kernels": kernels}
+                  "sweep_microbench": sweeps_mb, "kernels": kernels}
     solver.close()
     return result
 
@@ -427,6 +469,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--skip-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched-instances leg")
+    ap.add_argument("--skip-sweeps", action="store_true", help="skip the single-sweep microbenchmark")
     ap.add_argument("--batch-iters", type=int, default=40, help="fixed-point iteration cap of the batched leg")
     ap.add_argument("--grid", type=int, default=WORKLOAD["n"],
                     help="grid points per side (default: the 8192^2 workload; smaller sizes are for profiling)")
