@@ -42,7 +42,7 @@ KERNEL_FIELDS = {
 }
 # DRAM bytes per launch measured by ncu for the kernels of this workload (profiles/ summaries),
 # keyed by kernel name; filled only for kernels unchanged since their capture.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"rows_pass2": 1301.47e6}   # profiles/rows_pass2_ch2d_8192_full.md (DRAM read + write)
 
 
 def _peaks():
