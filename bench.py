@@ -40,9 +40,9 @@ KERNEL_FIELDS = {
     "cols_agg_H": (1, 0), "cols_agg_pass1": (1, 0), "cols_agg_pass3": (2, 0),
     "cols_final_H": (1, 1), "cols_final_pass1": (1, 2), "cols_final_pass3": (2, 2),
 }
-# DRAM bytes per launch measured by ncu for the kernels of this workload (profiles/ summaries),
-# keyed by kernel name; filled only for kernels unchanged since their capture.
-NCU_TRAFFIC = {"rows_pass2": 1301.47e6}   # profiles/rows_pass2_ch2d_8192_full.md (DRAM read + write)
+# DRAM bytes per launch measured by ncu for the kernels of this workload, keyed by kernel name;
+# filled only for kernels unchanged since their capture.
+NCU_TRAFFIC = {"rows_pass2": 1301.47e6}   # dram__bytes_read.sum + dram__bytes_write.sum, one 8192^2 launch
 
 
 def _peaks():
