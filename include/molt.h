@@ -233,6 +233,14 @@ long long molt_kernel_launches(const molt_solver* solver);
  * the sweep is launched or captured; both kernel families give bit-identical results. */
 long long molt_column_tma_launches(void);
 
+/* Diagnostics (no counterpart in the paper): checks on the GPU that a device-side wait gives up
+ * instead of hanging.  Launches one block whose mbarrier wait can never complete, through the
+ * same bounded wait the TMA column kernels use for their tile copies (limit: 1 s of GPU time).
+ * On return *timed_out = 1 if the wait gave up and set the status word, *waited_seconds = how
+ * long it waited.  Synchronizes the device; allocates two small device words.  Errors:
+ * MOLT_ERR_ARG (null output), MOLT_ERR_CUDA. */
+molt_status molt_selftest_bounded_wait(int* timed_out, double* waited_seconds);
+
 /* Diagnostic timing (not part of the method; off by default).  While enabled, every sweep
  * kernel launch is bracketed by two CUDA events on its stream. */
 molt_status molt_profile_enable(molt_solver* solver, int enable);

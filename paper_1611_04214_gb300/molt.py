@@ -26,7 +26,7 @@ EXPORTS = [
     "molt_last_error", "molt_kernel_launches", "molt_profile_enable", "molt_profile_collect",
     "molt_helmholtz_columns_noalloc", "molt_set_execution", "molt_graph_fallbacks",
     "molt_column_tma_launches", "molt_batch_create", "molt_batch_destroy", "molt_batch_points",
-    "molt_batch_offsets", "molt_batch_set_execution", "molt_batch_step",
+    "molt_batch_offsets", "molt_batch_set_execution", "molt_batch_step", "molt_selftest_bounded_wait",
 ]
 EXECUTION = {"host_loop": 0, "graph": 1}
 PROFILE_SLOTS = 32
@@ -88,6 +88,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_set_execution": ([P, I], I),
         "molt_graph_fallbacks": ([P], ctypes.c_longlong),
         "molt_column_tma_launches": ([], ctypes.c_longlong),
+        "molt_selftest_bounded_wait": ([ctypes.POINTER(I), ctypes.POINTER(D)], I),
         "molt_batch_create": ([ctypes.POINTER(VP), I, VP, I, I, D, I], I),
         "molt_batch_destroy": ([VP], I),
         "molt_batch_points": ([VP], ctypes.c_longlong),
@@ -137,6 +138,14 @@ def molt_helmholtz_columns_noalloc(nx: int, ny: int, Ly: float, bc: str, quad_or
 def molt_column_tma_launches() -> int:
     """Column-sweep kernels launched with TMA tile loads since the library was loaded (diagnostics)."""
     return int(load_library().molt_column_tma_launches())
+
+
+def molt_selftest_bounded_wait():
+    """Run one kernel whose bounded wait cannot complete; returns (timed_out, seconds waited)."""
+    t = ctypes.c_int(0)
+    sec = ctypes.c_double(0.0)
+    _check(load_library().molt_selftest_bounded_wait(ctypes.byref(t), ctypes.byref(sec)))
+    return bool(t.value), float(sec.value)
 
 
 def _stream_handle(stream):
