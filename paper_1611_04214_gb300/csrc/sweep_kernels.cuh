@@ -298,9 +298,9 @@ template <typename T, int M, int K, class Op>
 __global__ void __launch_bounds__(1024)
 rows_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, int tl_log2, int lpb,
             int pitch, unsigned long long* red_slots) {
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char sm_rows[];
     rows_body<T, M, K, Op>(lp, op, nlines, tl_log2, lpb, pitch, static_cast<int>(blockIdx.x) * lpb,
-                           reinterpret_cast<T*>(smraw), red_slots);
+                           reinterpret_cast<T*>(sm_rows), red_slots);
 }
 
 // =========================================================================================
@@ -332,13 +332,12 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
     // two swept fields (pass 2): their stencil and recurrence steps run as fma.rn.f32x2 pairs
     constexpr bool kPack = NF == 2;
     using PL = Lanes<2>;
-    extern __shared__ __align__(128) unsigned char smraw[];
-    float4* sm = reinterpret_cast<float4*>(smraw);
+    extern __shared__ __align__(128) unsigned char sm_rows_pipe[];
+    float4* sm = reinterpret_cast<float4*>(sm_rows_pipe);
     __shared__ T s_scan[16][2 + 2 * NF];   // per-warp segments: D_f, D_b, A_f[NF], A_b[NF]
     __shared__ T s_bnd[2 * NF];            // carries / B values of the line (FP64 solve)
 
     const int n = lp.n;
-    const int N = lp.N, jb = N - H + 1;
     const int nch = n / V;
     const int TL = blockDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wpl = TL >> 5;
@@ -411,6 +410,40 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
             op.prologue(sv, fv);
             return fv[q];
         };
+        // J^L_j, J^R_j of the wall positions of a non-periodic line (shifted wall stencils, Sec. 3.2
+        // reading), from the thread's own window: nodes 0..M of the first chunk sit at window
+        // indices H + o, nodes N-M..N of the last chunk at K - 1 - M + H + o.  Same operations in
+        // the same order as local_integrals.
+        auto wall_integrals = [&](const T* win, T (&jlo)[K], T (&jro)[K]) {
+            if (start == 0) {
+#pragma unroll
+                for (int k = 0; k < H; ++k) {   // j = k < H
+                    T jl = T(0), jr = T(0);
+#pragma unroll
+                    for (int o = 0; o <= M; ++o) {
+                        const T v = win[H + o];
+                        if (k >= 1) jl = fma(lp.wlA[k - 1][o], v, jl);
+                        jr = fma(lp.wrA[k][o], v, jr);
+                    }
+                    jlo[k] = jl;
+                    jro[k] = jr;
+                }
+            }
+            if (start + K == n) {
+#pragma unroll
+                for (int k = K - H; k < K; ++k) {   // j = start + k >= jb = n - H
+                    T jl = T(0), jr = T(0);
+#pragma unroll
+                    for (int o = 0; o <= M; ++o) {
+                        const T v = win[K - 1 - M + H + o];
+                        jl = fma(lp.wlB[k - (K - H)][o], v, jl);
+                        if (k < K - 1) jr = fma(lp.wrB[k - (K - H)][o], v, jr);
+                    }
+                    jlo[k] = jl;
+                    jro[k] = jr;
+                }
+            }
+        };
         if constexpr (kPack) {
             unsigned long long win2[K + M];
 #pragma unroll
@@ -427,30 +460,24 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
                 JL2[k] = jl;
                 JR2[k] = jr;
             }
-            if (!periodic && (start < H || start + K - 1 >= jb)) {
-                // chunks touching a wall: the shifted wall stencils, field by field (as local_integrals)
+            if (!periodic && (start == 0 || start + K == n)) {
+                // chunks touching a wall: the wall stencils field by field, then packed
+                T jl0[K], jr0[K], jl1[K], jr1[K];
+                wall_integrals(&fw[0][V - H], jl0, jr0);
+                wall_integrals(&fw[1][V - H], jl1, jr1);
+                if (start == 0) {
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const int j = start + k;
-                    if (j >= H && j < jb) continue;
-                    T jl[2] = {T(0), T(0)}, jr[2] = {T(0), T(0)};
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-#pragma unroll
-                        for (int o = 0; o <= M; ++o) {
-                            if (j < H) {
-                                const T v = at_field(o, q);
-                                if (j >= 1) jl[q] = fma(lp.wlA[j - 1][o], v, jl[q]);
-                                jr[q] = fma(lp.wrA[j][o], v, jr[q]);
-                            } else {
-                                const T v = at_field(N - M + o, q);
-                                jl[q] = fma(lp.wlB[j - jb][o], v, jl[q]);
-                                if (j < N) jr[q] = fma(lp.wrB[j - jb][o], v, jr[q]);
-                            }
-                        }
+                    for (int k = 0; k < H; ++k) {
+                        JL2[k] = PL::pack(jl0[k], jl1[k]);
+                        JR2[k] = PL::pack(jr0[k], jr1[k]);
                     }
-                    JL2[k] = PL::pack(jl[0], jl[1]);
-                    JR2[k] = PL::pack(jr[0], jr[1]);
+                }
+                if (start + K == n) {
+#pragma unroll
+                    for (int k = K - H; k < K; ++k) {
+                        JL2[k] = PL::pack(jl0[k], jl1[k]);
+                        JR2[k] = PL::pack(jr0[k], jr1[k]);
+                    }
                 }
             }
             const unsigned long long d2 = PL::splat(d);
@@ -470,8 +497,18 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
                 T win[K + M];
 #pragma unroll
                 for (int i = 0; i < K + M; ++i) win[i] = fw[q][V - H + i];
-                auto at = [&](int p) { return at_field(p, q); };
-                local_integrals<T, M, K>(lp, start, K, win, at, JL[q], JR[q]);
+#pragma unroll
+                for (int k = 0; k < K; ++k) {   // interior stencil (as local_integrals)
+                    T jl = T(0), jr = T(0);
+#pragma unroll
+                    for (int o = 0; o <= M; ++o) {
+                        jl = fma(lp.wl[o], win[k + o], jl);
+                        jr = fma(lp.wr[o], win[k + o], jr);
+                    }
+                    JL[q][k] = jl;
+                    JR[q][k] = jr;
+                }
+                if (!periodic) wall_integrals(win, JL[q], JR[q]);
                 chunk_aggregates<T, K>(d, K, JL[q], JR[q], aL[q], aR[q]);
             }
         }
@@ -686,8 +723,8 @@ cols_pipe_kernel(const __grid_constant__ LineParams<float> lp, const Op op, int 
     using T = float;
     constexpr int KY = 16, WY = 8, R = KY * WY, HR = kMaxM / 2, ROWS = R + 2 * HR, H = M / 2;
     constexpr int NS = Op::NS, NF = Op::NF, NO = Op::NO;
-    extern __shared__ __align__(128) unsigned char smraw[];
-    float* sm = reinterpret_cast<float*>(smraw);   // [2][NS][ROWS][32]
+    extern __shared__ __align__(128) unsigned char sm_cols_pipe[];
+    float* sm = reinterpret_cast<float*>(sm_cols_pipe);   // [2][NS][ROWS][32]
     __shared__ T sD[WY][32];
     __shared__ T sL[NF][WY][32];
     __shared__ T sR[NF][WY][32];
