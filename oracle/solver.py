@@ -231,8 +231,10 @@ class OracleSolver:
 
     def __init__(self, prob: Problem):
         self.prob = prob
-        self.v_prev = None      # v^{n-1} for BDF2
+        self.v_prev = None      # v^{n-1} for BDF2 / BDF3
         self.dt_prev = None
+        self.v_prev2 = None     # v^{n-2} for BDF3
+        self.dt_prev2 = None
         self.sdc_v0 = None      # level-[0] value v0_n for SDC2
         self.sdc_F0 = None      # level-[0] F0_n (a field) for SDC2
 
@@ -293,12 +295,23 @@ class OracleSolver:
                 res = stage_solve(self.prob, r, v, 2.0 * dt / 3.0)
                 self._record(info, res)
                 v_new = res.v
+        elif scheme == "bdf3":
+            # Eq. BDF3: tau = 6 dt / 11, r = (18 v^n - 9 v^{n-1} + 2 v^{n-2}) / 11; its two
+            # starting steps (and a restart after any dt change) are SDIRK2 steps (Sec. 4.4)
+            if self.v_prev is None or self.v_prev2 is None or self.dt_prev != dt or self.dt_prev2 != dt:
+                v_new = self._sdirk(v, dt, SDIRK2, info)
+            else:
+                r = (18.0 * v - 9.0 * self.v_prev + 2.0 * self.v_prev2) / 11.0
+                res = stage_solve(self.prob, r, v, 6.0 * dt / 11.0)
+                self._record(info, res)
+                v_new = res.v
         elif scheme == "sdc2":
             v_new = self._sdc2(v, dt, info)
         else:
             raise ValueError(scheme)
         if scheme != "sdc2":
             self.sdc_v0 = None
+        self.v_prev2, self.dt_prev2 = self.v_prev, self.dt_prev
         self.v_prev, self.dt_prev = v, dt
         return v_new - 1.0, info
 

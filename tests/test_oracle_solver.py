@@ -30,9 +30,10 @@ def _run_1d(scheme, dt, n=512, M=6, T=1.0, tol=1e-12):
     return u[0]
 
 
-@pytest.mark.parametrize("scheme", ["bdf2", "sdirk2", "sdc2", "sdirk3"])
+@pytest.mark.parametrize("scheme", ["bdf2", "sdirk2", "sdc2", "sdirk3", "bdf3"])
 def test_refinement_tables_reproduced(scheme):
     # Tables CH_refinement_second / CH_refinement_third: successive errors at dt = 0.05, 0.025, 0.0125.
+    # BDF3 starts with two SDIRK2 steps (Sec. 4.4); that start reproduces its column.
     g = _load_golden()
     dts = g["dt"][:4]
     us = [_run_1d(scheme, dt) for dt in dts]
@@ -90,6 +91,13 @@ def _scalar_scheme(scheme, lam, dt, steps):
         while len(ys) <= steps:
             ys.append((4 * ys[-1] - ys[-2]) / (3 - 2 * z))
         return ys[steps]
+    if scheme == "bdf3":        # two SDIRK2 steps, then 11 y_{n+1} - 18 y_n + 9 y_{n-1} - 2 y_{n-2} = 6 z y_{n+1}
+        s = SDIRK2.shape[0]
+        R2 = 1 + z * SDIRK2[-1] @ np.linalg.solve(np.eye(s) - z * SDIRK2, np.ones(s))
+        ys = [1.0, R2, R2 * R2]
+        while len(ys) <= steps:
+            ys.append((18 * ys[-1] - 9 * ys[-2] + 2 * ys[-3]) / (11 - 6 * z))
+        return ys[steps]
     if scheme == "sdc2":        # level 0 BE; level 1 trapezoid correction with F0 = lam y0
         y0, y1 = 1.0, 1.0
         for _ in range(steps):
@@ -100,7 +108,7 @@ def _scalar_scheme(scheme, lam, dt, steps):
     raise ValueError(scheme)
 
 
-@pytest.mark.parametrize("scheme", ["be", "bdf2", "sdirk2", "sdirk3", "sdc2"])
+@pytest.mark.parametrize("scheme", ["be", "bdf2", "sdirk2", "sdirk3", "sdc2", "bdf3"])
 @pytest.mark.parametrize("dt", [4e-3, 0.08])      # square and factorization regimes (eps = 0.18)
 def test_single_mode_matches_scalar_scheme_1d(scheme, dt):
     # A small mode a sin(kx) about u = 0 evolves by y' = (k^2 - eps^2 k^4) y (f(u) ~ -u); the
