@@ -52,7 +52,9 @@ typedef enum {
     MOLT_BDF2 = 1,    /* Eq. BDF2: tau = 2dt/3; first step (and after a dt change) is BE */
     MOLT_SDIRK2 = 2,  /* Sec. 4.2: two stages, eta = 1 - sqrt(2)/2 */
     MOLT_SDIRK3 = 3,  /* Sec. 4.4: Alexander's three-stage method, eta = 0.43587 */
-    MOLT_SDC2 = 4     /* Sec. 4.3 Eq. SDC_fixed: BE level [0] + trapezoid level [1] */
+    MOLT_SDC2 = 4,    /* Sec. 4.3 Eq. SDC_fixed: BE level [0] + trapezoid level [1] */
+    MOLT_BDF3 = 5     /* Eq. BDF3: tau = 6dt/11; its two starting steps (and two after a dt change)
+                         are SDIRK2 steps (Sec. 4.4) */
 } molt_scheme;
 
 typedef struct molt_grid molt_grid;

@@ -155,6 +155,8 @@ struct molt_solver {
     // history
     bool have_prev = false;
     double dt_prev = 0.0;
+    bool have_prev2 = false;     // a second earlier level (BDF3)
+    double dt_prev2 = 0.0;
     bool have_sdc = false;
     virtual ~molt_solver() { prof.release(); }
     virtual molt_status step(void* u, double dt, int scheme, cudaStream_t st, molt_step_info* info) = 0;
@@ -174,6 +176,7 @@ struct Solver final : molt_solver {
     T *w = nullptr, *wn = nullptr, *wprev = nullptr, *r = nullptr, *Y = nullptr;
     T *f1 = nullptr, *f2 = nullptr, *f3 = nullptr, *f4 = nullptr, *f5 = nullptr, *f6 = nullptr;
     T *k0 = nullptr, *k1 = nullptr, *ubuf = nullptr;
+    T *wprev2 = nullptr;                      // stored variable two levels back (BDF3)
     T *sdc_w0 = nullptr, *sdc_F0 = nullptr;   // SDC2: level-[0] state and its F
     molt::ColScratch<T> cs{};
     unsigned long long* red = nullptr;       // device [2]
@@ -225,7 +228,7 @@ struct Solver final : molt_solver {
 
     molt_status init() override {
         const size_t n = count();
-        T** fields[] = {&w, &wn, &wprev, &r, &Y, &f1, &f2, &f3, &f4, &f5, &f6, &k0, &k1, &sdc_w0, &sdc_F0};
+        T** fields[] = {&w, &wn, &wprev, &wprev2, &r, &Y, &f1, &f2, &f3, &f4, &f5, &f6, &k0, &k1, &sdc_w0, &sdc_F0};
         for (T** f : fields)
             if (!alloc(f, n)) return fail(MOLT_ERR_OOM, "device workspace allocation failed");
         const int nlines = g.nx;
@@ -655,13 +658,31 @@ struct Solver final : molt_solver {
             case MOLT_SDC2:
                 ms = sdc2(dt, st, info);
                 break;
+            case MOLT_BDF3:
+                if (!have_prev || !have_prev2 || dt_prev != dt || dt_prev2 != dt) {
+                    const double A[3][3] = {{kEta2, 0, 0}, {1.0 - kEta2, kEta2, 0}, {0, 0, 0}};
+                    ms = sdirk(dt, A, 2, st, info, 0);                 // SDIRK2 start (Sec. 4.4)
+                } else {
+                    if ((e = lin(r, wn, 18.0 / 11.0, wprev, -9.0 / 11.0, wprev2, 2.0 / 11.0, nullptr, 0, 0, st)) !=
+                        cudaSuccess)
+                        return cuda_fail(e, "bdf3 rhs");
+                    ms = stage(6.0 * dt / 11.0, r, st, &it, &res, &tu);
+                    record(info, 0, it, res, tu);
+                }
+                break;
             default:
                 return fail(MOLT_ERR_UNSUPPORTED, "scheme not supported by this build");
         }
         if (scheme != MOLT_SDC2) have_sdc = false;
         if (ms != MOLT_OK && ms != MOLT_ERR_NOT_CONVERGED) return ms;
         // history for BDF2: previous level
-        std::swap(wprev, wn);
+        // history: w^{n-2} <- w^{n-1} <- w^n (pointer rotation; wn takes the freed buffer)
+        T* freed = wprev2;
+        wprev2 = wprev;
+        wprev = wn;
+        wn = freed;
+        have_prev2 = have_prev;
+        dt_prev2 = dt_prev;
         have_prev = true;
         dt_prev = dt;
         if ((e = lin(u, w, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, -in_shift, st)) != cudaSuccess)
@@ -792,6 +813,7 @@ molt_status molt_set_params(molt_solver* s, const molt_params* p) {
     if (p->precision != s->p.precision) { s->err = "precision cannot change"; return MOLT_ERR_ARG; }
     s->p = *p;
     s->have_prev = false;
+    s->have_prev2 = false;
     s->have_sdc = false;
     s->drop_graphs();
     return MOLT_OK;
@@ -803,6 +825,7 @@ molt_status molt_set_bc(molt_solver* s, int bc) {
     s->bc = bc;
     s->g.bc = bc;
     s->have_prev = false;
+    s->have_prev2 = false;
     s->have_sdc = false;
     s->drop_graphs();
     return MOLT_OK;
@@ -820,6 +843,7 @@ long long molt_graph_fallbacks(const molt_solver* s) { return s ? s->graph_fallb
 molt_status molt_reset_history(molt_solver* s) {
     if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
     s->have_prev = false;
+    s->have_prev2 = false;
     s->have_sdc = false;
     return MOLT_OK;
 }
@@ -828,7 +852,7 @@ molt_status molt_step(molt_solver* s, void* u_dev, double dt, int scheme, void* 
     if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
     if (!u_dev) { s->err = "null field"; return MOLT_ERR_ARG; }
     if (!(dt > 0.0) || !std::isfinite(dt)) { s->err = "dt must be positive"; return MOLT_ERR_ARG; }
-    if (scheme < MOLT_BE || scheme > MOLT_SDC2) { s->err = "unknown scheme"; return MOLT_ERR_ARG; }
+    if (scheme < MOLT_BE || scheme > MOLT_BDF3) { s->err = "unknown scheme"; return MOLT_ERR_ARG; }
     return s->step(u_dev, dt, scheme, static_cast<cudaStream_t>(stream), info);
 }
 
@@ -837,7 +861,7 @@ molt_status molt_run_host(molt_solver* s, void* u_host, double dt, int scheme, i
     if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
     if (!u_host || nsteps < 0) { s->err = "bad host buffer or step count"; return MOLT_ERR_ARG; }
     if (!(dt > 0.0) || !std::isfinite(dt)) { s->err = "dt must be positive"; return MOLT_ERR_ARG; }
-    if (scheme < MOLT_BE || scheme > MOLT_SDC2) { s->err = "unknown scheme"; return MOLT_ERR_ARG; }
+    if (scheme < MOLT_BE || scheme > MOLT_BDF3) { s->err = "unknown scheme"; return MOLT_ERR_ARG; }
     return s->run_host(u_host, dt, scheme, nsteps, static_cast<cudaStream_t>(stream), info);
 }
 

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(PKG, "libmolt.so")
 MOLT_OK, MOLT_ERR_ARG, MOLT_ERR_NOT_CONVERGED, MOLT_ERR_CUDA, MOLT_ERR_OOM, MOLT_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 BC = {"periodic": 0, "neumann": 1, "dirichlet": 2}
 PRECISION = {"fp32": 0, "fp64": 1}
-SCHEME = {"be": 0, "bdf2": 1, "sdirk2": 2, "sdirk3": 3, "sdc2": 4}
+SCHEME = {"be": 0, "bdf2": 1, "sdirk2": 2, "sdirk3": 3, "sdc2": 4, "bdf3": 5}
 
 # Every symbol declared in include/molt.h.
 EXPORTS = [

@@ -263,7 +263,7 @@ def _fp32_bar(ref, bc, rho):
     return max(1e-6 * np.abs(ref + 1).max(), 8 * 2.0 ** -24 * np.abs(w).max() / max(1e-3, 1 - rho))
 
 
-@pytest.mark.parametrize("scheme", ["be", "bdf2", "sdirk2", "sdirk3", "sdc2"])
+@pytest.mark.parametrize("scheme", ["be", "bdf2", "sdirk2", "sdirk3", "sdc2", "bdf3"])
 @pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
 def test_steps_2d_fp64_match_oracle(scheme, bc):
     ny, nx = 72, 96
@@ -278,7 +278,7 @@ def test_steps_2d_fp64_match_oracle(scheme, bc):
         assert all(abs(x - y) <= 1 for x, y in zip(a, b)), (ig, ir)
 
 
-@pytest.mark.parametrize("scheme", ["be", "bdf2", "sdirk3"])
+@pytest.mark.parametrize("scheme", ["be", "bdf2", "sdirk3", "bdf3"])
 @pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
 def test_steps_2d_fp32_within_bar(scheme, bc):
     ny, nx = 72, 96
@@ -305,7 +305,7 @@ def test_1d_neumann_be_matches_oracle(precision):
         assert all(abs(a[0] - b[0]) <= 1 for a, b in zip(ig, ir))
 
 
-@pytest.mark.parametrize("scheme", ["be", "bdf2", "sdirk2", "sdirk3", "sdc2"])
+@pytest.mark.parametrize("scheme", ["be", "bdf2", "sdirk2", "sdirk3", "sdc2", "bdf3"])
 @pytest.mark.parametrize("dt", [0.025, 0.05])      # square and factorization regimes for SDC2 / BE
 def test_1d_periodic_paper_ic(scheme, dt):
     # The setting of the paper's refinement tables (M = 6, eps = 0.18, 512 nodes), four steps.
@@ -355,7 +355,8 @@ def test_not_converged_and_bad_arguments():
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("dims,bc,scheme", [((48, 64), "neumann", "sdirk3"), ((300, 96), "periodic", "bdf2"),
-                                            ((1, 256), "neumann", "sdc2"), ((40, 1024), "dirichlet", "be")])
+                                            ((1, 256), "neumann", "sdc2"), ((40, 1024), "dirichlet", "be"),
+                                            ((48, 64), "dirichlet", "bdf3")])
 def test_graph_loop_equals_host_loop(precision, dims, bc, scheme):
     # The device-driven loop (conditional WHILE graph) launches the same kernels in the same order
     # as the host-driven loop and applies the same stopping rule, so results are bit-identical.
