@@ -231,3 +231,21 @@ def test_energy_and_mass_closed_forms():
     exact = eps ** 2 / 2 * np.pi + 3 * np.pi / 16
     assert abs(energy(prob, u) - exact) < 1e-4
     assert abs(mass(prob, u)) < 1e-12
+
+
+def test_ripening_time_be_dt10_matches_paper():
+    # Sec. 6.1, Table 1DCH_ripeninglargedt: 1D periodic, 128 nodes, eps = 0.18, u0 of Eq.
+    # CH1D_initial, tolerance 1e-11; BE with dt = 10 ripens (u(pi) < 0 first) at t = 8250.00.
+    # 825 steps deep in the factorization regime (tau / eps^2 = 309).
+    n = 128
+    prob = Problem(nx=n, eps=0.18, M=6, tol=1e-11, max_iter=4000)
+    s = OracleSolver(prob)
+    u = paper_ic_1d(n)[None, :]
+    k = 0
+    while True:
+        u, info = s.step(u, 10.0, "be")
+        assert info.converged
+        k += 1
+        if u[0, n // 2] < 0 or k > 1000:
+            break
+    assert k * 10.0 == 8250.0
