@@ -178,6 +178,40 @@ molt_status molt_quadrature_weights(double nu, int M, const int* offsets, int si
 molt_status molt_helmholtz_columns_noalloc(int nx, int ny, double Ly, int bc, int quad_order, double c,
                                            const float* in_dev, float* out_dev, void* stream);
 
+/* ---- Adaptive step size (Sec. 5, Algorithm 1) ---------------------------------------------
+ * One call advances u by one accepted Backward Euler step whose local truncation error meets
+ * lte_tol.  The LTE is estimated by Richardson extrapolation: one BE step of size dt and two of
+ * size dt/2, eta = (1/2) max|u_dt - u_dt/2|; the two-half-step solution is kept.  With N_it the
+ * largest fixed-point iteration count of the three solves and N_maxit = params.max_iter:
+ *   eta <= lte_tol and N_it/N_maxit < 0.7: accept, next dt = dt min(theta sqrt(lte_tol/eta), gamma)
+ *   eta <= lte_tol and N_it/N_maxit < 1:   accept, next dt = dt min(theta sqrt(lte_tol/eta), 1)
+ *   eta <= lte_tol and N_it >= N_maxit:    reject, dt = dt / gamma
+ *   eta > 2 lte_tol:                       reject, dt = dt / gamma
+ *   lte_tol < eta <= 2 lte_tol:            reject, dt = dt theta sqrt(lte_tol/eta)
+ * and the retried / proposed dt is clipped to [dt_min, dt_max]. */
+typedef struct {
+    double lte_tol;    /* LTE tolerance sigma_tol (> 0) */
+    double dt_min;     /* smallest step (> 0); a rejection at dt_min is an error */
+    double dt_max;     /* largest step proposed (>= dt_min) */
+    double theta;      /* safety factor (paper: 0.8) */
+    double gamma;      /* growth / shrink factor (paper: 1.3) */
+} molt_adaptive;
+
+typedef struct {
+    double dt_used;    /* size of the accepted step */
+    double dt_next;    /* proposed size of the next step */
+    double eta;        /* LTE estimate of the accepted step */
+    int rejections;    /* rejected attempts before it */
+    int max_iters;     /* N_it of the accepted attempt */
+} molt_adaptive_info;
+
+/* One adaptive step in place on the device field u (FP32 or FP64 as the solver), starting with
+ * a trial size dt.  Allocates two work fields on first use.  The multistep history (BDF2/BDF3/
+ * SDC2) is reset.  Errors: MOLT_ERR_ARG (bad parameters), MOLT_ERR_NOT_CONVERGED (dt_min
+ * reached without meeting lte_tol; u unchanged), MOLT_ERR_CUDA, MOLT_ERR_OOM. */
+molt_status molt_step_adaptive(molt_solver* solver, void* u_dev, double dt, const molt_adaptive* params,
+                               void* stream, molt_adaptive_info* info);
+
 /* ---- Batched instances ----------------------------------------------------------------
  * Many independent 2D problems, each with its own grid size, eps and time step, stepped
  * together in FP32.  Every instance follows Sec. 2-5 exactly as molt_step does (stage

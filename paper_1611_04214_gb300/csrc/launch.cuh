@@ -642,6 +642,44 @@ cudaError_t energy_mass(const T* u, int nx, int ny, int bc, double hx, double hy
 
 }  // namespace molt
 
+namespace molt {
+namespace detail {
+
+// max |a - b| over n values, widened to FP64; the non-negative FP64 bit patterns order like the
+// values, so blocks combine by an integer atomicMax on *out (zeroed by the caller).
+template <typename T>
+__global__ void max_abs_diff_kernel(const T* __restrict__ a, const T* __restrict__ b, long long n,
+                                    unsigned long long* out) {
+    double m = 0.0;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        m = fmax(m, fabs(static_cast<double>(a[i]) - static_cast<double>(b[i])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+    __shared__ double s[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s[warp] = m;
+    __syncthreads();
+    if (warp == 0) {
+        m = lane < static_cast<int>(blockDim.x >> 5) ? s[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+        if (lane == 0) atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(m)));
+    }
+}
+
+}  // namespace detail
+
+template <typename T>
+cudaError_t max_abs_diff(const T* a, const T* b, long long n, unsigned long long* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    detail::max_abs_diff_kernel<T><<<detail::kRedBlocks, 256, 0, st>>>(a, b, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace molt
+
 #define MOLT_INSTANTIATE(T)                                                                                   \
     template cudaError_t molt::sweep<T>(int, const molt::LineParams<T>&, int, const molt::OpArgs<T>&, int, int, \
                                         molt::ColScratch<T>*, unsigned long long*, cudaStream_t, long long*,    \
@@ -651,4 +689,5 @@ cudaError_t energy_mass(const T* u, int nx, int ny, int bc, double hx, double hy
                                           const T*, double, double, cudaStream_t, long long*);                  \
     template cudaError_t molt::energy_mass<T>(const T*, int, int, int, double, double, double, int, double*,    \
                                               double*, cudaStream_t, long long*);                               \
-    template cudaError_t molt::cubic<T>(T*, long long, const T*, double, double, cudaStream_t, long long*);
+    template cudaError_t molt::cubic<T>(T*, long long, const T*, double, double, cudaStream_t, long long*);    \
+    template cudaError_t molt::max_abs_diff<T>(const T*, const T*, long long, unsigned long long*, cudaStream_t);

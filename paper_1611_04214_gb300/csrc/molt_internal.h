@@ -173,4 +173,8 @@ cudaError_t energy_mass(const T* u, int nx, int ny, int bc, double hx, double hy
                         long long* launches);
 int reduce_blocks();
 
+// max |a - b| over n values as FP64 bits in *out (device word; zeroed here), for step-size control.
+template <typename T>
+cudaError_t max_abs_diff(const T* a, const T* b, long long n, unsigned long long* out, cudaStream_t st);
+
 }  // namespace molt

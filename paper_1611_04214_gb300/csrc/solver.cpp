@@ -163,6 +163,8 @@ struct molt_solver {
     virtual molt_status run_host(void* u_host, double dt, int scheme, int nsteps, cudaStream_t st,
                                  molt_step_info* info) = 0;
     virtual molt_status reduce(const void* u, int which, double* out, cudaStream_t st) = 0;
+    virtual molt_status adaptive(void* u, double dt, const molt_adaptive& a, cudaStream_t st,
+                                 molt_adaptive_info* info) = 0;
     virtual molt_status apply(int axis, double c, const void* in, void* out, cudaStream_t st) = 0;
     virtual molt_status init() = 0;
     virtual void drop_graphs() = 0;
@@ -723,6 +725,77 @@ struct Solver final : molt_solver {
         return MOLT_OK;
     }
 
+    // Algorithm 1 (Sec. 5) with the Richardson BE estimate; see include/molt.h for the rules.
+    T *adapt_full = nullptr, *adapt_half = nullptr;
+    molt_status adaptive(void* u_void, double dt, const molt_adaptive& a, cudaStream_t st,
+                         molt_adaptive_info* out) override {
+        T* u = static_cast<T*>(u_void);
+        if (!adapt_full && (!alloc(&adapt_full, count()) || !alloc(&adapt_half, count())))
+            return fail(MOLT_ERR_OOM, "adaptive work fields");
+        cudaError_t e;
+        int rejections = 0;
+        for (;;) {
+            molt_step_info i1, i2, i3;
+            if ((e = lin(adapt_full, u, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess ||
+                (e = lin(adapt_half, u, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
+                return cuda_fail(e, "adaptive copy");
+            molt_status s1 = step(adapt_full, dt, MOLT_BE, st, &i1);
+            molt_status s2 = step(adapt_half, 0.5 * dt, MOLT_BE, st, &i2);
+            molt_status s3 = step(adapt_half, 0.5 * dt, MOLT_BE, st, &i3);
+            for (molt_status s : {s1, s2, s3})
+                if (s != MOLT_OK && s != MOLT_ERR_NOT_CONVERGED) return s;
+            if ((e = molt::max_abs_diff<T>(adapt_full, adapt_half, static_cast<long long>(count()), red, st)) !=
+                    cudaSuccess ||
+                (e = cudaMemcpyAsync(red_host, red, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) !=
+                    cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                return cuda_fail(e, "adaptive estimate");
+            double diff;
+            std::memcpy(&diff, &red_host[0], sizeof(double));
+            const double eta = 0.5 * diff;
+            const int n_it = std::max({i1.iters[0], i2.iters[0], i3.iters[0]});
+            const double ratio = eta == 0.0 ? INFINITY : std::sqrt(a.lte_tol / eta);
+            bool ok;
+            double next;
+            if (eta <= a.lte_tol) {
+                const double frac = static_cast<double>(n_it) / p.max_iter;
+                if (frac < 0.7) {
+                    ok = true;
+                    next = dt * std::min(a.theta * ratio, a.gamma);
+                } else if (frac < 1.0) {
+                    ok = true;
+                    next = dt * std::min(a.theta * ratio, 1.0);
+                } else {
+                    ok = false;
+                    next = dt / a.gamma;
+                }
+            } else {
+                ok = false;
+                next = eta / a.lte_tol > 2.0 ? dt / a.gamma : dt * a.theta * ratio;
+            }
+            next = std::min(std::max(next, a.dt_min), a.dt_max);
+            if (ok) {
+                if ((e = lin(u, adapt_half, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
+                    return cuda_fail(e, "adaptive store");
+                have_prev = have_prev2 = have_sdc = false;
+                if (out) {
+                    out->dt_used = dt;
+                    out->dt_next = next;
+                    out->eta = eta;
+                    out->rejections = rejections;
+                    out->max_iters = n_it;
+                }
+                return MOLT_OK;
+            }
+            ++rejections;
+            if (dt <= a.dt_min) {
+                have_prev = have_prev2 = have_sdc = false;
+                return fail(MOLT_ERR_NOT_CONVERGED, "adaptive step: dt_min reached without meeting the LTE tolerance");
+            }
+            dt = next;
+        }
+    }
+
     molt_status apply(int axis, double c, const void* in, void* out, cudaStream_t st) override {
         if (axis != 0 && axis != 1) return fail(MOLT_ERR_ARG, "axis must be 0 (x) or 1 (y)");
         if (axis == 1 && g.dim != 2) return fail(MOLT_ERR_ARG, "axis 1 needs a 2D grid");
@@ -893,6 +966,23 @@ molt_status molt_quadrature_weights(double nu, int M, const int* offsets, int si
 const char* molt_last_error(const molt_solver* s) {
     if (!s) return g_last_error.c_str();
     return s->err.c_str();
+}
+
+molt_status molt_step_adaptive(molt_solver* s, void* u, double dt, const molt_adaptive* a, void* stream,
+                               molt_adaptive_info* info) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    if (!u || !a) {
+        s->err = "null field or parameters";
+        return MOLT_ERR_ARG;
+    }
+    if (!(dt > 0.0) || !(a->lte_tol > 0.0) || !(a->dt_min > 0.0) || !(a->dt_max >= a->dt_min) ||
+        !(a->theta > 0.0) || !(a->gamma > 1.0) || !std::isfinite(dt) || !std::isfinite(a->dt_max))
+    {
+        s->err = "adaptive parameters: need dt, lte_tol, dt_min > 0, dt_max >= dt_min, theta > 0, gamma > 1";
+        return MOLT_ERR_ARG;
+    }
+    if (info) std::memset(info, 0, sizeof(*info));
+    return s->adaptive(u, std::min(std::max(dt, a->dt_min), a->dt_max), *a, static_cast<cudaStream_t>(stream), info);
 }
 
 long long molt_kernel_launches(const molt_solver* s) { return s ? s->launches : 0; }

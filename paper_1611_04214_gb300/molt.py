@@ -27,10 +27,21 @@ EXPORTS = [
     "molt_helmholtz_columns_noalloc", "molt_set_execution", "molt_graph_fallbacks",
     "molt_column_tma_launches", "molt_batch_create", "molt_batch_destroy", "molt_batch_points",
     "molt_batch_offsets", "molt_batch_set_execution", "molt_batch_step", "molt_selftest_bounded_wait",
+    "molt_step_adaptive",
 ]
 EXECUTION = {"host_loop": 0, "graph": 1}
 PROFILE_SLOTS = 32
 PASS_NAMES = ["H", "pass1", "pass2", "pass3", "pass4", "pass1d_a", "pass1d_b", ""]
+
+
+class _Adaptive(ctypes.Structure):
+    _fields_ = [("lte_tol", ctypes.c_double), ("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double),
+                ("theta", ctypes.c_double), ("gamma", ctypes.c_double)]
+
+
+class _AdaptiveInfo(ctypes.Structure):
+    _fields_ = [("dt_used", ctypes.c_double), ("dt_next", ctypes.c_double), ("eta", ctypes.c_double),
+                ("rejections", ctypes.c_int), ("max_iters", ctypes.c_int)]
 
 
 class MoltError(RuntimeError):
@@ -89,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_graph_fallbacks": ([P], ctypes.c_longlong),
         "molt_column_tma_launches": ([], ctypes.c_longlong),
         "molt_selftest_bounded_wait": ([ctypes.POINTER(I), ctypes.POINTER(D)], I),
+        "molt_step_adaptive": ([P, VP, D, ctypes.POINTER(_Adaptive), VP, ctypes.POINTER(_AdaptiveInfo)], I),
         "molt_batch_create": ([ctypes.POINTER(VP), I, VP, I, I, D, I], I),
         "molt_batch_destroy": ([VP], I),
         "molt_batch_points": ([VP], ctypes.c_longlong),
@@ -283,6 +295,17 @@ class Solver:
     def helmholtz_apply(self, axis: int, c: float, inp, out, stream=None):
         _check(self._lib.molt_helmholtz_apply(self._h, int(axis), float(c), self._field(inp), self._field(out),
                                               _stream_handle(stream)), self._h)
+
+    def step_adaptive(self, u, dt: float, lte_tol: float, dt_min: float, dt_max: float, theta: float = 0.8,
+                      gamma: float = 1.3, stream=None) -> dict:
+        """One accepted BE step of adaptive size (Algorithm 1, Richardson estimate); returns
+        dt_used, dt_next, eta, rejections, max_iters."""
+        a = _Adaptive(lte_tol, dt_min, dt_max, theta, gamma)
+        info = _AdaptiveInfo()
+        _check(self._lib.molt_step_adaptive(self._h, self._field(u), float(dt), ctypes.byref(a),
+                                            _stream_handle(stream), ctypes.byref(info)), self._h)
+        return {"dt_used": info.dt_used, "dt_next": info.dt_next, "eta": info.eta,
+                "rejections": info.rejections, "max_iters": info.max_iters}
 
     def kernel_launches(self) -> int:
         return int(self._lib.molt_kernel_launches(self._h))
