@@ -461,23 +461,31 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
                 JR2[k] = jr;
             }
             if (!periodic && (start == 0 || start + K == n)) {
-                // chunks touching a wall: the wall stencils field by field, then packed
-                T jl0[K], jr0[K], jl1[K], jr1[K];
-                wall_integrals(&fw[0][V - H], jl0, jr0);
-                wall_integrals(&fw[1][V - H], jl1, jr1);
-                if (start == 0) {
+                // chunks touching a wall: the shifted wall stencils, field by field (as
+                // local_integrals), node values gathered from the staged line
+                const int N = lp.N, jb = N - H + 1;
 #pragma unroll
-                    for (int k = 0; k < H; ++k) {
-                        JL2[k] = PL::pack(jl0[k], jl1[k]);
-                        JR2[k] = PL::pack(jr0[k], jr1[k]);
-                    }
-                }
-                if (start + K == n) {
+                for (int k = 0; k < K; ++k) {
+                    const int j = start + k;
+                    if (j >= H && j < jb) continue;
+                    T jl[2] = {T(0), T(0)}, jr[2] = {T(0), T(0)};
 #pragma unroll
-                    for (int k = K - H; k < K; ++k) {
-                        JL2[k] = PL::pack(jl0[k], jl1[k]);
-                        JR2[k] = PL::pack(jr0[k], jr1[k]);
+                    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+                        for (int o = 0; o <= M; ++o) {
+                            if (j < H) {
+                                const T v = at_field(o, q);
+                                if (j >= 1) jl[q] = fma(lp.wlA[j - 1][o], v, jl[q]);
+                                jr[q] = fma(lp.wrA[j][o], v, jr[q]);
+                            } else {
+                                const T v = at_field(N - M + o, q);
+                                jl[q] = fma(lp.wlB[j - jb][o], v, jl[q]);
+                                if (j < N) jr[q] = fma(lp.wrB[j - jb][o], v, jr[q]);
+                            }
+                        }
                     }
+                    JL2[k] = PL::pack(jl[0], jl[1]);
+                    JR2[k] = PL::pack(jr[0], jr[1]);
                 }
             }
             const unsigned long long d2 = PL::splat(d);
