@@ -336,6 +336,21 @@ def sweep_microbench(reps: int = 10):
     return out
 
 
+def combine_ranks(ms: float, points: float, dist):
+    """Whole-job timing over independent replicas (one per rank): the slowest rank's time and the
+    sum of the points all ranks swept.  The reduction tensor lives where the process group's
+    backend needs it (CUDA for NCCL, host memory otherwise)."""
+    if dist is None:
+        return ms, points
+    import torch
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([points], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -381,11 +396,7 @@ def run_ours(args, rank, world, dist):
     ms = ev0.elapsed_time(ev1)
     prof = solver.profile_collect()
     solver.profile_enable(False)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    pts_total = sweeps * n * n * world
+    ms, pts_total = combine_ranks(ms, sweeps * n * n, dist)
     value = pts_total / (ms * 1e-3) / 1e9
 
     # roofline of the dominant kernel (event-timed inside the timed region)
