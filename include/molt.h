@@ -179,10 +179,21 @@ molt_status molt_helmholtz_columns_noalloc(int nx, int ny, double Ly, int bc, in
                                            const float* in_dev, float* out_dev, void* stream);
 
 /* ---- Adaptive step size (Sec. 5, Algorithm 1) ---------------------------------------------
- * One call advances u by one accepted Backward Euler step whose local truncation error meets
- * lte_tol.  The LTE is estimated by Richardson extrapolation: one BE step of size dt and two of
- * size dt/2, eta = (1/2) max|u_dt - u_dt/2|; the two-half-step solution is kept.  With N_it the
- * largest fixed-point iteration count of the three solves and N_maxit = params.max_iter:
+ * One call advances u by one accepted step whose local truncation error estimate eta meets
+ * lte_tol.  Two estimators of Sec. 5 (params.estimator):
+ *   MOLT_LTE_RICHARDSON: Backward Euler by Richardson extrapolation.  One BE step of size dt and
+ *     two of size dt/2, eta = (1/2) max|u_dt - u_dt/2|; the two-half-step solution is kept.
+ *   MOLT_LTE_SDC2: BE-SDC2.  One SDC2 step from a fresh start, eta = max|u^[1] - u^[0]| over its
+ *     BE level [0] and its second-order level [1]; level [1] is kept.
+ *   MOLT_LTE_BDF2: BE-BDF2.  One BE step and one variable-step BDF2 step over the same interval,
+ *     from the state before the previous accepted adaptive step (u^{n-1}, step size dt_prev):
+ *     with omega = dt/dt_prev, v - tau F(v) = a_n u^n + a_prev u^{n-1}, tau = dt(1+omega)/(1+2omega),
+ *     a_n = (1+omega)^2/(1+2omega), a_prev = -omega^2/(1+2omega); eta = max|u_BDF2 - u_BE|, the
+ *     BDF2 solution is kept.  The solver keeps u^{n-1} after each accepted BE-BDF2 step; a call
+ *     without it (the first, or after molt_step, molt_run_host, molt_reset_history,
+ *     molt_set_params, molt_set_bc or an adaptive step with another estimator) uses BE-SDC2.
+ * With N_it the largest fixed-point iteration count of the attempt's stage solves and
+ * N_maxit = params.max_iter:
  *   eta <= lte_tol and N_it/N_maxit < 0.7: accept, next dt = dt min(theta sqrt(lte_tol/eta), gamma)
  *   eta <= lte_tol and N_it/N_maxit < 1:   accept, next dt = dt min(theta sqrt(lte_tol/eta), 1)
  *   eta <= lte_tol and N_it >= N_maxit:    reject, dt = dt / gamma
@@ -195,7 +206,10 @@ typedef struct {
     double dt_max;     /* largest step proposed (>= dt_min) */
     double theta;      /* safety factor (paper: 0.8) */
     double gamma;      /* growth / shrink factor (paper: 1.3) */
+    int estimator;     /* MOLT_LTE_RICHARDSON (0), MOLT_LTE_SDC2 (1) or MOLT_LTE_BDF2 (2) */
 } molt_adaptive;
+
+enum { MOLT_LTE_RICHARDSON = 0, MOLT_LTE_SDC2 = 1, MOLT_LTE_BDF2 = 2 };
 
 typedef struct {
     double dt_used;    /* size of the accepted step */
@@ -206,8 +220,8 @@ typedef struct {
 } molt_adaptive_info;
 
 /* One adaptive step in place on the device field u (FP32 or FP64 as the solver), starting with
- * a trial size dt.  Allocates two work fields on first use.  The multistep history (BDF2/BDF3/
- * SDC2) is reset.  Errors: MOLT_ERR_ARG (bad parameters), MOLT_ERR_NOT_CONVERGED (dt_min
+ * a trial size dt.  Allocates up to three work fields on first use.  The multistep history (BDF2/BDF3/
+ * SDC2) is reset.  Errors: MOLT_ERR_ARG (bad parameters or estimator), MOLT_ERR_NOT_CONVERGED (dt_min
  * reached without meeting lte_tol; u unchanged), MOLT_ERR_CUDA, MOLT_ERR_OOM. */
 molt_status molt_step_adaptive(molt_solver* solver, void* u_dev, double dt, const molt_adaptive* params,
                                void* stream, molt_adaptive_info* info);

@@ -158,6 +158,8 @@ struct molt_solver {
     bool have_prev2 = false;     // a second earlier level (BDF3)
     double dt_prev2 = 0.0;
     bool have_sdc = false;
+    bool have_adapt_prev = false;  // BE-BDF2 estimate: state before the last accepted adaptive step
+    double dt_adapt_prev = 0.0;    // and that step's size
     virtual ~molt_solver() { prof.release(); }
     virtual molt_status step(void* u, double dt, int scheme, cudaStream_t st, molt_step_info* info) = 0;
     virtual molt_status run_host(void* u_host, double dt, int scheme, int nsteps, cudaStream_t st,
@@ -725,35 +727,81 @@ struct Solver final : molt_solver {
         return MOLT_OK;
     }
 
-    // Algorithm 1 (Sec. 5) with the Richardson BE estimate; see include/molt.h for the rules.
-    T *adapt_full = nullptr, *adapt_half = nullptr;
+    // Algorithm 1 (Sec. 5) with the Richardson BE, BE-SDC2 or BE-BDF2 estimate; see
+    // include/molt.h for the rules.  The candidate solution of an attempt is built in
+    // adapt_half, so u is untouched until a step is accepted.
+    T *adapt_full = nullptr, *adapt_half = nullptr, *adapt_prev = nullptr;
     molt_status adaptive(void* u_void, double dt, const molt_adaptive& a, cudaStream_t st,
                          molt_adaptive_info* out) override {
         T* u = static_cast<T*>(u_void);
-        if (!adapt_full && (!alloc(&adapt_full, count()) || !alloc(&adapt_half, count())))
-            return fail(MOLT_ERR_OOM, "adaptive work fields");
+        const bool want_bdf = a.estimator == MOLT_LTE_BDF2;
+        const bool bdf = want_bdf && have_adapt_prev;
+        const bool sdc = a.estimator == MOLT_LTE_SDC2 || (want_bdf && !have_adapt_prev);   // BE-BDF2's first step
+        if (!adapt_half && !alloc(&adapt_half, count())) return fail(MOLT_ERR_OOM, "adaptive work fields");
+        if (!sdc && !adapt_full && !alloc(&adapt_full, count())) return fail(MOLT_ERR_OOM, "adaptive work fields");
+        if (want_bdf && !adapt_prev && !alloc(&adapt_prev, count())) return fail(MOLT_ERR_OOM, "adaptive history");
         cudaError_t e;
         int rejections = 0;
         for (;;) {
             molt_step_info i1, i2, i3;
-            if ((e = lin(adapt_full, u, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess ||
-                (e = lin(adapt_half, u, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
+            if ((e = lin(adapt_half, u, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess ||
+                (!sdc && (e = lin(adapt_full, u, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess))
                 return cuda_fail(e, "adaptive copy");
-            molt_status s1 = step(adapt_full, dt, MOLT_BE, st, &i1);
-            molt_status s2 = step(adapt_half, 0.5 * dt, MOLT_BE, st, &i2);
-            molt_status s3 = step(adapt_half, 0.5 * dt, MOLT_BE, st, &i3);
-            for (molt_status s : {s1, s2, s3})
-                if (s != MOLT_OK && s != MOLT_ERR_NOT_CONVERGED) return s;
-            if ((e = molt::max_abs_diff<T>(adapt_full, adapt_half, static_cast<long long>(count()), red, st)) !=
-                    cudaSuccess ||
+            const T* x;   // the two fields whose largest difference gives eta
+            const T* y;
+            int n_it;
+            if (bdf) {
+                // One BE step, and one variable-step BDF2 step from (u^{n-1}, u^n) = (adapt_prev, u)
+                // with omega = dt / dt_prev:
+                //   v - tau F(v) = a_n w^n + a_prev w^{n-1},  tau = dt (1 + omega) / (1 + 2 omega),
+                //   a_n = (1 + omega)^2 / (1 + 2 omega),     a_prev = -omega^2 / (1 + 2 omega),
+                // the quadratic through the three levels whose slope at t_{n+1} is F(v).
+                molt_status s1 = step(adapt_full, dt, MOLT_BE, st, &i1);
+                if (s1 != MOLT_OK && s1 != MOLT_ERR_NOT_CONVERGED) return s1;
+                const double om = dt / dt_adapt_prev;
+                const double tau = dt * (1.0 + om) / (1.0 + 2.0 * om);
+                const double an = (1.0 + om) * (1.0 + om) / (1.0 + 2.0 * om), ap = -om * om / (1.0 + 2.0 * om);
+                const double in_shift = 1.0 - static_cast<double>(shift());   // w = u + (1 - s)
+                if ((e = lin(w, u, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, in_shift, st)) != cudaSuccess ||
+                    (e = lin(r, u, an, adapt_prev, ap, nullptr, 0, nullptr, 0, in_shift * (an + ap), st)) !=
+                        cudaSuccess)
+                    return cuda_fail(e, "bdf2 estimate rhs");
+                int it2;
+                double res2, tu2;
+                molt_status s2 = stage(tau, r, st, &it2, &res2, &tu2);
+                if (s2 != MOLT_OK && s2 != MOLT_ERR_NOT_CONVERGED) return s2;
+                if ((e = lin(adapt_half, w, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, -in_shift, st)) != cudaSuccess)
+                    return cuda_fail(e, "bdf2 estimate store");
+                x = adapt_full;
+                y = adapt_half;
+                n_it = std::max(i1.iters[0], it2);
+            } else if (sdc) {
+                // One SDC2 step from a fresh start.  Afterwards w holds level [1] and sdc_w0
+                // level [0], both in the stored variable, whose difference is that of u.
+                have_sdc = false;
+                molt_status s1 = step(adapt_half, dt, MOLT_SDC2, st, &i1);
+                if (s1 != MOLT_OK && s1 != MOLT_ERR_NOT_CONVERGED) return s1;
+                x = w;
+                y = sdc_w0;
+                n_it = std::max(i1.iters[0], i1.iters[1]);
+            } else {
+                molt_status s1 = step(adapt_full, dt, MOLT_BE, st, &i1);
+                molt_status s2 = step(adapt_half, 0.5 * dt, MOLT_BE, st, &i2);
+                molt_status s3 = step(adapt_half, 0.5 * dt, MOLT_BE, st, &i3);
+                for (molt_status s : {s1, s2, s3})
+                    if (s != MOLT_OK && s != MOLT_ERR_NOT_CONVERGED) return s;
+                x = adapt_full;
+                y = adapt_half;
+                n_it = std::max({i1.iters[0], i2.iters[0], i3.iters[0]});
+            }
+            if ((e = molt::max_abs_diff<T>(x, y, static_cast<long long>(count()), red, st)) != cudaSuccess ||
                 (e = cudaMemcpyAsync(red_host, red, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) !=
                     cudaSuccess ||
                 (e = cudaStreamSynchronize(st)) != cudaSuccess)
                 return cuda_fail(e, "adaptive estimate");
             double diff;
             std::memcpy(&diff, &red_host[0], sizeof(double));
-            const double eta = 0.5 * diff;
-            const int n_it = std::max({i1.iters[0], i2.iters[0], i3.iters[0]});
+            const double eta = (sdc || bdf) ? diff : 0.5 * diff;   // the factor 1/2 is Richardson's
             const double ratio = eta == 0.0 ? INFINITY : std::sqrt(a.lte_tol / eta);
             bool ok;
             double next;
@@ -775,8 +823,12 @@ struct Solver final : molt_solver {
             }
             next = std::min(std::max(next, a.dt_min), a.dt_max);
             if (ok) {
+                if (want_bdf && (e = lin(adapt_prev, u, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
+                    return cuda_fail(e, "adaptive history");
                 if ((e = lin(u, adapt_half, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
                     return cuda_fail(e, "adaptive store");
+                have_adapt_prev = want_bdf;
+                dt_adapt_prev = dt;
                 have_prev = have_prev2 = have_sdc = false;
                 if (out) {
                     out->dt_used = dt;
@@ -888,6 +940,7 @@ molt_status molt_set_params(molt_solver* s, const molt_params* p) {
     s->have_prev = false;
     s->have_prev2 = false;
     s->have_sdc = false;
+    s->have_adapt_prev = false;
     s->drop_graphs();
     return MOLT_OK;
 }
@@ -900,6 +953,7 @@ molt_status molt_set_bc(molt_solver* s, int bc) {
     s->have_prev = false;
     s->have_prev2 = false;
     s->have_sdc = false;
+    s->have_adapt_prev = false;
     s->drop_graphs();
     return MOLT_OK;
 }
@@ -918,6 +972,7 @@ molt_status molt_reset_history(molt_solver* s) {
     s->have_prev = false;
     s->have_prev2 = false;
     s->have_sdc = false;
+    s->have_adapt_prev = false;
     return MOLT_OK;
 }
 
@@ -926,6 +981,7 @@ molt_status molt_step(molt_solver* s, void* u_dev, double dt, int scheme, void* 
     if (!u_dev) { s->err = "null field"; return MOLT_ERR_ARG; }
     if (!(dt > 0.0) || !std::isfinite(dt)) { s->err = "dt must be positive"; return MOLT_ERR_ARG; }
     if (scheme < MOLT_BE || scheme > MOLT_BDF3) { s->err = "unknown scheme"; return MOLT_ERR_ARG; }
+    s->have_adapt_prev = false;
     return s->step(u_dev, dt, scheme, static_cast<cudaStream_t>(stream), info);
 }
 
@@ -935,6 +991,7 @@ molt_status molt_run_host(molt_solver* s, void* u_host, double dt, int scheme, i
     if (!u_host || nsteps < 0) { s->err = "bad host buffer or step count"; return MOLT_ERR_ARG; }
     if (!(dt > 0.0) || !std::isfinite(dt)) { s->err = "dt must be positive"; return MOLT_ERR_ARG; }
     if (scheme < MOLT_BE || scheme > MOLT_BDF3) { s->err = "unknown scheme"; return MOLT_ERR_ARG; }
+    s->have_adapt_prev = false;
     return s->run_host(u_host, dt, scheme, nsteps, static_cast<cudaStream_t>(stream), info);
 }
 
@@ -976,9 +1033,11 @@ molt_status molt_step_adaptive(molt_solver* s, void* u, double dt, const molt_ad
         return MOLT_ERR_ARG;
     }
     if (!(dt > 0.0) || !(a->lte_tol > 0.0) || !(a->dt_min > 0.0) || !(a->dt_max >= a->dt_min) ||
-        !(a->theta > 0.0) || !(a->gamma > 1.0) || !std::isfinite(dt) || !std::isfinite(a->dt_max))
+        !(a->theta > 0.0) || !(a->gamma > 1.0) || !std::isfinite(dt) || !std::isfinite(a->dt_max) ||
+        (a->estimator != MOLT_LTE_RICHARDSON && a->estimator != MOLT_LTE_SDC2 && a->estimator != MOLT_LTE_BDF2))
     {
-        s->err = "adaptive parameters: need dt, lte_tol, dt_min > 0, dt_max >= dt_min, theta > 0, gamma > 1";
+        s->err = "adaptive parameters: need dt, lte_tol, dt_min > 0, dt_max >= dt_min, theta > 0, gamma > 1, "
+                 "estimator MOLT_LTE_RICHARDSON, MOLT_LTE_SDC2 or MOLT_LTE_BDF2";
         return MOLT_ERR_ARG;
     }
     if (info) std::memset(info, 0, sizeof(*info));

@@ -17,6 +17,7 @@ MOLT_OK, MOLT_ERR_ARG, MOLT_ERR_NOT_CONVERGED, MOLT_ERR_CUDA, MOLT_ERR_OOM, MOLT
 BC = {"periodic": 0, "neumann": 1, "dirichlet": 2}
 PRECISION = {"fp32": 0, "fp64": 1}
 SCHEME = {"be": 0, "bdf2": 1, "sdirk2": 2, "sdirk3": 3, "sdc2": 4, "bdf3": 5}
+LTE_ESTIMATOR = {"richardson": 0, "sdc2": 1, "bdf2": 2}          # molt_adaptive.estimator
 
 # Every symbol declared in include/molt.h.
 EXPORTS = [
@@ -36,7 +37,7 @@ PASS_NAMES = ["H", "pass1", "pass2", "pass3", "pass4", "pass1d_a", "pass1d_b", "
 
 class _Adaptive(ctypes.Structure):
     _fields_ = [("lte_tol", ctypes.c_double), ("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double),
-                ("theta", ctypes.c_double), ("gamma", ctypes.c_double)]
+                ("theta", ctypes.c_double), ("gamma", ctypes.c_double), ("estimator", ctypes.c_int)]
 
 
 class _AdaptiveInfo(ctypes.Structure):
@@ -297,10 +298,11 @@ class Solver:
                                               _stream_handle(stream)), self._h)
 
     def step_adaptive(self, u, dt: float, lte_tol: float, dt_min: float, dt_max: float, theta: float = 0.8,
-                      gamma: float = 1.3, stream=None) -> dict:
-        """One accepted BE step of adaptive size (Algorithm 1, Richardson estimate); returns
-        dt_used, dt_next, eta, rejections, max_iters."""
-        a = _Adaptive(lte_tol, dt_min, dt_max, theta, gamma)
+                      gamma: float = 1.3, estimator: str = "richardson", stream=None) -> dict:
+        """One accepted step of adaptive size (Algorithm 1) with the "richardson" (BE), "sdc2"
+        (BE-SDC2) or "bdf2" (BE-BDF2) LTE estimate; returns dt_used, dt_next, eta, rejections,
+        max_iters.  BE-BDF2 keeps the previous accepted state in the solver between calls."""
+        a = _Adaptive(lte_tol, dt_min, dt_max, theta, gamma, LTE_ESTIMATOR[estimator])
         info = _AdaptiveInfo()
         _check(self._lib.molt_step_adaptive(self._h, self._field(u), float(dt), ctypes.byref(a),
                                             _stream_handle(stream), ctypes.byref(info)), self._h)
