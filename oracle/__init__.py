@@ -17,6 +17,11 @@ notation, with no blocking, fusion or reordering:
                   (Eq. CH_BE_fixed2_factor, CH_BE_fixed_complete, Sec. 5.1),
                   time schemes (BE, BDF2, SDIRK2, SDIRK3) and the discrete
                   energy / mass.
+* ``adaptive``  - adaptive step-size control (Algorithm 1) with the Richardson,
+                  BE-SDC2 and BE-BDF2 LTE estimates.
+* ``vch``       - the vector (three-phase) model of Eq. CH_vector: potential,
+                  stage parameters of Eq. CH_vector_fixed1/2, stage solve, BE and
+                  BDF2 steps and energy (Sec. 5.2).
 
 Readings of passages the paper leaves open are listed in each docstring.
 """
