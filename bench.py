@@ -295,6 +295,96 @@ def batched_leg(args, sample: int = 16):
     return out
 
 
+VCH = dict(name="vch2d_4096_bdf2_periodic", n=4096, eps=0.32, dt=1e-4, M=4, bc="periodic")
+# field words moved per point by one vector CH iteration (two components): passes 1-4 of each
+# component read / write 2+2, 4+2, 2+2 and 5+1 fields; each stage's rhs inverses 4 x (1+1) per component
+VCH_WORDS_ITER, VCH_WORDS_RHS = 40, 16
+VCH_SWEEPS_ITER, VCH_SWEEPS_RHS = 14, 8
+# (read, write) fields per point of each vector CH kernel slot; the vector passes 1 and 2 read
+# both components (the column aggregate of pass 1 reads them once more)
+VCH_KERNEL_FIELDS = {
+    "rows_H": (1, 1), "rows_pass2": (4, 2), "rows_pass4": (5, 1),
+    "cols_agg_H": (1, 0), "cols_agg_pass1": (2, 0), "cols_agg_pass3": (2, 0),
+    "cols_final_H": (1, 1), "cols_final_pass1": (2, 2), "cols_final_pass3": (2, 2),
+}
+
+
+def vch_leg(args, steps: int = 3):
+    """The vector (three-phase) model of Sec. 5.2 at scale: 4096^2 periodic nodes with the paper's
+    node spacing 2pi/64 and eps = 0.32 (so the domain is [0, 128 pi]^2), u1 from Eq. CH2D_initial and
+    u2 = sin y repeated 64 x 64 times; BDF2 steps of dt = 1e-4 after one BE start, the same
+    fixed-point iteration cap as the main workload.  FP32 device time per step, the algorithmic HBM
+    fraction of the step, and the largest difference from the FP64 path over the same steps."""
+    import numpy as np
+    import torch
+
+    from paper_1611_04214_gb300.molt import Solver
+    n, L = VCH["n"], 2 * np.pi * VCH["n"] / 64
+    x = (L / n) * np.arange(n)
+    sxy = np.sin(x)[None, :] + np.sin(x)[:, None]
+    u10 = 2 * np.exp(sxy - 2) + 2.2 * np.exp(-sxy - 2) - 1
+    u20 = np.broadcast_to(np.sin(x)[:, None], (n, n))
+    peak, _ = _peaks()
+    out = {"workload": VCH["name"], "grid": [n, n], "eps": VCH["eps"], "dt": VCH["dt"], "scheme": "bdf2",
+           "iters_cap": args.iters}
+    fields = {}
+
+    def run(s, timed_profile):
+        u1 = torch.tensor(u10, dtype=torch.float32, device="cuda").to(s.dtype)
+        u2 = torch.tensor(np.ascontiguousarray(u20), dtype=torch.float32, device="cuda").to(s.dtype)
+        s.reset_history()
+        s.vch_step(u1, u2, VCH["dt"], "bdf2", raise_on_nonconvergence=False)     # BE start
+        torch.cuda.synchronize()
+        if timed_profile:
+            s.profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0 = s.kernel_launches()
+        e0.record()
+        infos = [s.vch_step(u1, u2, VCH["dt"], "bdf2", raise_on_nonconvergence=False) for _ in range(steps)]
+        e1.record()
+        torch.cuda.synchronize()
+        prof = None
+        if timed_profile:
+            prof = s.profile_collect()
+            s.profile_enable(False)
+        return u1, u2, infos, e0.elapsed_time(e1) / steps, (s.kernel_launches() - k0) / steps, prof
+
+    for prec in ("fp32", "fp64"):
+        with Solver(nx=n, ny=n, Lx=L, Ly=L, bc=VCH["bc"], eps=VCH["eps"], quad_order=VCH["M"], precision=prec,
+                    tol=1e-6, max_iter=args.iters) as s:
+            # device-driven stage loops (the default) for the step time; host-driven loops with
+            # per-kernel events for the kernel table
+            u1, u2, infos, ms, launches, _ = run(s, False)
+            elem = 4 if prec == "fp32" else 8
+            iters = sum(i.iters[0] for i in infos)
+            step_bytes = (iters * VCH_WORDS_ITER + steps * VCH_WORDS_RHS) * elem * n * n / steps
+            out[prec] = {"ms_per_step": ms, "iters_per_step": [i.iters[0] for i in infos],
+                         "line_sweep_gpts": (iters * VCH_SWEEPS_ITER + steps * VCH_SWEEPS_RHS) * n * n / steps
+                         / (ms * 1e-3) / 1e9,
+                         "hbm_frac_step_algorithmic": step_bytes / (ms * 1e-3) / 1e9 / peak,
+                         "kernel_launches_per_step": launches}
+            fields[prec] = (u1.double(), u2.double())
+            if prec == "fp32":
+                s.set_execution("host_loop")
+                _, _, _, ms_h, _, prof = run(s, True)
+                kern = {k: {"ms_total": v[0], "launches": v[1], "gbs": (
+                    sum(VCH_KERNEL_FIELDS[k]) * elem * n * n / (v[0] / v[1] * 1e-3) / 1e9
+                    if k in VCH_KERNEL_FIELDS else None)} for k, v in prof.items()}
+                dom = max((k for k in prof if k in VCH_KERNEL_FIELDS), key=lambda k: prof[k][0])
+                total = sum(v[0] for v in prof.values())
+                out["fp32"]["ms_per_step_host_loop"] = ms_h
+                out["fp32"]["kernels"] = kern
+                out["fp32"]["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
+                                           "unit": "GB/s", "frac": kern[dom]["gbs"] / peak,
+                                           "share_of_kernel_time": prof[dom][0] / total if total else None}
+    d = max((fields["fp32"][c] - fields["fp64"][c]).abs().max().item() for c in range(2))
+    out["max_abs_diff_fp32_vs_fp64"] = d
+    out["speedup_fp32"] = out["fp64"]["ms_per_step"] / out["fp32"]["ms_per_step"]
+    del fields
+    torch.cuda.empty_cache()
+    return out
+
+
 def sweep_microbench(reps: int = 10):
     """Single H_c applications (one line sweep of a whole field, Sec. 3.2) through
     molt_helmholtz_apply: along x and along y, the three boundary conditions, M = 4, nu = h/sqrt(c)
@@ -456,6 +546,7 @@ def run_ours(args, rank, world, dist):
         fp64 = fp64_comparison(args, u0) if (args.precision == "fp32" and not args.skip_fp64) else None
         batched = None if args.skip_batch else batched_leg(args)
         sweeps_mb = None if args.skip_sweeps else sweep_microbench()
+        vch = None if args.skip_vch else vch_leg(args)
         last = infos[-1]
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                   "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -465,7 +556,7 @@ def run_ours(args, rank, world, dist):
                   "ch_steps_per_s": args.steps / (ms * 1e-3), "iters_per_stage": last.iters,
                   "final_residual": last.residual, "hbm_frac_step_algorithmic": hbm_frac_step,
                   "ms_per_step_graph_mode": graph_ms, "fp32_vs_fp64": fp64, "batched": batched,
-                  "sweep_microbench": sweeps_mb, "kernels": kernels}
+                  "sweep_microbench": sweeps_mb, "vector_ch": vch, "kernels": kernels}
     solver.close()
     return result
 
@@ -481,6 +572,9 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched-instances leg")
     ap.add_argument("--skip-sweeps", action="store_true", help="skip the single-sweep microbenchmark")
+    ap.add_argument("--skip-vch", action="store_true", help="skip the vector Cahn-Hilliard leg")
+    ap.add_argument("--vch-only", action="store_true",
+                    help="run only the vector Cahn-Hilliard leg and print its JSON (for profiling)")
     ap.add_argument("--batch-iters", type=int, default=40, help="fixed-point iteration cap of the batched leg")
     ap.add_argument("--grid", type=int, default=WORKLOAD["n"],
                     help="grid points per side (default: the 8192^2 workload; smaller sizes are for profiling)")
@@ -503,6 +597,10 @@ def main():
     from paper_1611_04214_gb300 import build
     if rank == 0:
         build.build_library()
+    if args.vch_only:
+        if rank == 0:
+            print(json.dumps({"vector_ch": vch_leg(args)}), flush=True)
+        return
     if dist:
         dist.barrier()
     res = run_ours(args, rank, world, dist)

@@ -178,6 +178,31 @@ molt_status molt_quadrature_weights(double nu, int M, const int* offsets, int si
 molt_status molt_helmholtz_columns_noalloc(int nx, int ny, double Ly, int bc, int quad_order, double c,
                                            const float* in_dev, float* out_dev, void* stream);
 
+/* ---- Vector Cahn-Hilliard (Sec. 5.2, Eq. CH_vector) -----------------------------------------
+ * One step of the three-phase vector model u_t = -Lap[eps^2 Lap u - grad W(u)], u = (u1, u2),
+ * W = |z^3 - 1|^2 with z = u1 + i u2, in place on two distinct device fields of the solver's grid
+ * and precision (row-major like molt_step).  The state is translated about
+ * z3 = (-1/2, -sqrt(3)/2) (Eq. CH_vector_linearize).  Each component's stage solve is the scalar
+ * one with 18 in place of 2:
+ *   - tau >= eps^2/81: Eq. CH_vector_fixed1, c = 9 tau +- sqrt(81 tau^2 - eps^2 tau);
+ *   - otherwise: Eq. CH_vector_fixed2, c = sqrt(eps^2 tau).
+ * The lagged term of component j is G_j = [grad W(v + z3)]_j - ((c1 + c2)/tau) v_j.  Both
+ * components' lagged terms come from the previous iterate.  The iteration stops on the larger
+ * of the two components' changes, as in molt_step.  Boundary conditions apply to v = u - z3, so
+ * Dirichlet walls hold u = z3.
+ * scheme: MOLT_BE, or MOLT_BDF2 (BE start, and a BE step again after any dt change).
+ * The BDF2 history is the state before the previous vector step.  molt_reset_history,
+ * molt_set_params and molt_set_bc clear it.
+ * Allocates nine work fields on first use.
+ * Errors:
+ *   MOLT_ERR_ARG: null, equal fields, or a bad dt.
+ *   MOLT_ERR_UNSUPPORTED: another scheme, or 2D x lines longer than the two-field row kernels
+ *     allow.
+ *   MOLT_ERR_NOT_CONVERGED: the fields hold the last iterate.
+ *   MOLT_ERR_CUDA, MOLT_ERR_OOM. */
+molt_status molt_vch_step(molt_solver* solver, void* u1_dev, void* u2_dev, double dt, int scheme, void* stream,
+                          molt_step_info* info);
+
 /* ---- Adaptive step size (Sec. 5, Algorithm 1) ---------------------------------------------
  * One call advances u by one accepted step whose local truncation error estimate eta meets
  * lte_tol.  Two estimators of Sec. 5 (params.estimator):

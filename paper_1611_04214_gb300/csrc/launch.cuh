@@ -51,6 +51,18 @@ template <typename T> inline Op1a<T> build(const OpArgs<T>& a, Op1a<T>*) {
 template <typename T> inline Op1b<T> build(const OpArgs<T>& a, Op1b<T>*) {
     Op1b<T> o; o.e_in = a.in0; o.y_in = a.in1; o.w = a.out0; o.shift = a.shift; return o;
 }
+template <typename T> inline OpP1V<T> build(const OpArgs<T>& a, OpP1V<T>*) {
+    OpP1V<T> o; o.v1 = a.in0; o.v2 = a.in1; o.t_out = a.out0; o.s_out = a.out1; o.s = a.vs; o.comp = a.comp;
+    return o;
+}
+template <typename T> inline OpP2V<T> build(const OpArgs<T>& a, OpP2V<T>*) {
+    OpP2V<T> o; o.v1 = a.in0; o.v2 = a.in1; o.t_in = a.in2; o.s_in = a.in3; o.p_out = a.out0; o.u_out = a.out1;
+    o.s = a.vs; o.beta = a.beta; o.comp = a.comp; return o;
+}
+template <typename T> inline Op1aV<T> build(const OpArgs<T>& a, Op1aV<T>*) {
+    Op1aV<T> o; o.v1 = a.in0; o.v2 = a.in1; o.e_out = a.out0; o.s = a.vs; o.beta = a.beta; o.comp = a.comp;
+    return o;
+}
 
 // Opt the kernel into the largest dynamic shared memory the device allows next to its static
 // shared memory; returns that limit (bytes) or -1 on error.
@@ -554,6 +566,12 @@ __global__ void sum_partials_kernel(const double* partials, int n, double* resul
 
 }  // namespace detail
 
+// The vector CH passes (OP_V1, OP_V2, OP_V1A), instantiated in their own translation units
+// (kernels_vch_f32.cu, kernels_vch_f64.cu) so that they compile in parallel with the rest.
+template <typename T>
+cudaError_t sweep_vch(int axis, const LineParams<T>& lp, int kind, const OpArgs<T>& a, int nx, int ny,
+                      ColScratch<T>* cs, unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof);
+
 template <typename T>
 cudaError_t sweep(int axis, const LineParams<T>& lp, int kind, const OpArgs<T>& a, int nx, int ny, ColScratch<T>* cs,
                   unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof) {
@@ -566,6 +584,9 @@ cudaError_t sweep(int axis, const LineParams<T>& lp, int kind, const OpArgs<T>& 
         case OP_P4: return dispatch<T, OpP4<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
         case OP_1A: return dispatch<T, Op1a<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
         case OP_1B: return dispatch<T, Op1b<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
+        case OP_V1:
+        case OP_V2:
+        case OP_V1A: return sweep_vch<T>(axis, lp, kind, a, nx, ny, cs, red, st, launches, prof);
     }
     return cudaErrorInvalidValue;
 }

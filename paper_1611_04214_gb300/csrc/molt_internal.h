@@ -96,7 +96,7 @@ struct ColScratch {
 namespace molt {
 
 // Which fused prologue/epilogue a sweep runs (see sweep_common.cuh for the formulas).
-enum OpKind { OP_COPY = 0, OP_P1, OP_P2, OP_P3, OP_P4, OP_1A, OP_1B };
+enum OpKind { OP_COPY = 0, OP_P1, OP_P2, OP_P3, OP_P4, OP_1A, OP_1B, OP_V1, OP_V2, OP_V1A };
 
 template <typename T>
 struct OpArgs {
@@ -107,6 +107,8 @@ struct OpArgs {
     T* out0 = nullptr;
     T* out1 = nullptr;
     T g2 = 0, g1 = 0, beta = 0, shift = 0;
+    T vs = 0;       // vector CH: s = (c1 + c2)/tau
+    int comp = 0;   // vector CH: component of the pass
 };
 
 // Optional per-kernel event timing (diagnostic; off unless a solver enables it).

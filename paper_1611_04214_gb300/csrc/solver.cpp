@@ -160,6 +160,8 @@ struct molt_solver {
     bool have_sdc = false;
     bool have_adapt_prev = false;  // BE-BDF2 estimate: state before the last accepted adaptive step
     double dt_adapt_prev = 0.0;    // and that step's size
+    bool vch_have_prev = false;    // vector CH BDF2: previous level held
+    double vch_dt_prev = 0.0;
     virtual ~molt_solver() { prof.release(); }
     virtual molt_status step(void* u, double dt, int scheme, cudaStream_t st, molt_step_info* info) = 0;
     virtual molt_status run_host(void* u_host, double dt, int scheme, int nsteps, cudaStream_t st,
@@ -167,6 +169,8 @@ struct molt_solver {
     virtual molt_status reduce(const void* u, int which, double* out, cudaStream_t st) = 0;
     virtual molt_status adaptive(void* u, double dt, const molt_adaptive& a, cudaStream_t st,
                                  molt_adaptive_info* info) = 0;
+    virtual molt_status vch_step(void* u1, void* u2, double dt, int scheme, cudaStream_t st,
+                                 molt_step_info* info) = 0;
     virtual molt_status apply(int axis, double c, const void* in, void* out, cudaStream_t st) = 0;
     virtual molt_status init() = 0;
     virtual void drop_graphs() = 0;
@@ -182,6 +186,11 @@ struct Solver final : molt_solver {
     T *k0 = nullptr, *k1 = nullptr, *ubuf = nullptr;
     T *wprev2 = nullptr;                      // stored variable two levels back (BDF3)
     T *sdc_w0 = nullptr, *sdc_F0 = nullptr;   // SDC2: level-[0] state and its F
+    // vector CH (allocated on first use): second component's state, Y, start of step, previous
+    // level and right side, the pass outputs the second component keeps until its last pass, and
+    // the first component's previous level
+    T *vw2 = nullptr, *vY2 = nullptr, *vn2 = nullptr, *vp2 = nullptr, *vr2 = nullptr;
+    T *vg4 = nullptr, *vg5 = nullptr, *vg6 = nullptr, *vp1 = nullptr;
     molt::ColScratch<T> cs{};
     unsigned long long* red = nullptr;       // device [2]
     unsigned long long* red_host = nullptr;  // pinned [2]
@@ -340,6 +349,8 @@ struct Solver final : molt_solver {
         molt::LineParams<T> lix, lox, liy, loy;
         T g2, g1, beta, s;
         bool two_d;
+        bool vch = false;   // vector CH iteration (both components)
+        T vs = 0;           // vector CH: (c1 + c2)/tau
     };
 
     bool make_passes(const StageParams& sp, Passes* ps) {
@@ -353,9 +364,80 @@ struct Solver final : molt_solver {
         return true;
     }
 
+    // Vector CH stage (Sec. 5.2): the factorization of Eq. CH_vector_fixed1 for tau >= eps^2/81
+    // (c = 9 tau +- sqrt(81 tau^2 - eps^2 tau)), else the completed square of Eq. CH_vector_fixed2
+    // (c1 = c2 = sqrt(eps^2 tau)); s = (c1 + c2)/tau.
+    bool make_vch_passes(double tau, Passes* ps, double* c_in, double* c_out) {
+        const double e2 = p.eps * p.eps;
+        double c1, c2;
+        if (81.0 * tau >= e2) {
+            const double disc = std::sqrt(81.0 * tau * tau - e2 * tau);
+            c1 = 9.0 * tau + disc;
+            c2 = 9.0 * tau - disc;
+        } else {
+            c1 = c2 = std::sqrt(e2 * tau);
+        }
+        *c_in = std::max(c1, c2);
+        *c_out = std::min(c1, c2);
+        ps->two_d = g.dim == 2;
+        if (!line_params(*c_in, 0, &ps->lix) || !line_params(*c_out, 0, &ps->lox)) return false;
+        if (ps->two_d && (!line_params(*c_in, 1, &ps->liy) || !line_params(*c_out, 1, &ps->loy))) return false;
+        ps->s = shift();
+        ps->g2 = ps->g1 = T(0);
+        ps->beta = static_cast<T>(tau / *c_in);
+        ps->vch = true;
+        ps->vs = static_cast<T>((c1 + c2) / tau);
+        return true;
+    }
+
+    // One vector CH iteration.  Both components' lagged terms come from the previous iterate, so
+    // every pass that reads both state fields runs before either is overwritten: passes 1-3 of
+    // each component, then pass 4 of each (2D); pass a of each, then pass b of each (1D).
+    cudaError_t launch_vch_iteration(const Passes& ps, cudaStream_t st) {
+        cudaError_t e;
+        T* V[2] = {w, vw2};
+        const T* Yc[2] = {Y, vY2};
+        if (ps.two_d) {
+            T* U[2] = {f4, vg4};
+            T* Q1[2] = {f5, vg5};
+            T* Q2[2] = {f6, vg6};
+            for (int c = 0; c < 2; ++c) {
+                molt::OpArgs<T> a1;
+                a1.in0 = w; a1.in1 = vw2; a1.out0 = f1; a1.out1 = f2; a1.vs = ps.vs; a1.comp = c;
+                if ((e = sweep(1, ps.liy, molt::OP_V1, a1, st)) != cudaSuccess) return e;
+                molt::OpArgs<T> a2;
+                a2.in0 = w; a2.in1 = vw2; a2.in2 = f1; a2.in3 = f2; a2.out0 = f3; a2.out1 = U[c];
+                a2.vs = ps.vs; a2.beta = ps.beta; a2.comp = c;
+                if ((e = sweep(0, ps.lix, molt::OP_V2, a2, st)) != cudaSuccess) return e;
+                molt::OpArgs<T> a3;
+                a3.in0 = f3; a3.in1 = U[c]; a3.out0 = Q1[c]; a3.out1 = Q2[c];
+                if ((e = sweep(1, ps.loy, molt::OP_P3, a3, st)) != cudaSuccess) return e;
+            }
+            for (int c = 0; c < 2; ++c) {
+                molt::OpArgs<T> a4;
+                a4.in0 = Q1[c]; a4.in1 = Q2[c]; a4.in2 = U[c]; a4.in3 = Yc[c]; a4.out0 = V[c]; a4.shift = ps.s;
+                if ((e = sweep(0, ps.lox, molt::OP_P4, a4, st)) != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        }
+        T* E[2] = {f1, f2};
+        for (int c = 0; c < 2; ++c) {
+            molt::OpArgs<T> aa;
+            aa.in0 = w; aa.in1 = vw2; aa.out0 = E[c]; aa.vs = ps.vs; aa.beta = ps.beta; aa.comp = c;
+            if ((e = sweep(0, ps.lix, molt::OP_V1A, aa, st)) != cudaSuccess) return e;
+        }
+        for (int c = 0; c < 2; ++c) {
+            molt::OpArgs<T> ab;
+            ab.in0 = E[c]; ab.in1 = Yc[c]; ab.out0 = V[c]; ab.shift = ps.s;
+            if ((e = sweep(0, ps.lox, molt::OP_1B, ab, st)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+
     // One iteration: 2D passes 1-4 (column, row, column, row) or the two 1D row passes.  The
     // last pass accumulates the residual into `red`.
     cudaError_t launch_iteration(const Passes& ps, cudaStream_t st) {
+        if (ps.vch) return launch_vch_iteration(ps, st);
         cudaError_t e;
         if (ps.two_d) {
             molt::OpArgs<T> a1;
@@ -384,6 +466,7 @@ struct Solver final : molt_solver {
     // node whose body is one iteration followed by the device-side stopping check.
     struct LoopGraph {
         bool valid = false;
+        bool vch = false;
         double tau = 0.0;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
@@ -406,7 +489,7 @@ struct Solver final : molt_solver {
 
     LoopGraph* loop_graph(double tau, const Passes& ps) {
         for (LoopGraph& lg : graphs)
-            if (lg.valid && lg.tau == tau) return &lg;
+            if (lg.valid && lg.tau == tau && lg.vch == ps.vch) return &lg;
         LoopGraph& lg = graphs[next_graph];
         next_graph = (next_graph + 1) % kGraphSlots;
         if (lg.exec) cudaGraphExecDestroy(lg.exec);
@@ -450,6 +533,7 @@ struct Solver final : molt_solver {
             return nullptr;
         }
         lg.valid = true;
+        lg.vch = ps.vch;
         lg.tau = tau;
         lg.graph = graph;
         lg.exec = exec;
@@ -458,11 +542,13 @@ struct Solver final : molt_solver {
 
     // Solve v - tau F(v) = r for w (in: first guess, out: last iterate), r in stored form.
     // With y_given, the field Y already holds M_o^{-1} M_i^{-1} r and rhs is not read.
+    // With `given`, its passes are run (the vector CH stage) and Y must be given.
     molt_status stage(double tau, const T* rhs, cudaStream_t st, int* iters, double* res_out, double* tol_out,
-                      bool y_given = false) {
+                      bool y_given = false, const Passes* given = nullptr) {
         const StageParams sp = stage_params(tau, p.eps);
         Passes ps;
-        if (!make_passes(sp, &ps)) return MOLT_ERR_ARG;
+        if (given) ps = *given;
+        else if (!make_passes(sp, &ps)) return MOLT_ERR_ARG;
         cudaError_t e = cudaSuccess;
         if (!y_given) {
             // Y = M_o^{-1} M_i^{-1} r
@@ -848,6 +934,64 @@ struct Solver final : molt_solver {
         }
     }
 
+    // Vector CH step (Sec. 5.2) on the two device fields u1, u2 in place, in the stored variable
+    // v = u - z3, z3 = (-1/2, -sqrt(3)/2).  BE, or BDF2 (Eq. BDF2 per component) with a BE start
+    // that is repeated whenever dt changes.
+    molt_status vch_step(void* u1v, void* u2v, double dt, int scheme, cudaStream_t st,
+                         molt_step_info* info) override {
+        T* u1 = static_cast<T*>(u1v);
+        T* u2 = static_cast<T*>(u2v);
+        if (info) std::memset(info, 0, sizeof(*info));
+        if (scheme != MOLT_BE && scheme != MOLT_BDF2)
+            return fail(MOLT_ERR_UNSUPPORTED, "vector CH steps support BE and BDF2");
+        if (g.dim == 2 && g.nx > molt::max_row_length<T>(2))
+            return fail(MOLT_ERR_UNSUPPORTED, "2D steps need x lines within the two-field row kernels' length");
+        if (!vw2) {
+            T** fields[] = {&vw2, &vY2, &vn2, &vp2, &vr2, &vg4, &vg5, &vg6, &vp1};
+            for (T** f : fields)
+                if (!alloc(f, count())) return fail(MOLT_ERR_OOM, "vector CH workspace");
+        }
+        const double zx = -0.5, zy = -0.86602540378443864676;
+        cudaError_t e;
+        if ((e = lin(w, u1, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, -zx, st)) != cudaSuccess ||
+            (e = lin(vw2, u2, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, -zy, st)) != cudaSuccess ||
+            (e = lin(wn, w, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess ||
+            (e = lin(vn2, vw2, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
+            return cuda_fail(e, "vector CH load");
+        const bool bdf = scheme == MOLT_BDF2 && vch_have_prev && vch_dt_prev == dt;
+        const T* r1 = wn;
+        const T* r2 = vn2;
+        double tau = dt;
+        if (bdf) {
+            tau = 2.0 * dt / 3.0;
+            if ((e = lin(r, wn, 4.0 / 3.0, vp1, -1.0 / 3.0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess ||
+                (e = lin(vr2, vn2, 4.0 / 3.0, vp2, -1.0 / 3.0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
+                return cuda_fail(e, "vector CH bdf2 rhs");
+            r1 = r;
+            r2 = vr2;
+        }
+        Passes ps;
+        double c_in, c_out;
+        if (!make_vch_passes(tau, &ps, &c_in, &c_out)) return MOLT_ERR_ARG;
+        if ((e = mm_inv(c_in, r1, f2, st)) != cudaSuccess || (e = mm_inv(c_out, f2, Y, st)) != cudaSuccess ||
+            (e = mm_inv(c_in, r2, f2, st)) != cudaSuccess || (e = mm_inv(c_out, f2, vY2, st)) != cudaSuccess)
+            return cuda_fail(e, "vector CH rhs inverse");
+        int it;
+        double res, tu;
+        molt_status ms = stage(tau, nullptr, st, &it, &res, &tu, true, &ps);
+        if (ms != MOLT_OK && ms != MOLT_ERR_NOT_CONVERGED) return ms;
+        record(info, 0, it, res, tu);
+        std::swap(vp1, wn);   // v^n becomes the previous level
+        std::swap(vp2, vn2);
+        vch_have_prev = true;
+        vch_dt_prev = dt;
+        if ((e = lin(u1, w, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, zx, st)) != cudaSuccess ||
+            (e = lin(u2, vw2, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, zy, st)) != cudaSuccess)
+            return cuda_fail(e, "vector CH store");
+        if (info) info->status = ms;
+        return ms;
+    }
+
     molt_status apply(int axis, double c, const void* in, void* out, cudaStream_t st) override {
         if (axis != 0 && axis != 1) return fail(MOLT_ERR_ARG, "axis must be 0 (x) or 1 (y)");
         if (axis == 1 && g.dim != 2) return fail(MOLT_ERR_ARG, "axis 1 needs a 2D grid");
@@ -941,6 +1085,7 @@ molt_status molt_set_params(molt_solver* s, const molt_params* p) {
     s->have_prev2 = false;
     s->have_sdc = false;
     s->have_adapt_prev = false;
+    s->vch_have_prev = false;
     s->drop_graphs();
     return MOLT_OK;
 }
@@ -954,6 +1099,7 @@ molt_status molt_set_bc(molt_solver* s, int bc) {
     s->have_prev2 = false;
     s->have_sdc = false;
     s->have_adapt_prev = false;
+    s->vch_have_prev = false;
     s->drop_graphs();
     return MOLT_OK;
 }
@@ -973,6 +1119,7 @@ molt_status molt_reset_history(molt_solver* s) {
     s->have_prev2 = false;
     s->have_sdc = false;
     s->have_adapt_prev = false;
+    s->vch_have_prev = false;
     return MOLT_OK;
 }
 
@@ -1023,6 +1170,15 @@ molt_status molt_quadrature_weights(double nu, int M, const int* offsets, int si
 const char* molt_last_error(const molt_solver* s) {
     if (!s) return g_last_error.c_str();
     return s->err.c_str();
+}
+
+molt_status molt_vch_step(molt_solver* s, void* u1_dev, void* u2_dev, double dt, int scheme, void* stream,
+                          molt_step_info* info) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    if (!u1_dev || !u2_dev || u1_dev == u2_dev) { s->err = "need two distinct component fields"; return MOLT_ERR_ARG; }
+    if (!(dt > 0.0) || !std::isfinite(dt)) { s->err = "dt must be positive"; return MOLT_ERR_ARG; }
+    if (scheme < MOLT_BE || scheme > MOLT_BDF3) { s->err = "unknown scheme"; return MOLT_ERR_ARG; }
+    return s->vch_step(u1_dev, u2_dev, dt, scheme, static_cast<cudaStream_t>(stream), info);
 }
 
 molt_status molt_step_adaptive(molt_solver* s, void* u, double dt, const molt_adaptive* a, void* stream,

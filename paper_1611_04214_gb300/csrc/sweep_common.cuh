@@ -376,6 +376,106 @@ struct Op1b : OpBase<T> {
     }
 };
 
+// ---- Vector CH (Sec. 5.2): two components in the stored variable v = u - z3 ----
+// Lagged term of component `comp`: G = [grad W(v + z3)]_comp - s v_comp with
+// grad W = 6 (z^3 - 1) conj(z^2), z = u1 + i u2 (W = |z^3 - 1|^2, Eq. CH_vector_reaction), and
+// s = (c1 + c2)/tau the linear part the factorization moves to the left (Eq. CH_vector_fixed1/2).
+template <typename T>
+__device__ __forceinline__ T vch_lag(T v1, T v2, int comp, T s) {
+    const T a = v1 - T(0.5), b = v2 - T(0.86602540378443864676);   // u = v + z3
+    const T a2 = a * a, b2 = b * b;
+    const T fr = a * (a2 - T(3) * b2) - T(1), fi = b * (T(3) * a2 - b2);   // z^3 - 1
+    const T zr = a2 - b2, zi = T(2) * a * b;                                // z^2
+    return comp == 0 ? T(6) * (fr * zr + fi * zi) - s * v1 : T(6) * (fi * zr - fr * zi) - s * v2;
+}
+
+// 2D pass 1 of component comp (y, inner c): T = H_iy G_comp(v), S = H_iy v_comp.
+template <typename T>
+struct OpP1V : OpBase<T> {
+    static constexpr int NF = 2;
+    static constexpr int NA = 1;
+    static constexpr int kAxes = 2;
+    static constexpr bool kReduce = false;
+    const T* v1;
+    const T* v2;
+    T* t_out;
+    T* s_out;
+    T s;
+    int comp;
+    __device__ __forceinline__ void load(int line, int pos, T (&f)[2]) const {
+        const size_t i = this->at(line, pos);
+        const T x1 = v1[i], x2 = v2[i];
+        f[0] = vch_lag(x1, x2, comp, s);
+        f[1] = comp == 0 ? x1 : x2;
+    }
+    __device__ __forceinline__ void fetch(int, int, T (&)[NA]) const {}
+    __device__ __forceinline__ void put(int line, int pos, const T (&h)[2], const T (&)[NA], RedAcc<T>&) const {
+        const size_t i = this->at(line, pos);
+        t_out[i] = h[0];
+        s_out[i] = h[1];
+    }
+};
+
+// 2D pass 2 of component comp (x, inner c): OpP2 with G_comp(v) in place of G(w).
+template <typename T>
+struct OpP2V : OpBase<T> {
+    static constexpr int NF = 2;
+    static constexpr int NA = 2;
+    static constexpr int kAxes = 1;
+    static constexpr bool kReduce = false;
+    const T* v1;
+    const T* v2;
+    const T* t_in;
+    const T* s_in;
+    T* p_out;
+    T* u_out;
+    T s, beta;
+    int comp;
+    __device__ __forceinline__ void load(int line, int pos, T (&f)[2]) const {
+        const size_t i = this->at(line, pos);
+        const T x1 = v1[i], x2 = v2[i];
+        f[0] = T(2) * t_in[i] - vch_lag(x1, x2, comp, s);
+        f[1] = (comp == 0 ? x1 : x2) - s_in[i];
+    }
+    __device__ __forceinline__ void fetch(int line, int pos, T (&a)[NA]) const {
+        const size_t i = this->at(line, pos);
+        a[0] = t_in[i];
+        a[1] = s_in[i];
+    }
+    __device__ __forceinline__ void put(int line, int pos, const T (&h)[2], const T (&a)[NA], RedAcc<T>&) const {
+        const size_t i = this->at(line, pos);
+        const T u = a[1] + h[1];
+        u_out[i] = u;
+        p_out[i] = fma(beta, h[0] - a[0], u);
+    }
+};
+
+// 1D pass a of component comp (inner c): E = H_i[beta G_comp(v)] - beta G_comp(v).
+template <typename T>
+struct Op1aV : OpBase<T> {
+    static constexpr int NF = 1;
+    static constexpr int NA = 2;
+    static constexpr int kAxes = 1;
+    static constexpr bool kReduce = false;
+    const T* v1;
+    const T* v2;
+    T* e_out;
+    T s, beta;
+    int comp;
+    __device__ __forceinline__ void load(int line, int pos, T (&f)[1]) const {
+        const size_t i = this->at(line, pos);
+        f[0] = beta * vch_lag(v1[i], v2[i], comp, s);
+    }
+    __device__ __forceinline__ void fetch(int line, int pos, T (&a)[NA]) const {
+        const size_t i = this->at(line, pos);
+        a[0] = v1[i];
+        a[1] = v2[i];
+    }
+    __device__ __forceinline__ void put(int line, int pos, const T (&h)[1], const T (&a)[NA], RedAcc<T>&) const {
+        e_out[this->at(line, pos)] = h[0] - beta * vch_lag(a[0], a[1], comp, s);
+    }
+};
+
 // Block-wide max of the two residual values, then one atomic max per block on the
 // bit patterns (non-negative doubles order like their unsigned bits).
 template <typename T>

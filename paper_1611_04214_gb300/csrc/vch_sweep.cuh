@@ -1,0 +1,26 @@
+// Vector Cahn-Hilliard passes (Sec. 5.2): the sweeps whose prologues evaluate the coupled lagged
+// term of one component from both state fields.  They run on the generic row and column kernels
+// and are profiled in the slots of their scalar counterparts.
+#pragma once
+#include "launch.cuh"
+
+namespace molt {
+
+template <typename T>
+cudaError_t sweep_vch(int axis, const LineParams<T>& lp, int kind, const OpArgs<T>& a, int nx, int ny,
+                      ColScratch<T>* cs, unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof) {
+    using namespace detail;
+    switch (kind) {
+        case OP_V1: return dispatch<T, OpP1V<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, OP_P1);
+        case OP_V2: return dispatch<T, OpP2V<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, OP_P2);
+        case OP_V1A: return dispatch<T, Op1aV<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, OP_1A);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace molt
+
+#define MOLT_INSTANTIATE_VCH(T)                                                                                   \
+    template cudaError_t molt::sweep_vch<T>(int, const molt::LineParams<T>&, int, const molt::OpArgs<T>&, int, int, \
+                                            molt::ColScratch<T>*, unsigned long long*, cudaStream_t, long long*,    \
+                                            molt::Prof*);

@@ -29,6 +29,7 @@ EXPORTS = [
     "molt_column_tma_launches", "molt_batch_create", "molt_batch_destroy", "molt_batch_points",
     "molt_batch_offsets", "molt_batch_set_execution", "molt_batch_step", "molt_selftest_bounded_wait",
     "molt_step_adaptive",
+    "molt_vch_step",
 ]
 EXECUTION = {"host_loop": 0, "graph": 1}
 PROFILE_SLOTS = 32
@@ -102,6 +103,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_column_tma_launches": ([], ctypes.c_longlong),
         "molt_selftest_bounded_wait": ([ctypes.POINTER(I), ctypes.POINTER(D)], I),
         "molt_step_adaptive": ([P, VP, D, ctypes.POINTER(_Adaptive), VP, ctypes.POINTER(_AdaptiveInfo)], I),
+        "molt_vch_step": ([P, VP, VP, D, I, VP, ctypes.POINTER(_StepInfo)], I),
         "molt_batch_create": ([ctypes.POINTER(VP), I, VP, I, I, D, I], I),
         "molt_batch_destroy": ([VP], I),
         "molt_batch_points": ([VP], ctypes.c_longlong),
@@ -263,6 +265,19 @@ class Solver:
         info = _StepInfo()
         st = self._lib.molt_step(self._h, self._field(u), float(dt), SCHEME[scheme], _stream_handle(stream),
                                  ctypes.byref(info))
+        out = StepInfo(info.status, info.stages, list(info.iters)[: max(info.stages, 0)], info.total_iters,
+                       info.residual, info.tol_used)
+        if st == MOLT_ERR_NOT_CONVERGED and not raise_on_nonconvergence:
+            return out
+        _check(st, self._h)
+        return out
+
+    def vch_step(self, u1, u2, dt: float, scheme: str = "be", stream=None,
+                 raise_on_nonconvergence: bool = True) -> StepInfo:
+        """One vector Cahn-Hilliard step (Sec. 5.2) in place on the two component fields."""
+        info = _StepInfo()
+        st = self._lib.molt_vch_step(self._h, self._field(u1), self._field(u2), float(dt), SCHEME[scheme],
+                                     _stream_handle(stream), ctypes.byref(info))
         out = StepInfo(info.status, info.stages, list(info.iters)[: max(info.stages, 0)], info.total_iters,
                        info.residual, info.tol_used)
         if st == MOLT_ERR_NOT_CONVERGED and not raise_on_nonconvergence:
