@@ -182,6 +182,14 @@ template <> struct PipeOf<OpP2<float>> { using type = PipeP2<float>; };
 template <> struct PipeOf<OpP4<float>> { using type = PipeP4<float>; };
 template <> struct PipeOf<Op1a<float>> { using type = Pipe1a<float>; };
 template <> struct PipeOf<Op1b<float>> { using type = Pipe1b<float>; };
+template <> struct PipeOf<OpP2V<float>> { using type = PipeP2V<float>; };
+template <> struct PipeOf<Op1aV<float>> { using type = Pipe1aV<float>; };
+
+// vector CH pipe forms carry (c1 + c2)/tau and the component; the scalar ones do not
+template <class P> inline void set_vch(P&, const OpArgs<float>&) {}
+inline void set_vch(PipeP2V<float>& p, const OpArgs<float>& a) { p.vs = a.vs; p.comp = a.comp; }
+inline void set_vch(Pipe1aV<float>& p, const OpArgs<float>& a) { p.vs = a.vs; p.comp = a.comp; }
+inline void set_vch(PipeP1V<float>& p, const OpArgs<float>& a) { p.vs = a.vs; p.comp = a.comp; }
 
 template <class P>
 P pipe_build(int kind, const OpArgs<float>& a) {
@@ -195,7 +203,12 @@ P pipe_build(int kind, const OpArgs<float>& a) {
         case OP_P4: p.s[0] = a.in0; p.s[1] = a.in2; p.a[0] = a.out0; p.a[1] = a.in3; p.a[2] = a.in1; p.o[0] = a.out0; break;
         case OP_1A: p.s[0] = a.in0; p.o[0] = a.out0; break;
         case OP_1B: p.s[0] = a.in0; p.a[0] = a.out0; p.a[1] = a.in1; p.o[0] = a.out0; break;
+        case OP_V2:
+            p.s[0] = a.in0; p.s[1] = a.in1; p.s[2] = a.in2; p.s[3] = a.in3; p.o[0] = a.out0; p.o[1] = a.out1;
+            break;
+        case OP_V1A: p.s[0] = a.in0; p.s[1] = a.in1; p.o[0] = a.out0; break;
     }
+    set_vch(p, a);
     return p;
 }
 
@@ -204,6 +217,8 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 template <class P>
 bool pipe_eligible(const P& p, int n) {
     if (n % 512 != 0 || n < 1024 || n > 8192) return false;
+    if (static_cast<long long>(2 * P::NS + P::NA) * n * static_cast<long long>(sizeof(float)) > kRowMaxSmem)
+        return false;   // staged lines do not fit (four staged fields at n = 8192)
     for (int f = 0; f < P::NS; ++f) if (!aligned16(p.s[f])) return false;
     for (int f = 0; f < P::NA; ++f) if (!aligned16(p.a[f])) return false;
     for (int f = 0; f < P::NO; ++f) if (!aligned16(p.o[f])) return false;
@@ -238,6 +253,7 @@ template <class Op> struct ColPipeOf { using type = void; };
 template <> struct ColPipeOf<OpCopy<float>> { using type = PipeCopy<float>; };
 template <> struct ColPipeOf<OpP1<float>> { using type = PipeP1<float>; };
 template <> struct ColPipeOf<OpP3<float>> { using type = PipeP3<float>; };
+template <> struct ColPipeOf<OpP1V<float>> { using type = PipeP1V<float>; };
 
 template <class P>
 P col_pipe_build(int kind, const OpArgs<float>& a) {
@@ -249,7 +265,9 @@ P col_pipe_build(int kind, const OpArgs<float>& a) {
         case OP_COPY: p.s[0] = a.in0; p.o[0] = a.out0; break;
         case OP_P1: p.s[0] = a.in0; p.o[0] = a.out0; p.o[1] = a.out1; break;
         case OP_P3: p.s[0] = a.in0; p.s[1] = a.in1; p.o[0] = a.out0; p.o[1] = a.out1; break;
+        case OP_V1: p.s[0] = a.in0; p.s[1] = a.in1; p.o[0] = a.out0; p.o[1] = a.out1; break;
     }
+    set_vch(p, a);
     return p;
 }
 
@@ -401,6 +419,8 @@ template <typename T, class Op>
 cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int nx, int ny, ColScratch<T>* cs,
                      unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof, int kind) {
     Op op = build(a, static_cast<Op*>(nullptr));
+    // the vector CH passes are timed in the slots of their scalar counterparts
+    const int pk = kind == OP_V1 ? OP_P1 : kind == OP_V2 ? OP_P2 : kind == OP_V1A ? OP_1A : kind;
     const int nlines = axis == 0 ? ny : nx;
     set_strides<T>(op, axis == 0 ? nx : 1, axis == 0 ? 1 : nx);
     if (launches) *launches += 1;
@@ -410,17 +430,17 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
             const P pop = pipe_build<P>(kind, a);
             if (pipe_eligible(pop, lp.n)) {
                 switch (lp.M) {
-                    case 2: return rows_pipe<2>(lp, pop, nlines, red, st, prof, kind);
-                    case 4: return rows_pipe<4>(lp, pop, nlines, red, st, prof, kind);
-                    case 6: return rows_pipe<6>(lp, pop, nlines, red, st, prof, kind);
+                    case 2: return rows_pipe<2>(lp, pop, nlines, red, st, prof, pk);
+                    case 4: return rows_pipe<4>(lp, pop, nlines, red, st, prof, pk);
+                    case 6: return rows_pipe<6>(lp, pop, nlines, red, st, prof, pk);
                 }
             }
         }
         if constexpr ((Op::kAxes & 1) != 0) {
             switch (lp.M) {
-                case 2: return rows<T, 2>(lp, op, nlines, red, st, prof, kind);
-                case 4: return rows<T, 4>(lp, op, nlines, red, st, prof, kind);
-                case 6: return rows<T, 6>(lp, op, nlines, red, st, prof, kind);
+                case 2: return rows<T, 2>(lp, op, nlines, red, st, prof, pk);
+                case 4: return rows<T, 4>(lp, op, nlines, red, st, prof, pk);
+                case 6: return rows<T, 6>(lp, op, nlines, red, st, prof, pk);
             }
         }
     } else {
@@ -431,23 +451,23 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
                 ColMaps maps;
                 if (cols_tma_enabled() && col_tma_maps(pop, nlines, lp.n, kColR + lp.M, &maps)) {
                     switch (lp.M) {
-                        case 2: return cols_tma<2>(lp, maps, pop, nlines, cs, red, st, launches, prof, kind);
-                        case 4: return cols_tma<4>(lp, maps, pop, nlines, cs, red, st, launches, prof, kind);
-                        case 6: return cols_tma<6>(lp, maps, pop, nlines, cs, red, st, launches, prof, kind);
+                        case 2: return cols_tma<2>(lp, maps, pop, nlines, cs, red, st, launches, prof, pk);
+                        case 4: return cols_tma<4>(lp, maps, pop, nlines, cs, red, st, launches, prof, pk);
+                        case 6: return cols_tma<6>(lp, maps, pop, nlines, cs, red, st, launches, prof, pk);
                     }
                 }
                 switch (lp.M) {
-                    case 2: return cols_pipe<2>(lp, pop, nlines, cs, red, st, launches, prof, kind);
-                    case 4: return cols_pipe<4>(lp, pop, nlines, cs, red, st, launches, prof, kind);
-                    case 6: return cols_pipe<6>(lp, pop, nlines, cs, red, st, launches, prof, kind);
+                    case 2: return cols_pipe<2>(lp, pop, nlines, cs, red, st, launches, prof, pk);
+                    case 4: return cols_pipe<4>(lp, pop, nlines, cs, red, st, launches, prof, pk);
+                    case 6: return cols_pipe<6>(lp, pop, nlines, cs, red, st, launches, prof, pk);
                 }
             }
         }
         if constexpr ((Op::kAxes & 2) != 0) {
             switch (lp.M) {
-                case 2: return cols<T, 2>(lp, op, nlines, cs, red, st, launches, prof, kind);
-                case 4: return cols<T, 4>(lp, op, nlines, cs, red, st, launches, prof, kind);
-                case 6: return cols<T, 6>(lp, op, nlines, cs, red, st, launches, prof, kind);
+                case 2: return cols<T, 2>(lp, op, nlines, cs, red, st, launches, prof, pk);
+                case 4: return cols<T, 4>(lp, op, nlines, cs, red, st, launches, prof, pk);
+                case 6: return cols<T, 6>(lp, op, nlines, cs, red, st, launches, prof, pk);
             }
         }
     }

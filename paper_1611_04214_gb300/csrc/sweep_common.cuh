@@ -611,6 +611,49 @@ struct Pipe1b {
     }
 };
 
+// vector CH pass 2 of component comp: staged v1, v2, T, S; outputs P, U (see OpP2V)
+template <typename T>
+struct PipeP2V {
+    static constexpr int NS = 4, NA = 0, NF = 2, NO = 2;
+    static constexpr bool kReduce = false;
+    const T* s[NS];
+    const T* a[1];
+    T* o[NO];
+    T g2, g1, beta;
+    T vs;
+    int comp;
+    __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const {
+        f[0] = T(2) * sv[2] - vch_lag(sv[0], sv[1], comp, vs);
+        f[1] = (comp == 0 ? sv[0] : sv[1]) - sv[3];
+    }
+    __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&sv)[NS], const T (&)[1], T (&ov)[NO],
+                                             RedAcc<T>&) const {
+        const T u = sv[3] + h[1];
+        ov[0] = fma(beta, h[0] - sv[2], u);
+        ov[1] = u;
+    }
+};
+
+// vector CH 1D pass a of component comp: staged v1, v2; output E (see Op1aV)
+template <typename T>
+struct Pipe1aV {
+    static constexpr int NS = 2, NA = 0, NF = 1, NO = 1;
+    static constexpr bool kReduce = false;
+    const T* s[NS];
+    const T* a[1];
+    T* o[NO];
+    T g2, g1, beta;
+    T vs;
+    int comp;
+    __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const {
+        f[0] = beta * vch_lag(sv[0], sv[1], comp, vs);
+    }
+    __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&sv)[NS], const T (&)[1], T (&ov)[NO],
+                                             RedAcc<T>&) const {
+        ov[0] = h[0] - beta * vch_lag(sv[0], sv[1], comp, vs);
+    }
+};
+
 // Ampere-style asynchronous 16-byte global -> shared copies (LDGSTS), grouped and awaited.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -642,6 +685,29 @@ struct PipeP1 {
     __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const {
         f[0] = g_lag(sv[0], g2, g1);
         f[1] = sv[0];
+    }
+    __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&)[NS], const T (&)[1], T (&ov)[NO],
+                                             RedAcc<T>&) const {
+        ov[0] = h[0];
+        ov[1] = h[1];
+    }
+};
+
+// vector CH pass 1 of component comp (y, inner c): staged v1, v2; sweep G_comp(v), v_comp;
+// outputs T, S (see OpP1V)
+template <typename T>
+struct PipeP1V {
+    static constexpr int NS = 2, NA = 0, NF = 2, NO = 2;
+    static constexpr bool kReduce = false;
+    const T* s[NS];
+    const T* a[1];
+    T* o[NO];
+    T g2, g1, beta;
+    T vs;
+    int comp;
+    __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const {
+        f[0] = vch_lag(sv[0], sv[1], comp, vs);
+        f[1] = comp == 0 ? sv[0] : sv[1];
     }
     __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&)[NS], const T (&)[1], T (&ov)[NO],
                                              RedAcc<T>&) const {

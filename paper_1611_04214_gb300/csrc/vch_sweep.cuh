@@ -1,6 +1,7 @@
 // Vector Cahn-Hilliard passes (Sec. 5.2): the sweeps whose prologues evaluate the coupled lagged
-// term of one component from both state fields.  They run on the generic row and column kernels
-// and are profiled in the slots of their scalar counterparts.
+// term of one component from both state fields.  In FP32 they take the pipelined row kernel and
+// the TMA column kernel where those apply (the generic kernels otherwise), and they are profiled
+// in the slots of their scalar counterparts.
 #pragma once
 #include "launch.cuh"
 
@@ -11,9 +12,9 @@ cudaError_t sweep_vch(int axis, const LineParams<T>& lp, int kind, const OpArgs<
                       ColScratch<T>* cs, unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof) {
     using namespace detail;
     switch (kind) {
-        case OP_V1: return dispatch<T, OpP1V<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, OP_P1);
-        case OP_V2: return dispatch<T, OpP2V<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, OP_P2);
-        case OP_V1A: return dispatch<T, Op1aV<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, OP_1A);
+        case OP_V1: return dispatch<T, OpP1V<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
+        case OP_V2: return dispatch<T, OpP2V<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
+        case OP_V1A: return dispatch<T, Op1aV<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
     }
     return cudaErrorInvalidValue;
 }

@@ -96,12 +96,19 @@ def test_vch_fp64_parity_2d_square_regime():
     assert max(np.abs(g1 - o1).max(), np.abs(g2 - o2).max()) < 1e-10
 
 
-@pytest.mark.parametrize("dims", [(1000, 1), (256, 200)])
-def test_vch_fp32_parity(dims):
+# (1000, 1) and (256, 200) run the generic kernels; (1024, 1) and (1024, 40) the pipelined row
+# kernel (vector passes a and 2); (64, 288) the TMA column kernel (vector pass 1) over three tiles
+@pytest.mark.parametrize("dims", [(1000, 1), (256, 200), (1024, 1), (1024, 40), (64, 288)])
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+def test_vch_fp32_parity(dims, bc):
+    from paper_1611_04214_gb300 import molt
     nx, ny = dims
-    (g1, g2), (o1, o2), _, _, _ = _run_both(nx, ny, "periodic", "bdf2", 2e-3, 3, precision="fp32", tol=1e-7)
+    t0 = molt.molt_column_tma_launches()
+    (g1, g2), (o1, o2), _, _, _ = _run_both(nx, ny, bc, "bdf2", 2e-3, 3, precision="fp32", tol=1e-7)
     # FP32 rounding of the fields (|u| <= 1.2) amplified by the stage solves; the oracle converges to 1e-7
     assert max(np.abs(g1 - o1).max(), np.abs(g2 - o2).max()) < 2e-5
+    if dims == (64, 288):
+        assert molt.molt_column_tma_launches() > t0
 
 
 def test_vch_paper_configuration():
