@@ -54,6 +54,18 @@ def gaussian_noise(shape, amp: float, seed: int, mean: float = 0.0) -> np.ndarra
     return (mean + amp * z).reshape(shape)
 
 
+def three_phase_mixture(shape, seed: int):
+    """A random three-phase mixture for the two-component (vector) model: per node, phase fractions
+    (p1, p2, p3) ~ Dirichlet(1, 1, 1) (normalised Exp(1) draws from SplitMix64 uniforms), placed at
+    the fractions' barycentre of the three phase values, the cube roots of unity of the (u1, u2)
+    plane.  Returns (u1, u2) of ``shape``."""
+    count = int(np.prod(shape))
+    e = -np.log(1.0 - uniform01(seed, 3 * count).reshape(count, 3))   # Exp(1), finite
+    p = e / e.sum(axis=1, keepdims=True)
+    ang = np.array([0.0, 2.0 * np.pi / 3.0, -2.0 * np.pi / 3.0])
+    return (p @ np.cos(ang)).reshape(shape), (p @ np.sin(ang)).reshape(shape)
+
+
 def spacing(n: int, length: float, periodic: bool) -> float:
     """Node spacing for ``n`` stored nodes on a line of ``length``."""
     return length / n if periodic else length / (n - 1)

@@ -146,3 +146,28 @@ def test_vch_arguments_and_scalar_state():
             b_info = fresh.step(v, 1e-4, "bdf2", raise_on_nonconvergence=False)
             assert a_info.iters == b_info.iters
         assert torch.equal(u, v)
+
+
+def test_vch_three_phase_mixture_crop_fixed_iterations():
+    # The shape of the 4096^2 three-phase workload on a 96 x 80 Neumann crop with its node spacing
+    # (2pi/4095), eps = 0.03 and a Dirichlet(1, 1, 1) mixture: one BE start and two BDF2 steps of
+    # dt = 1e-6, each stage capped at 40 fixed-point iterations (the grid-scale mixture contracts
+    # slowly), on both sides the same iterations.
+    from paper_1611_04214_gb300.inputs import three_phase_mixture
+    from paper_1611_04214_gb300.molt import Solver
+    nx, ny, h = 96, 80, 2 * np.pi / 4095
+    prob = Problem(nx=nx, ny=ny, Lx=(nx - 1) * h, Ly=(ny - 1) * h, bc="neumann", eps=0.03, M=4, tol=1e-14,
+                   max_iter=40)
+    u1, u2 = three_phase_mixture((ny, nx), seed=7)
+    o = VchSolver(prob)
+    r1, r2 = u1, u2
+    g1 = torch.tensor(u1, device="cuda")
+    g2 = torch.tensor(u2, device="cuda")
+    with Solver(nx=nx, ny=ny, Lx=prob.Lx, Ly=prob.Ly, bc="neumann", eps=0.03, quad_order=4, precision="fp64",
+                tol=1e-14, max_iter=40) as s:
+        for _ in range(3):
+            info = s.vch_step(g1, g2, 1e-6, "bdf2", raise_on_nonconvergence=False)
+            r1, r2, oinfo = o.step(r1, r2, 1e-6, "bdf2")
+            assert info.iters[0] == oinfo.iters[0] == 40
+        got = (g1.cpu().numpy(), g2.cpu().numpy())
+    assert max(np.abs(got[0] - r1).max(), np.abs(got[1] - r2).max()) < 1e-11
