@@ -171,3 +171,16 @@ def test_paper_initial_state_stage_converges():
     v1, v2 = u1 - Z3[0], u2 - Z3[1]
     res = vch_stage_solve(prob, v1, v2, v1, v2, 1e-4)
     assert res.converged and res.iters < 400
+
+
+def test_dirichlet_walls_hold_z3():
+    # Boundary conditions apply to v = u - z3, so homogeneous Dirichlet walls hold u = z3 after a step.
+    n = 64
+    prob = Problem(nx=n, bc="dirichlet", eps=0.32, M=4, tol=1e-12, max_iter=500)
+    x = nodes(n, 2 * np.pi, False)[None, :]
+    u1 = Z3[0] + 0.1 * np.sin(x / 2)
+    u2 = Z3[1] + 0.05 * np.sin(x)
+    n1, n2, info = VchSolver(prob).step(u1, u2, 1e-3, "be")
+    assert info.converged
+    for a, z in ((n1, Z3[0]), (n2, Z3[1])):
+        assert abs(a[0, 0] - z) < 1e-13 and abs(a[0, -1] - z) < 1e-13
