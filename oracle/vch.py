@@ -28,6 +28,8 @@ Readings:
   model).
 - **Energy.** The scalar edge / trapezoid rule over both components, with W(u) in place of F(u)
   (Eq. EnergyFunctional_vector).
+- **Adaptive steps** (``vch_adaptive_step``): Algorithm 1 with the Richardson or BE-BDF2 estimate,
+  as in the paper's vector run (Sec. 6.2.2); readings in its docstring.
 """
 from __future__ import annotations
 
@@ -165,5 +167,55 @@ def vch_energy(prob: Problem, u1: np.ndarray, u2: np.ndarray) -> float:
     return prob.hx * prob.hy * (0.5 * eps2 * (gx + gy) + np.sum(wy[:, None] * wx[None, :] * pot))
 
 
+def vch_adaptive_step(solver: VchSolver, u1, u2, dt: float, tol: float, dt_min: float, dt_max: float,
+                      theta: float = 0.8, gamma: float = 1.3, estimator: str = "bdf2", history: dict | None = None):
+    """One accepted step of the vector model under Algorithm 1 (Sec. 5), as the paper runs it in
+    Sec. 6.2.2.  Returns (u1, u2, AdaptiveInfo).
+
+    Readings:
+    - **Estimators.** "richardson": BE with two half steps, eta = (1/2) max|u_dt - u_dt/2| over both
+      components; the half-step solution is kept.  "bdf2" (BE-BDF2): one BE step and one
+      variable-step BDF2 step from the previous accepted state; eta = max|u_BDF2 - u_BE| and the
+      BDF2 solution is kept.
+    - **First step.** The vector model has no SDC2 here, so a BE-BDF2 step without history takes
+      the Richardson estimate.
+    - **History.** ``history`` is a dict holding the previous accepted state ("u1", "u2") and its
+      step ("dt"); an accepted step updates it.
+    """
+    from .adaptive import AdaptiveInfo, bdf2_variable, decide
+    if estimator not in ("richardson", "bdf2"):
+        raise ValueError(estimator)
+    if estimator == "bdf2" and history is None:
+        raise ValueError("the BE-BDF2 estimate needs a history dict")
+    prob = solver.prob
+    rejections = 0
+    while True:
+        if estimator == "bdf2" and history.get("u1") is not None:
+            b1, b2, ib = VchSolver(prob).step(u1, u2, dt, "be")
+            tau, a_n, a_prev = bdf2_variable(dt, history["dt"])
+            v1, v2 = np.asarray(u1, dtype=np.float64) - Z3[0], np.asarray(u2, dtype=np.float64) - Z3[1]
+            p1, p2 = history["u1"] - Z3[0], history["u2"] - Z3[1]
+            res = vch_stage_solve(prob, a_n * v1 + a_prev * p1, a_n * v2 + a_prev * p2, v1, v2, tau)
+            c1, c2 = res.v1 + Z3[0], res.v2 + Z3[1]
+            eta = float(max(np.max(np.abs(c1 - b1)), np.max(np.abs(c2 - b2))))
+            n_it = max(ib.iters[0], res.iters)
+        else:
+            f1, f2, i1 = VchSolver(prob).step(u1, u2, dt, "be")
+            h1, h2, i2 = VchSolver(prob).step(u1, u2, 0.5 * dt, "be")
+            c1, c2, i3 = VchSolver(prob).step(h1, h2, 0.5 * dt, "be")
+            eta = 0.5 * float(max(np.max(np.abs(f1 - c1)), np.max(np.abs(f2 - c2))))
+            n_it = max(i1.iters[0], i2.iters[0], i3.iters[0])
+        ok, dt_next = decide(eta, tol, n_it, prob.max_iter, dt, theta, gamma)
+        dt_next = min(max(dt_next, dt_min), dt_max)
+        if ok:
+            if history is not None:
+                history.update(u1=np.array(u1, dtype=np.float64), u2=np.array(u2, dtype=np.float64), dt=dt)
+            return c1, c2, AdaptiveInfo(dt, dt_next, eta, rejections, n_it)
+        rejections += 1
+        if dt <= dt_min:
+            raise RuntimeError("adaptive step: dt reached dt_min without meeting the LTE tolerance")
+        dt = dt_next
+
+
 __all__ = ["Z3", "cube_roots", "W", "grad_W", "vch_stage_params", "G_vec", "vch_stage_solve", "VchSolver",
-           "vch_energy", "PERIODIC"]
+           "vch_energy", "vch_adaptive_step", "PERIODIC"]

@@ -184,3 +184,49 @@ def test_dirichlet_walls_hold_z3():
     assert info.converged
     for a, z in ((n1, Z3[0]), (n2, Z3[1])):
         assert abs(a[0, 0] - z) < 1e-13 and abs(a[0, -1] - z) < 1e-13
+
+
+@pytest.mark.parametrize("estimator", ["richardson", "bdf2"])
+def test_vch_lte_estimates_scale_as_dt_squared(estimator):
+    # Both estimates are dominated by BE's local error, O(dt^2): halving dt divides eta by a factor
+    # that tends to 4 (from below here: the stiff modes are not yet asymptotic).
+    from oracle.vch import vch_adaptive_step
+    n = 64
+    prob = Problem(nx=n, eps=0.32, M=6, tol=1e-14, max_iter=3000)
+    x = nodes(n, 2 * np.pi, True)[None, :]
+    u1, u2 = Z3[0] + 0.1 * np.cos(x), Z3[1] + 0.1 * np.sin(2 * x)
+    etas = []
+    for dt in (5e-5, 2.5e-5, 1.25e-5):
+        hist = None
+        if estimator == "bdf2":
+            p1, p2, _ = VchSolver(prob).step(u1, u2, dt, "be")      # history: one BE step of the same size
+            hist, a1, a2 = {"u1": u1, "u2": u2, "dt": dt}, p1, p2
+        else:
+            a1, a2 = u1, u2
+        _, _, info = vch_adaptive_step(VchSolver(prob), a1, a2, dt, 1.0, 1e-9, 1.0, estimator=estimator,
+                                       history=hist)
+        etas.append(info.eta)
+    r1, r2 = etas[0] / etas[1], etas[1] / etas[2]
+    assert 3.5 < r1 < 4.1 and 3.7 < r2 < 4.1 and r2 > r1, (r1, r2)
+
+
+def test_vch_adaptive_run_keeps_mass_and_lowers_energy():
+    from oracle.solver import mass
+    from oracle.vch import vch_adaptive_step
+    n = 48
+    prob = Problem(nx=n, ny=n, eps=0.32, M=4, tol=1e-10, max_iter=400)
+    x = nodes(n, 2 * np.pi, True)[None, :]
+    y = nodes(n, 2 * np.pi, True)[:, None]
+    u1 = Z3[0] + 0.1 * np.cos(x) * np.cos(y)
+    u2 = Z3[1] + 0.1 * np.sin(x + y)
+    e0, m0 = vch_energy(prob, u1, u2), (mass(prob, u1), mass(prob, u2))
+    hist, dt, t = {}, 1e-4, 0.0
+    s = VchSolver(prob)
+    for _ in range(6):
+        u1, u2, info = vch_adaptive_step(s, u1, u2, dt, 1e-4, 1e-8, 0.1, estimator="bdf2", history=hist)
+        assert info.eta <= 1e-4
+        t += info.dt_used
+        dt = info.dt_next
+    assert t > 6e-4                      # the controller grew the step
+    assert vch_energy(prob, u1, u2) < e0
+    assert abs(mass(prob, u1) - m0[0]) < 1e-9 and abs(mass(prob, u2) - m0[1]) < 1e-9
