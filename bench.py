@@ -14,6 +14,13 @@ tolerance it cannot reach in practical time.
 value = line-sweep points per second (Gpts/s) over the whole step: sum of field sweeps x
 points / device time.  Every field is 256 MiB, larger than the 129 MB L2, so no flush is
 needed between steps.
+
+Side legs on the same JSON line:
+- the FP64 GPU path on the same start;
+- 512 batched instances;
+- single sweeps;
+- the vector (three-phase) model at 4096^2 on a Neumann three-phase mixture (``vector_ch``).
+  ``--vch-only`` runs just that leg, and its 64 MiB fields also exceed L2.
 """
 from __future__ import annotations
 
