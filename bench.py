@@ -302,8 +302,15 @@ def batched_leg(args, sample: int = 16):
     return out
 
 
-VCH = dict(name="vch2d_4096_neumann_mixture_bdf2", n=4096, L=2 * 3.141592653589793, eps=0.03, dt=1e-6, M=4,
-           bc="neumann", seed=0)
+VCH_WORKLOADS = {
+    # the three-phase mixture workload (the default)
+    "mixture": dict(name="vch2d_4096_neumann_mixture_bdf2", n=4096, L=2 * 3.141592653589793, eps=0.03, dt=1e-6,
+                    M=4, bc="neumann", seed=0, ic="mixture"),
+    # the paper's vector run (Sec. 6.2.2) tiled 64 x 64 at its node spacing 2pi/64
+    "paper_tiled": dict(name="vch2d_4096_bdf2_periodic", n=4096, L=2 * 3.141592653589793 * 64, eps=0.32, dt=1e-4,
+                        M=4, bc="periodic", seed=0, ic="paper"),
+}
+VCH = dict(VCH_WORKLOADS["mixture"])
 # field words moved per point by one vector CH iteration (two components): passes 1-4 of each
 # component read / write 2+2, 4+2, 2+2 and 5+1 fields; each stage's rhs inverses 4 x (1+1) per component
 VCH_WORDS_ITER, VCH_WORDS_RHS = 40, 16
@@ -318,24 +325,35 @@ VCH_KERNEL_FIELDS = {
 
 
 def vch_leg(args, steps: int = 3):
-    """The vector (three-phase) model of Sec. 5.2 at scale: 4096^2 nodes on [0, 2pi]^2 with
-    Neumann walls, eps = 0.03, a random three-phase mixture (per-node Dirichlet(1, 1, 1) phase
-    fractions placed at their barycentre of the three phase values, seed 0).  The method has no
-    fourth-order SDC or energy-based step control here, so the steps are BDF2 at dt = 1e-6, the
-    smallest step of that range, after one BE start, with the main workload's fixed-point
-    iteration cap.  FP32 device time per step, the algorithmic HBM fraction of the step, and the
-    largest difference from the FP64 path over the same steps."""
+    """The vector (three-phase) model of Sec. 5.2 at scale.  Default workload: 4096^2 nodes on
+    [0, 2pi]^2 with Neumann walls, eps = 0.03, a random three-phase mixture (per-node
+    Dirichlet(1, 1, 1) phase fractions placed at their barycentre of the three phase values,
+    seed 0).  The method has no fourth-order SDC or energy-based step control here, so the steps
+    are BDF2 at dt = 1e-6, the smallest step of that range, after one BE start, with the main
+    workload's fixed-point iteration cap.  ``--vch-workload paper_tiled`` runs instead the paper's
+    vector run (u1 from Eq. CH2D_initial, u2 = sin y, eps = 0.32, periodic) tiled 64 x 64 at its
+    node spacing, BDF2 at dt = 1e-4.  FP32 device time per step, the algorithmic HBM fraction of
+    the step, and the largest difference from the FP64 path over the same steps."""
     import numpy as np
     import torch
 
     from paper_1611_04214_gb300.inputs import three_phase_mixture
     from paper_1611_04214_gb300.molt import Solver
+    VCH.clear()
+    VCH.update(VCH_WORKLOADS[getattr(args, "vch_workload", "mixture")])
     n, L = VCH["n"], VCH["L"]
-    u10, u20 = three_phase_mixture((n, n), seed=VCH["seed"])
+    if VCH["ic"] == "mixture":
+        u10, u20 = three_phase_mixture((n, n), seed=VCH["seed"])
+    else:
+        x = (L / n) * np.arange(n)
+        sxy = np.sin(x)[None, :] + np.sin(x)[:, None]
+        u10 = 2 * np.exp(sxy - 2) + 2.2 * np.exp(-sxy - 2) - 1
+        u20 = np.broadcast_to(np.sin(x)[:, None], (n, n))
     peak, _ = _peaks()
     out = {"workload": VCH["name"], "grid": [n, n], "bc": VCH["bc"], "eps": VCH["eps"], "dt": VCH["dt"],
            "scheme": "bdf2", "iters_cap": args.iters,
-           "initial_state": "per-node Dirichlet(1,1,1) three-phase fractions, seed 0"}
+           "initial_state": ("per-node Dirichlet(1,1,1) three-phase fractions, seed 0" if VCH["ic"] == "mixture"
+                             else "u1 = Eq. CH2D_initial, u2 = sin y, tiled 64 x 64")}
     fields = {}
 
     def run(s, timed_profile):
@@ -582,6 +600,8 @@ def main():
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched-instances leg")
     ap.add_argument("--skip-sweeps", action="store_true", help="skip the single-sweep microbenchmark")
     ap.add_argument("--skip-vch", action="store_true", help="skip the vector Cahn-Hilliard leg")
+    ap.add_argument("--vch-workload", default="mixture", choices=sorted(VCH_WORKLOADS),
+                    help="vector-model workload of the vector_ch leg")
     ap.add_argument("--vch-only", action="store_true",
                     help="run only the vector Cahn-Hilliard leg and print its JSON (for profiling)")
     ap.add_argument("--batch-iters", type=int, default=40, help="fixed-point iteration cap of the batched leg")
