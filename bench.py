@@ -573,7 +573,12 @@ def run_ours(args, rank, world, dist):
         fp64 = fp64_comparison(args, u0) if (args.precision == "fp32" and not args.skip_fp64) else None
         batched = None if args.skip_batch else batched_leg(args)
         sweeps_mb = None if args.skip_sweeps else sweep_microbench()
-        vch = None if args.skip_vch else vch_leg(args)
+        vch = None
+        if not args.skip_vch:
+            try:
+                vch = vch_leg(args)
+            except Exception as exc:   # a side leg records its failure instead of costing the main line
+                vch = {"error": f"{type(exc).__name__}: {exc}"}
         last = infos[-1]
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                   "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
