@@ -170,13 +170,23 @@ molt_status molt_quadrature_weights(double nu, int M, const int* offsets, int si
  * quadrature order are those of molt_grid_create / molt_params, with Ly the column length.
  * The scan's scratch is a 4 MiB file-scope device array, held by every GPU that loads the
  * library until the process exits; grids need ceil(ny/128) * nx <= 262144, otherwise
- * MOLT_ERR_ARG.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share
- * the array: each call writes the
- * scratch before reading it, and calls that overlap on the GPU race on it.  Errors are reported
- * by molt_last_error(NULL). */
+ * MOLT_ERR_ARG.  Outside stream capture every call looks up the array's device address
+ * (cudaGetSymbolAddress) in the current context; a call made while `stream` is capturing reuses
+ * the address of the last uncaptured call on that device, so make the first call on each device
+ * before any stream capture.  All calls share the array: each call writes the scratch before
+ * reading it, and calls that overlap on the GPU race on it.  Each call also clears, on `stream`,
+ * a device status word that its column kernels set when a bounded wait for a tile copy ran out
+ * of time (read it with molt_helmholtz_columns_noalloc_status).  Errors are reported by
+ * molt_last_error(NULL). */
 molt_status molt_helmholtz_columns_noalloc(int nx, int ny, double Ly, int bc, int quad_order, double c,
                                            const float* in_dev, float* out_dev, void* stream);
+
+/* Status of the last molt_helmholtz_columns_noalloc call (no counterpart in the paper).
+ * Synchronizes `stream` and writes the device status word to *status: 0 when every column
+ * kernel of that call completed its tiles; bit 0 set when a tile copy did not arrive within its
+ * one-second wait, in which case that call's output is incomplete and must not be used.
+ * Allocates nothing.  Errors: MOLT_ERR_ARG (null status), MOLT_ERR_CUDA. */
+molt_status molt_helmholtz_columns_noalloc_status(void* stream, unsigned* status);
 
 /* ---- Vector Cahn-Hilliard (Sec. 5.2, Eq. CH_vector) -----------------------------------------
  * One step of the three-phase vector model u_t = -Lap[eps^2 Lap u - grad W(u)], u = (u1, u2),

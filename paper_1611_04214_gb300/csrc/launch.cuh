@@ -21,6 +21,7 @@ constexpr int kRowMaxSmem = 225 * 1024;   // planning bound (opt-in limit minus 
 constexpr int kColKY = 16;   // positions per thread in a column tile
 constexpr int kColWY = 8;    // warps per column tile
 constexpr int kColR = kColKY * kColWY;
+static_assert(kColR == kColTileRows, "column tile height must match the scratch sizing constant");
 
 template <typename T>
 inline void set_strides(OpBase<T>& o, long long ls, long long ps) {

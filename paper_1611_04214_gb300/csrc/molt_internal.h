@@ -13,6 +13,7 @@ namespace molt {
 enum Bc { BC_PERIODIC = 0, BC_NEUMANN = 1, BC_DIRICHLET = 2 };
 
 constexpr int kMaxM = 6;           // largest quadrature order
+constexpr int kColTileRows = 128;  // rows per column tile of the column sweep kernels
 constexpr int kMaxStencil = kMaxM + 1;
 constexpr int kMaxWall = kMaxM / 2;
 

@@ -54,6 +54,21 @@ def gaussian_noise(shape, amp: float, seed: int, mean: float = 0.0) -> np.ndarra
     return (mean + amp * z).reshape(shape)
 
 
+def gaussian_noise_block(shape, rows: int, cols: int, amp: float, seed: int, mean: float = 0.0) -> np.ndarray:
+    """The top-left ``rows`` x ``cols`` block of ``gaussian_noise(shape, ...)`` without drawing the
+    rest of the field (a crop of a large initial state).  Needs rows * shape[1] <= half the field,
+    where every value of the block is the cosine half of its Box-Muller pair."""
+    ny, nx = shape
+    count = ny * nx
+    m = (count + 1) // 2
+    k = rows * nx
+    if rows > ny or cols > nx or k > m:
+        raise ValueError("the block must lie within the first half of the field")
+    u = uniform01(seed, 2 * k)
+    z = np.sqrt(-2.0 * np.log(1.0 - u[0::2])) * np.cos(2 * np.pi * u[1::2])
+    return (mean + amp * z).reshape(rows, nx)[:, :cols].copy()
+
+
 def three_phase_mixture(shape, seed: int):
     """A random three-phase mixture for the two-component (vector) model: per node, phase fractions
     (p1, p2, p3) ~ Dirichlet(1, 1, 1) (normalised Exp(1) draws from SplitMix64 uniforms), placed at

@@ -25,7 +25,7 @@ EXPORTS = [
     "molt_set_params", "molt_set_bc", "molt_reset_history", "molt_step", "molt_run_host",
     "molt_energy", "molt_mass", "molt_helmholtz_apply", "molt_quadrature_weights",
     "molt_last_error", "molt_kernel_launches", "molt_profile_enable", "molt_profile_collect",
-    "molt_helmholtz_columns_noalloc", "molt_set_execution", "molt_graph_fallbacks",
+    "molt_helmholtz_columns_noalloc", "molt_helmholtz_columns_noalloc_status", "molt_set_execution", "molt_graph_fallbacks",
     "molt_column_tma_launches", "molt_batch_create", "molt_batch_destroy", "molt_batch_points",
     "molt_batch_offsets", "molt_batch_set_execution", "molt_batch_step", "molt_selftest_bounded_wait",
     "molt_step_adaptive",
@@ -98,6 +98,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_profile_enable": ([P, I], I),
         "molt_profile_collect": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)], I),
         "molt_helmholtz_columns_noalloc": ([I, I, D, I, I, D, VP, VP, VP], I),
+        "molt_helmholtz_columns_noalloc_status": ([VP, ctypes.POINTER(ctypes.c_uint)], I),
         "molt_set_execution": ([P, I], I),
         "molt_graph_fallbacks": ([P], ctypes.c_longlong),
         "molt_column_tma_launches": ([], ctypes.c_longlong),
@@ -148,6 +149,13 @@ def molt_helmholtz_columns_noalloc(nx: int, ny: int, Ly: float, bc: str, quad_or
     _check(lib.molt_helmholtz_columns_noalloc(int(nx), int(ny), float(Ly), BC[bc], int(quad_order), float(c),
                                               ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                               _stream_handle(stream)))
+
+
+def molt_helmholtz_columns_noalloc_status(stream=None) -> int:
+    """Status word of the last allocation-free column sweep (0 = complete; see include/molt.h)."""
+    word = ctypes.c_uint(0)
+    _check(load_library().molt_helmholtz_columns_noalloc_status(_stream_handle(stream), ctypes.byref(word)))
+    return int(word.value)
 
 
 def molt_column_tma_launches() -> int:

@@ -3,8 +3,8 @@
 For instances whose rows are shorter than 1024 nodes and whose columns are shorter than 256, the
 single-instance solver runs the same general row / column block bodies, the same stopping rule
 and the same pointwise kernels as the batched passes, so every instance of a batch must match a
-single-instance run of the same problem bit for bit, iteration counts included.  The oracle
-bounds both with the FP32 fixed-point bar of test_gpu_parity.
+single-instance run of the same problem bit for bit, iteration counts included.  Against the
+oracle, every instance is held to 1e-6 of max|u + 1| (tests/_parity.py).
 """
 import numpy as np
 import pytest
@@ -15,6 +15,11 @@ pytestmark = pytest.mark.gpu
 
 from oracle.solver import OracleSolver, Problem  # noqa: E402
 from paper_1611_04214_gb300.inputs import uniform_noise  # noqa: E402
+
+from _parity import check_fp32  # noqa: E402
+
+# converged cases whose contraction factor puts 1e-6 below the FP32 rounding floor
+BATCH_RHO_LIMITED: set = set()
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -88,20 +93,27 @@ def test_batch_graph_equals_host_loop(bc):
         assert np.array_equal(x, y)
 
 
-def _posteriori_bar(ref, bc, rho, residuals):
-    """Error bound of a converged FP32 step sequence against the FP64 fixed points.  For a
-    contraction with factor rho, an iterate whose last change was res lies within
-    (rho res + delta) / (1 - rho) of the fixed point, delta the rounding of one evaluation of the
-    map (a few ulp of max|w|, w = u or u + 1 on Dirichlet grids); the steps' errors add up.
-    Never below the 1e-6 relative target on v = u + 1."""
-    w = ref if bc != "dirichlet" else ref + 1
-    ulp = 2.0 ** -24 * np.abs(w).max()
-    bound = sum((rho * r + 8 * ulp) / max(1e-3, 1 - rho) for r in residuals)
-    return max(1e-6 * np.abs(ref + 1).max(), bound)
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+def test_batch_matches_oracle_fixed_iterations(bc):
+    # Every instance and the oracle run the same 8 fixed-point iterations per stage (the FP32 stop
+    # rules never fire that early), so the difference is the FP32 rounding of the batched passes,
+    # held to 1e-6 of max|u + 1|.
+    u0, out, infos = _run_batch(bc, "be", 2, tol=1e-30, max_iter=8)
+    for i in range(len(INSTANCES)):
+        nx, ny, Lx, Ly, eps, dt = INSTANCES[i]
+        o = OracleSolver(Problem(nx=nx, ny=ny, Lx=Lx, Ly=Ly, bc=bc, eps=eps, M=4, tol=1e-30, max_iter=8))
+        u = u0[i].astype(np.float64)
+        for k in range(2):
+            u, info = o.step(u, dt, "be")
+            assert infos[k].iters[i] == info.iters[0] == 8
+        check_fp32(f"batch_instance{i}_{nx}x{ny}_{bc}_be_2steps_8it", out[i], u, np.abs(u + 1).max())
 
 
 @pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
-def test_batch_matches_oracle(bc):
+def test_batch_matches_oracle_converged(bc):
+    # Converged steps (tolerance 1e-10, which FP32 replaces by its rounding floor) against the
+    # oracle converged to 1e-11; instances whose iteration contracts slowly are rho-limited
+    # (tests/_parity.py) and named in BATCH_RHO_LIMITED.
     u0, out, infos = _run_batch(bc, "be", 2, tol=1e-10, max_iter=3000)
     for i in (0, 3, 4):
         nx, ny, Lx, Ly, eps, dt = INSTANCES[i]
@@ -112,9 +124,11 @@ def test_batch_matches_oracle(bc):
         for _ in range(2):
             u, info = o.step(u, dt, "be")
             rho = max(rho, info.contraction)
-        err = np.abs(out[i] - u).max()
-        bar = _posteriori_bar(u, bc, rho, [inf.residual[i] for inf in infos])
-        assert err <= bar, (i, err, bar, rho, [inf.residual[i] for inf in infos])
+        case = f"batch_instance{i}_{nx}x{ny}_{bc}_be_2steps_converged"
+        w = u if bc != "dirichlet" else u + 1
+        check_fp32(case, out[i], u, np.abs(u + 1).max(), rho,
+                   rho_limited_w=np.abs(w).max() if case in BATCH_RHO_LIMITED else None,
+                   residuals=[float(inf.residual[i]) for inf in infos])
 
 
 def test_batch_arguments_and_status():

@@ -23,3 +23,10 @@ def test_three_phase_mixture_statistics_and_seeding():
     a1, a2 = three_phase_mixture((10, 10), seed=11)
     b1, _ = three_phase_mixture((10, 10), seed=12)
     assert np.array_equal(a1, three_phase_mixture((10, 10), seed=11)[0]) and not np.array_equal(a1, b1)
+
+
+def test_gaussian_noise_block_is_the_crop_of_the_full_field():
+    from paper_1611_04214_gb300.inputs import gaussian_noise, gaussian_noise_block
+    full = gaussian_noise((64, 48), 0.05, seed=0, mean=0.1)
+    for rows, cols in ((32, 48), (10, 7), (1, 1)):
+        assert np.array_equal(gaussian_noise_block((64, 48), rows, cols, 0.05, seed=0, mean=0.1), full[:rows, :cols])

@@ -26,7 +26,8 @@ def _library():
 @pytest.mark.parametrize("shape", [(300, 96), (1000, 100)])   # pipelined and general column kernels
 def test_noalloc_columns_match_solver_sweep(bc, shape):
     from paper_1611_04214_gb300.inputs import spacing, uniform_noise
-    from paper_1611_04214_gb300.molt import Solver, molt_helmholtz_columns_noalloc
+    from paper_1611_04214_gb300.molt import (Solver, molt_helmholtz_columns_noalloc,
+                                             molt_helmholtz_columns_noalloc_status)
     ny, nx = shape
     L = 2 * np.pi
     h = spacing(ny, L, bc == "periodic")
@@ -38,6 +39,7 @@ def test_noalloc_columns_match_solver_sweep(bc, shape):
             got = torch.full_like(f, float("nan"))
             s.helmholtz_apply(1, c, f, ref)
             molt_helmholtz_columns_noalloc(nx, ny, L, bc, 4, c, f, got)
+            assert molt_helmholtz_columns_noalloc_status() == 0, call   # every tile copy arrived
             torch.cuda.synchronize()
             r, g = ref.double().cpu().numpy(), got.double().cpu().numpy()
             assert np.all(np.isfinite(g)), call
