@@ -132,40 +132,92 @@ def _initial_state(n):
     return gaussian_noise((n, n), WORKLOAD["amp"], seed=WORKLOAD["seed"], mean=WORKLOAD["mean"])
 
 
-def oracle_sample(iters: int, crop: int = 512):
-    """The FP64 oracle as it stands on a bounded sample of the workload: one SDIRK3 step of a
-    crop x crop periodic patch with the workload's h, eps, dt and initial-state statistics, the
-    same fixed-point iteration cap.  Returns (equivalent line-sweep points, seconds)."""
+# ---- the FP64 oracle on the host cores (the cpu_baseline leg and the reference arm) ----
+CROP_TILES = [(r, c) for r in range(0, 4096, 1024) for c in range(0, 8192, 1024)]   # 32 disjoint 1024^2 blocks
+
+
+def _crop_state(n, row0, col0):
+    from paper_1611_04214_gb300.inputs import gaussian_noise_block
+    return gaussian_noise_block((WORKLOAD["n"], WORKLOAD["n"]), n, n, WORKLOAD["amp"], seed=WORKLOAD["seed"],
+                                mean=WORKLOAD["mean"], row0=row0, col0=col0)
+
+
+def oracle_crop_task(task):
+    """One SDIRK3 step of the FP64 oracle, as it stands, on an n x n periodic block of the 8192^2
+    initial state (its h, eps, dt; the bench's fixed iteration count per stage), from the
+    FP32-rounded start.  Returns (line-sweep points, seconds, start and end wall clock, field or None)."""
+    n, row0, col0, iters, keep = task
+    import numpy as np
+
     from oracle.solver import OracleSolver, Problem
-    from paper_1611_04214_gb300.inputs import gaussian_noise
     h = WORKLOAD["L"] / WORKLOAD["n"]
-    prob = Problem(nx=crop, ny=crop, Lx=crop * h, Ly=crop * h, bc="periodic", eps=WORKLOAD["eps"],
-                   M=WORKLOAD["M"], tol=1e-30, max_iter=iters)
-    u = gaussian_noise((crop, crop), WORKLOAD["amp"], seed=WORKLOAD["seed"], mean=WORKLOAD["mean"])
-    t0 = time.perf_counter()
-    _, info = OracleSolver(prob).step(u, WORKLOAD["dt"], WORKLOAD["scheme"])
+    prob = Problem(nx=n, ny=n, Lx=n * h, Ly=n * h, bc="periodic", eps=WORKLOAD["eps"], M=WORKLOAD["M"], tol=1e-30,
+                   max_iter=iters)
+    u = _crop_state(n, row0, col0).astype(np.float32).astype(np.float64)
+    w0, t0 = time.time(), time.perf_counter()
+    out, info = OracleSolver(prob).step(u, WORKLOAD["dt"], WORKLOAD["scheme"])
     el = time.perf_counter() - t0
     sweeps = sum(SWEEPS_RHS + SWEEPS_ITER * k for k in info.iters)
-    return sweeps * crop * crop, el
+    return sweeps * n * n, el, w0, time.time(), (out if keep else None)
+
+
+CONFIG1 = dict(n=256, eps=0.1, dt=1e-3, steps=1000, tol=1e-10, max_iter=500, M=4, bc="neumann", amp=0.05, seed=0)
+
+
+def oracle_config1_task(_=None):
+    """The 1D Neumann BE workload in full on the oracle: N = 256, eps = 0.1, dt = 1e-3, 1000 steps,
+    tolerance 1e-10.  Returns (seconds, field, total iterations)."""
+    import numpy as np
+
+    from oracle.solver import OracleSolver, Problem
+    from paper_1611_04214_gb300.inputs import uniform_noise
+    c = CONFIG1
+    prob = Problem(nx=c["n"], ny=1, bc=c["bc"], eps=c["eps"], M=c["M"], tol=c["tol"], max_iter=c["max_iter"])
+    o = OracleSolver(prob)
+    u = uniform_noise((1, c["n"]), c["amp"], seed=c["seed"]).astype(np.float32).astype(np.float64)
+    t0, its = time.perf_counter(), 0
+    for _ in range(c["steps"]):
+        u, info = o.step(u, c["dt"], "be")
+        its += info.iters[0]
+    return time.perf_counter() - t0, u, its
+
+
+def oracle_pool(procs):
+    """A process pool for the oracle, started with spawn (no CUDA state is inherited)."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(processes=procs)
+
+
+def _pool_throughput(results):
+    """Whole-pool oracle throughput: every task's line-sweep points over the wall time from the
+    first task's start to the last task's end."""
+    pts = sum(r[0] for r in results)
+    wall = max(r[3] for r in results) - min(r[2] for r in results)
+    return pts / wall / 1e9, wall
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
-    pts, secs = 0.0, 0.0
-    for i in range(args.warmup + args.steps):
-        p, s = oracle_sample(args.iters)
-        if i >= args.warmup:
-            pts += p
-            secs += s
-    value = pts / secs / 1e9
+    procs = max(1, os.cpu_count() or 1)
+    crop = 256
+    tasks = [(crop, r, c, args.iters, False) for (r, c) in (CROP_TILES * 4)[:procs]]
+    values, walls = [], []
+    with oracle_pool(procs) as pool:
+        for i in range(args.warmup + args.steps):
+            v, wall = _pool_throughput(pool.map(oracle_crop_task, tasks))
+            if i >= args.warmup:
+                values.append(v)
+                walls.append(wall)
+    value = sum(v * w for v, w in zip(values, walls)) / sum(walls)
+    sample = (f"per step, {procs} concurrent processes (one per host core), each one SDIRK3 step of its own "
+              f"{crop}x{crop} periodic block of the 8192^2 initial state (same h, eps, dt, {args.iters} "
+              "fixed-point iterations per stage); numpy/scipy FP64 oracle as it stands")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": _config(args),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one SDIRK3 step of a 512x512 periodic patch of the workload (same h, eps, "
-                                       f"dt, {args.iters} fixed-point iterations per stage) per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -453,6 +505,103 @@ def sweep_microbench(reps: int = 10):
     return out
 
 
+CONFIG2 = dict(name="ch2d_1024_neumann_bdf2_converged", n=1024, eps=0.05, dt=1e-4, steps=200, tol=1e-6,
+               max_iter=20000, M=4, bc="neumann", amp=0.05, seed=0)
+
+
+def converged_leg():
+    """The 1024^2 Neumann BDF2 workload in full (eps = 0.05, dt = 1e-4, 200 steps, u0 = 0.05 U[-1,1]
+    seed 0, BE start), every stage iterated to the tolerance 1e-6 (the tolerance of the paper's 2D
+    runs), FP32 and the plain FP64 path, graph-driven stage loops (the library default).  The
+    fields (4 MiB FP32) are L2-resident.  Steps per second over the device time of the steps,
+    fixed-point iterations per step, the final residual, the mass drift and whether the energy
+    decreased at every step (both queried after every step, outside the step timing), and the
+    largest FP32 - FP64 difference at the end relative to max|u + 1|."""
+    import numpy as np
+    import torch
+
+    from paper_1611_04214_gb300.inputs import uniform_noise
+    from paper_1611_04214_gb300.molt import Solver
+    c = CONFIG2
+    n = c["n"]
+    u0 = uniform_noise((n, n), c["amp"], seed=c["seed"]).astype(np.float32)
+    out = {"workload": c["name"], "grid": [n, n], "eps": c["eps"], "dt": c["dt"], "scheme": "bdf2", "steps": c["steps"],
+           "tol": c["tol"], "max_iter": c["max_iter"], "l2": "L2-resident (4 MiB FP32 fields)"}
+    fields = {}
+    for prec in ("fp32", "fp64"):
+        with Solver(nx=n, ny=n, bc=c["bc"], eps=c["eps"], quad_order=c["M"], precision=prec, tol=c["tol"],
+                    max_iter=c["max_iter"]) as s:
+            u = torch.tensor(u0, device="cuda").to(s.dtype)
+            m0, e_prev = s.mass(u), s.energy(u)
+            iters, ms, monotone, converged, res = [], 0.0, True, 0, 0.0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for _ in range(c["steps"]):
+                e0.record()
+                info = s.step(u, c["dt"], "bdf2", raise_on_nonconvergence=False)
+                e1.record()
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                iters.append(info.iters[0])
+                converged += info.status == 0
+                res = info.residual
+                e = s.energy(u)
+                monotone &= e <= e_prev * (1 + (1e-13 if prec == "fp64" else 1e-6))
+                e_prev = e
+            drift = s.mass(u) - m0
+            it = np.array(iters)
+            out[prec] = {"ms_total": ms, "steps_per_s": c["steps"] / (ms * 1e-3), "steps_converged": int(converged),
+                         "iters_first_step": int(it[0]), "iters_total": int(it.sum()),
+                         "iters_median": float(np.median(it)), "iters_max_after_first": int(it[1:].max()),
+                         "final_residual": res, "mass_drift": drift, "energy_monotone": bool(monotone)}
+            fields[prec] = u.double()
+    diff = (fields["fp32"] - fields["fp64"]).abs().max().item()
+    out["fp32_vs_fp64"] = {"speedup": out["fp64"]["ms_total"] / out["fp32"]["ms_total"], "max_abs_diff": diff,
+                           "max_rel_diff_v": diff / (fields["fp64"] + 1).abs().max().item()}
+    del fields
+    torch.cuda.empty_cache()
+    return out
+
+
+def oracle_parity(args, crop_field, config1):
+    """The FP32 and FP64 GPU paths against the oracle results of the cpu_baseline pool: the top-left
+    1024^2 periodic block of the 8192^2 workload after one SDIRK3 step (the bench's fixed iterations
+    per stage on both sides), and the 1D Neumann BE workload after its 1000 steps."""
+    import numpy as np
+    import torch
+
+    from paper_1611_04214_gb300.inputs import uniform_noise
+    from paper_1611_04214_gb300.molt import Solver
+    out = {}
+    n = 1024
+    h = WORKLOAD["L"] / WORKLOAD["n"]
+    start = _crop_state(n, 0, 0).astype(np.float32)
+    scale = float(np.abs(crop_field + 1).max())
+    for prec in ("fp32", "fp64"):
+        with Solver(nx=n, ny=n, Lx=n * h, Ly=n * h, bc="periodic", eps=WORKLOAD["eps"], quad_order=WORKLOAD["M"],
+                    precision=prec, tol=1e-30, max_iter=args.iters) as s:
+            u = torch.tensor(start, device="cuda").to(s.dtype)
+            s.step(u, WORKLOAD["dt"], WORKLOAD["scheme"], raise_on_nonconvergence=False)
+            err = float(np.abs(u.double().cpu().numpy() - crop_field).max())
+        out[f"config3_crop1024_{prec}"] = {"max_abs_err": err, "max_rel_err_v": err / scale}
+    secs, ref1, its1 = config1
+    c = CONFIG1
+    u1 = uniform_noise((1, c["n"]), c["amp"], seed=c["seed"]).astype(np.float32)
+    for prec in ("fp32", "fp64"):
+        with Solver(nx=c["n"], ny=1, bc=c["bc"], eps=c["eps"], quad_order=c["M"], precision=prec, tol=c["tol"],
+                    max_iter=c["max_iter"]) as s:
+            u = torch.tensor(u1, device="cuda").to(s.dtype)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its = sum(s.step(u, c["dt"], "be", raise_on_nonconvergence=False).iters[0] for _ in range(c["steps"]))
+            el = time.perf_counter() - t0
+            err = float(np.abs(u.double().cpu().numpy() - ref1).max())
+        out[f"config1_1d256_be_1000steps_{prec}"] = {"max_abs_err": err,
+                                                     "max_rel_err_v": err / float(np.abs(ref1 + 1).max()),
+                                                     "iters_total": int(its), "seconds": el}
+    out["config1_oracle"] = {"seconds": secs, "iters_total": int(its1), "cores": 1}
+    return out
+
+
 def combine_ranks(ms: float, points: float, dist):
     """Whole-job timing over independent replicas (one per rank): the slowest rank's time and the
     sum of the points all ranks swept.  The reduction tensor lives where the process group's
@@ -472,7 +621,16 @@ def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
 
-    from paper_1611_04214_gb300.molt import Solver
+    from paper_1611_04214_gb300.molt import Solver, molt_fma_throughput_probe
+    # the oracle's share of the work (cpu_baseline, parity of the crop and of the 1D workload) runs
+    # on the host cores in spawned processes while the GPU legs run
+    pool, crop_jobs, c1_job, procs = None, None, None, 0
+    if rank == 0 and world == 1 and not args.skip_oracle:
+        procs = max(1, (os.cpu_count() or 1) - 2)
+        pool = oracle_pool(procs)
+        tasks = [(1024, r, c, args.iters, i == 0) for i, (r, c) in enumerate((CROP_TILES * 4)[:procs])]
+        crop_jobs = pool.map_async(oracle_crop_task, tasks)
+        c1_job = pool.apply_async(oracle_config1_task)
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     n = WORKLOAD["n"]
@@ -550,12 +708,6 @@ def run_ours(args, rank, world, dist):
         e2e_secs = time.perf_counter() - t0
         e2e = {"value": e2e_pts / e2e_secs / 1e9, "unit": UNIT, "h2d_bytes_per_step": n * n * elem,
                "d2h_bytes_per_step": n * n * elem, "steps": e2e_steps}
-        cpu = None
-        if world == 1:
-            p, s = oracle_sample(args.iters)
-            cpu = {"value": p / s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": "one SDIRK3 step of a 512x512 periodic patch of the workload (same h, eps, dt, "
-                             f"{args.iters} fixed-point iterations per stage), numpy/scipy FP64, one thread"}
         # the product default: stage loops as device-driven graphs (no profiling events)
         solver.set_execution("graph")
         ug = torch.tensor(u0, dtype=dtype, device="cuda")
@@ -573,6 +725,32 @@ def run_ours(args, rank, world, dist):
         fp64 = fp64_comparison(args, u0) if (args.precision == "fp32" and not args.skip_fp64) else None
         batched = None if args.skip_batch else batched_leg(args)
         sweeps_mb = None if args.skip_sweeps else sweep_microbench()
+        converged = None if args.skip_converged else converged_leg()
+        try:
+            fp64_probe = {"fp64_fma_tflops": molt_fma_throughput_probe("fp64"),
+                          "fp32_fma_tflops": molt_fma_throughput_probe("fp32")}
+        except Exception as exc:
+            fp64_probe = {"error": f"{type(exc).__name__}: {exc}"}
+        if sweeps_mb and "fp64_fma_tflops" in fp64_probe:
+            for r in sweeps_mb:     # FP64 sweeps against the FP64 FMA ceiling (about 30 flops per point)
+                if r["precision"] == "fp64":
+                    r["tflops_at_30_flop_per_pt"] = 30 * r["gpts_per_s"] / 1e3
+                    r["frac_of_fp64_fma_peak"] = r["tflops_at_30_flop_per_pt"] / fp64_probe["fp64_fma_tflops"]
+        cpu, parity = None, None
+        if pool is not None:
+            crops = crop_jobs.get()
+            v, wall = _pool_throughput(crops)
+            cpu = {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
+                   "sample": f"{procs} concurrent processes (host cores minus two), each one SDIRK3 step of its own "
+                             "1024x1024 periodic block of the 8192^2 initial state (same h, eps, dt, "
+                             f"{args.iters} fixed-point iterations per stage), numpy/scipy FP64 oracle as it "
+                             f"stands; run while the GPU legs ran; wall {wall:.1f} s"}
+            try:
+                parity = oracle_parity(args, crops[0][4], c1_job.get())
+            except Exception as exc:
+                parity = {"error": f"{type(exc).__name__}: {exc}"}
+            pool.close()
+            pool.join()
         vch = None
         if not args.skip_vch:
             try:
@@ -585,10 +763,18 @@ def run_ours(args, rank, world, dist):
                   "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
                   "data": "synthetic", "config": _config(args), "roofline": roofline, "cpu_baseline": cpu,
                   "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(),
-                  "ch_steps_per_s": args.steps / (ms * 1e-3), "iters_per_stage": last.iters,
+                  "fixed_iteration_steps_per_s": args.steps / (ms * 1e-3),
+                  "fixed_iteration_note": (f"each stage runs {args.iters} fixed-point iterations and stops at the "
+                                           "final_residual, not at 1e-6; see converged_l2_resident for steps "
+                                           "iterated to their tolerance"),
+                  "iters_per_stage": last.iters,
                   "final_residual": last.residual, "hbm_frac_step_algorithmic": hbm_frac_step,
                   "ms_per_step_graph_mode": graph_ms, "fp32_vs_fp64": fp64, "batched": batched,
-                  "sweep_microbench": sweeps_mb, "vector_ch": vch, "kernels": kernels}
+                  "sweep_microbench": sweeps_mb, "vector_ch": vch, "kernels": kernels,
+                  "converged_l2_resident": converged, "oracle_parity": parity, "fma_probe": fp64_probe}
+        if parity and "config3_crop1024_fp32" in parity:
+            result["config3_crop_err_vs_oracle"] = {p_: parity[f"config3_crop1024_{p_}"]["max_rel_err_v"]
+                                                    for p_ in ("fp32", "fp64")}
     solver.close()
     return result
 
@@ -605,6 +791,8 @@ def main():
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched-instances leg")
     ap.add_argument("--skip-sweeps", action="store_true", help="skip the single-sweep microbenchmark")
     ap.add_argument("--skip-vch", action="store_true", help="skip the vector Cahn-Hilliard leg")
+    ap.add_argument("--skip-converged", action="store_true", help="skip the converged 1024^2 Neumann BDF2 leg")
+    ap.add_argument("--skip-oracle", action="store_true", help="skip the host-core oracle (cpu_baseline, parity)")
     ap.add_argument("--vch-workload", default="mixture", choices=sorted(VCH_WORKLOADS),
                     help="vector-model workload of the vector_ch leg")
     ap.add_argument("--vch-only", action="store_true",

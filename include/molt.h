@@ -326,6 +326,13 @@ long long molt_column_tma_launches(void);
  * MOLT_ERR_ARG (null output), MOLT_ERR_CUDA. */
 molt_status molt_selftest_bounded_wait(int* timed_out, double* waited_seconds);
 
+/* Diagnostics (no counterpart in the paper): the fused multiply-add throughput the current GPU
+ * sustains in `precision` (MOLT_FP32 or MOLT_FP64), in TFLOP/s (one FMA = 2 flops): independent
+ * FMA chains in registers, 8 blocks of 256 threads per SM, timed with CUDA events after one
+ * warm-up launch.  The ceiling of the FP64 line sweeps, which are arithmetic-bound on this part.
+ * Synchronizes the device; allocates a small result buffer.  Errors: MOLT_ERR_ARG, MOLT_ERR_CUDA. */
+molt_status molt_fma_throughput_probe(int precision, double* tflops);
+
 /* Diagnostic timing (not part of the method; off by default).  While enabled, every sweep
  * kernel launch is bracketed by two CUDA events on its stream. */
 molt_status molt_profile_enable(molt_solver* solver, int enable);

@@ -54,19 +54,20 @@ def gaussian_noise(shape, amp: float, seed: int, mean: float = 0.0) -> np.ndarra
     return (mean + amp * z).reshape(shape)
 
 
-def gaussian_noise_block(shape, rows: int, cols: int, amp: float, seed: int, mean: float = 0.0) -> np.ndarray:
-    """The top-left ``rows`` x ``cols`` block of ``gaussian_noise(shape, ...)`` without drawing the
-    rest of the field (a crop of a large initial state).  Needs rows * shape[1] <= half the field,
-    where every value of the block is the cosine half of its Box-Muller pair."""
+def gaussian_noise_block(shape, rows: int, cols: int, amp: float, seed: int, mean: float = 0.0, row0: int = 0,
+                         col0: int = 0) -> np.ndarray:
+    """The block of rows row0 .. row0+rows-1 and columns col0 .. col0+cols-1 of
+    ``gaussian_noise(shape, ...)`` without drawing the rest of the field (a crop of a large
+    initial state).  Needs (row0 + rows) * shape[1] <= half the field, where every value of the
+    block is the cosine half of its Box-Muller pair."""
     ny, nx = shape
-    count = ny * nx
-    m = (count + 1) // 2
-    k = rows * nx
-    if rows > ny or cols > nx or k > m:
+    m = (ny * nx + 1) // 2
+    k0, k1 = row0 * nx, (row0 + rows) * nx
+    if row0 + rows > ny or col0 + cols > nx or k1 > m:
         raise ValueError("the block must lie within the first half of the field")
-    u = uniform01(seed, 2 * k)
+    u = uniform01(seed, 2 * (k1 - k0), offset=2 * k0)
     z = np.sqrt(-2.0 * np.log(1.0 - u[0::2])) * np.cos(2 * np.pi * u[1::2])
-    return (mean + amp * z).reshape(rows, nx)[:, :cols].copy()
+    return (mean + amp * z).reshape(rows, nx)[:, col0:col0 + cols].copy()
 
 
 def three_phase_mixture(shape, seed: int):

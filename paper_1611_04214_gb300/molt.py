@@ -29,7 +29,7 @@ EXPORTS = [
     "molt_column_tma_launches", "molt_batch_create", "molt_batch_destroy", "molt_batch_points",
     "molt_batch_offsets", "molt_batch_set_execution", "molt_batch_step", "molt_selftest_bounded_wait",
     "molt_step_adaptive",
-    "molt_vch_step",
+    "molt_vch_step", "molt_fma_throughput_probe",
 ]
 EXECUTION = {"host_loop": 0, "graph": 1}
 PROFILE_SLOTS = 32
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_graph_fallbacks": ([P], ctypes.c_longlong),
         "molt_column_tma_launches": ([], ctypes.c_longlong),
         "molt_selftest_bounded_wait": ([ctypes.POINTER(I), ctypes.POINTER(D)], I),
+        "molt_fma_throughput_probe": ([I, ctypes.POINTER(D)], I),
         "molt_step_adaptive": ([P, VP, D, ctypes.POINTER(_Adaptive), VP, ctypes.POINTER(_AdaptiveInfo)], I),
         "molt_vch_step": ([P, VP, VP, D, I, VP, ctypes.POINTER(_StepInfo)], I),
         "molt_batch_create": ([ctypes.POINTER(VP), I, VP, I, I, D, I], I),
@@ -161,6 +162,13 @@ def molt_helmholtz_columns_noalloc_status(stream=None) -> int:
 def molt_column_tma_launches() -> int:
     """Column-sweep kernels launched with TMA tile loads since the library was loaded (diagnostics)."""
     return int(load_library().molt_column_tma_launches())
+
+
+def molt_fma_throughput_probe(precision: str) -> float:
+    """Sustained FMA throughput of the current GPU in TFLOP/s ("fp32" or "fp64"; diagnostics)."""
+    out = ctypes.c_double(0.0)
+    _check(load_library().molt_fma_throughput_probe(PRECISION[precision], ctypes.byref(out)))
+    return float(out.value)
 
 
 def molt_selftest_bounded_wait():

@@ -30,3 +30,5 @@ def test_gaussian_noise_block_is_the_crop_of_the_full_field():
     full = gaussian_noise((64, 48), 0.05, seed=0, mean=0.1)
     for rows, cols in ((32, 48), (10, 7), (1, 1)):
         assert np.array_equal(gaussian_noise_block((64, 48), rows, cols, 0.05, seed=0, mean=0.1), full[:rows, :cols])
+    assert np.array_equal(gaussian_noise_block((64, 48), 9, 11, 0.05, seed=0, mean=0.1, row0=20, col0=30),
+                          full[20:29, 30:41])
