@@ -220,7 +220,9 @@ cols_tma_kernel(const __grid_constant__ LineParams<float> lp, const __grid_const
                 if (tile == tiles - 1) injR[q] = carR[o];
             }
         }
-        auto at = [&](int p, int q) {
+        // all NF swept values at line position p (prologue applied), from the stage or from global
+        // memory when p lies outside it
+        auto at_v = [&](int p) -> V {
             const int rr = p - r0;
             T sv[NS], fv[NF];
             if (rr >= 0 && rr < ROWS) {
@@ -231,35 +233,58 @@ cols_tma_kernel(const __grid_constant__ LineParams<float> lp, const __grid_const
                 for (int f = 0; f < NS; ++f) sv[f] = op.s[f][static_cast<long long>(p) * ld + line];
             }
             op.prologue(sv, fv);
-            return fv[q];
+            return Ln::make(fv);
         };
-        auto wq = [&](int i, int q) { return Ln::get(win[i], q); };
-        // J^L / J^R of field q at chunk position k (j = start + k), wall stencils and injections
-        auto jl = [&](int q, int k) {
-            const int j = start + k;
-            T a = T(0);
-            if (!periodic && j < H) {
-                if (j == 0) return injL[q];
-                for (int o = 0; o <= M; ++o) a = fmaf(lp.wlA[j - 1][o], at(o, q), a);
-            } else if (!periodic && j >= jb) {
-                for (int o = 0; o <= M; ++o) a = fmaf(lp.wlB[j - jb][o], at(N - M + o, q), a);
-            } else {
+        // J^L, J^R at chunk position k of a chunk that is not interior (it touches a wall of a
+        // non-periodic line, or it is the ragged end of the line): interior positions from the
+        // window; the first and last H positions of a non-periodic line from the shifted wall
+        // stencils (Sec. 3.2 reading) on wall nodes 0..M or N-M..N, whose prologue is evaluated
+        // once per node into wv; zero past the end of the line.  In the final phase J^L_0 = B_a and
+        // J^R_N = B_b (injected, from the scan).  Same operations in the same order as
+        // local_integrals.  (A chunk of 16 rows touches at most one wall: lines have n >= 256.)
+        const bool nearA = !periodic && start < H;
+        const bool nearB = !periodic && start + cnt - 1 >= jb;
+        V wv[M + 1];
+        if (!interior) {
+            const int base = nearA ? 0 : N - M;
 #pragma unroll
-                for (int o = 0; o <= M; ++o) a = fmaf(lp.wl[o], wq(k + o, q), a);
+            for (int o = 0; o <= M; ++o) wv[o] = (nearA || nearB) ? at_v(base + o) : Ln::zero();
+        }
+        auto jl_e = [&](int k) -> V {
+            const int j = start + k;
+            V a = Ln::zero();
+            if (nearA && j < H) {
+                if (j == 0) return Ln::make(injL);
+                a = Ln::fma(Ln::splat(lp.wlA[j - 1][0]), wv[0], a);
+#pragma unroll
+                for (int o = 1; o <= M; ++o) a = Ln::fma(Ln::splat(lp.wlA[j - 1][o]), wv[o], a);
+            } else if (nearB && j >= jb) {
+                a = Ln::fma(Ln::splat(lp.wlB[j - jb][0]), wv[0], a);
+#pragma unroll
+                for (int o = 1; o <= M; ++o) a = Ln::fma(Ln::splat(lp.wlB[j - jb][o]), wv[o], a);
+            } else {
+                a = Ln::fma(WL(0), win[k], a);
+#pragma unroll
+                for (int o = 1; o <= M; ++o) a = Ln::fma(WL(o), win[k + o], a);
             }
             return a;
         };
-        auto jr = [&](int q, int k) {
+        auto jr_e = [&](int k) -> V {
             const int j = start + k;
-            T a = T(0);
-            if (!periodic && j < H) {
-                for (int o = 0; o <= M; ++o) a = fmaf(lp.wrA[j][o], at(o, q), a);
-            } else if (!periodic && j >= jb) {
-                if (j == N) return injR[q];
-                for (int o = 0; o <= M; ++o) a = fmaf(lp.wrB[j - jb][o], at(N - M + o, q), a);
-            } else {
+            V a = Ln::zero();
+            if (nearA && j < H) {
+                a = Ln::fma(Ln::splat(lp.wrA[j][0]), wv[0], a);
 #pragma unroll
-                for (int o = 0; o <= M; ++o) a = fmaf(lp.wr[o], wq(k + o, q), a);
+                for (int o = 1; o <= M; ++o) a = Ln::fma(Ln::splat(lp.wrA[j][o]), wv[o], a);
+            } else if (nearB && j >= jb) {
+                if (j == N) return Ln::make(injR);
+                a = Ln::fma(Ln::splat(lp.wrB[j - jb][0]), wv[0], a);
+#pragma unroll
+                for (int o = 1; o <= M; ++o) a = Ln::fma(Ln::splat(lp.wrB[j - jb][o]), wv[o], a);
+            } else {
+                a = Ln::fma(WR(0), win[k], a);
+#pragma unroll
+                for (int o = 1; o <= M; ++o) a = Ln::fma(WR(o), win[k + o], a);
             }
             return a;
         };
@@ -288,19 +313,15 @@ cols_tma_kernel(const __grid_constant__ LineParams<float> lp, const __grid_const
             aL = a;
             aR = b;
         } else {
-            T a[NF], b[NF];
+            V a = Ln::zero(), b = Ln::zero();
 #pragma unroll
-            for (int q = 0; q < NF; ++q) {
-                a[q] = b[q] = T(0);
+            for (int k = 0; k < KY; ++k)
+                if (k < cnt) a = Ln::fma(dv, a, jl_e(k));
 #pragma unroll
-                for (int k = 0; k < KY; ++k)
-                    if (k < cnt) a[q] = fmaf(d, a[q], jl(q, k));
-#pragma unroll
-                for (int k = KY - 1; k >= 0; --k)
-                    if (k < cnt) b[q] = fmaf(d, b[q], jr(q, k));
-            }
-            aL = Ln::make(a);
-            aR = Ln::make(b);
+            for (int k = KY - 1; k >= 0; --k)
+                if (k < cnt) b = Ln::fma(dv, b, jr_e(k));
+            aL = a;
+            aR = b;
         }
         sL[pb][wy][lane] = aL;
         sR[pb][wy][lane] = aR;
@@ -360,33 +381,22 @@ cols_tma_kernel(const __grid_constant__ LineParams<float> lp, const __grid_const
                     out[k] = Ln::add(out[k], s2);
                 }
             } else {
-                T o2[NF][KY];
+                V p = cr;
 #pragma unroll
-                for (int q = 0; q < NF; ++q) {
-                    T p = Ln::get(cr, q);
-#pragma unroll
-                    for (int k = KY - 1; k >= 0; --k) {
-                        o2[q][k] = T(0);
-                        if (k < cnt) {
-                            p = fmaf(d, p, jr(q, k));
-                            o2[q][k] = p;
-                        }
+                for (int k = KY - 1; k >= 0; --k) {
+                    out[k] = Ln::zero();
+                    if (k < cnt) {
+                        p = Ln::fma(dv, p, jr_e(k));
+                        out[k] = p;
                     }
-                    T s2 = Ln::get(cl, q);
-#pragma unroll
-                    for (int k = 0; k < KY; ++k)
-                        if (k < cnt) {
-                            s2 = fmaf(d, s2, jl(q, k));
-                            o2[q][k] += s2;
-                        }
                 }
+                V s2 = cl;
 #pragma unroll
-                for (int k = 0; k < KY; ++k) {
-                    T v[NF];
-#pragma unroll
-                    for (int q = 0; q < NF; ++q) v[q] = o2[q][k];
-                    out[k] = Ln::make(v);
-                }
+                for (int k = 0; k < KY; ++k)
+                    if (k < cnt) {
+                        s2 = Ln::fma(dv, s2, jl_e(k));
+                        out[k] = Ln::add(out[k], s2);
+                    }
             }
             T* ob[NO];
 #pragma unroll

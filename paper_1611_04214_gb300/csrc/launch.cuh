@@ -215,38 +215,85 @@ P pipe_build(int kind, const OpArgs<float>& a) {
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// Shared memory of one block of the pipelined row kernel: the double-buffered staged fields of
+// its slice with a halo chunk on each side (padded to 8 chunks), and the auxiliary fields.
 template <class P>
-bool pipe_eligible(const P& p, int n) {
-    if (n % 512 != 0 || n < 1024 || n > 8192) return false;
-    if (static_cast<long long>(2 * P::NS + P::NA) * n * static_cast<long long>(sizeof(float)) > kRowMaxSmem)
-        return false;   // staged lines do not fit (four staged fields at n = 8192)
-    for (int f = 0; f < P::NS; ++f) if (!aligned16(p.s[f])) return false;
-    for (int f = 0; f < P::NA; ++f) if (!aligned16(p.a[f])) return false;
-    for (int f = 0; f < P::NO; ++f) if (!aligned16(p.o[f])) return false;
-    return true;
+long long pipe_smem(int n, int C) {
+    const long long nchl = n / 4 / C;
+    return (2LL * P::NS * (nchl + 8) + static_cast<long long>(P::NA) * nchl) * 16;
 }
 
-template <int M, class P>
+// Cluster sizes the pipelined row kernel can run a line of n nodes with: slices of whole warps of
+// 16-position threads (n % (512 C) == 0), at most 512 threads per block, and shared memory that fits.
+template <class P>
+bool pipe_fits(int n, int C) {
+    if (n < 1024 || n % (512 * C) != 0 || n / (16 * C) > 512) return false;
+    return pipe_smem<P>(n, C) <= kRowMaxSmem;
+}
+
+// The cluster size of a line length: MOLT_ROWS_CLUSTER (1 or 2) in the environment when it
+// fits, else the smallest that fits; 0 when none does (or a field is not 16-byte aligned).
+template <class P>
+int pipe_cluster(const P& p, int n) {
+    for (int f = 0; f < P::NS; ++f) if (!aligned16(p.s[f])) return 0;
+    for (int f = 0; f < P::NA; ++f) if (!aligned16(p.a[f])) return 0;
+    for (int f = 0; f < P::NO; ++f) if (!aligned16(p.o[f])) return 0;
+    if (const char* v = std::getenv("MOLT_ROWS_CLUSTER")) {
+        const int c = std::atoi(v);
+        if ((c == 1 || c == 2) && pipe_fits<P>(n, c)) return c;
+    }
+    for (int c : {1, 2})
+        if (pipe_fits<P>(n, c)) return c;
+    return 0;
+}
+
+template <int M, class P, int C>
 cudaError_t rows_pipe(const LineParams<float>& lp, const P& op, int nlines, unsigned long long* red, cudaStream_t st,
                       Prof* prof, int kind) {
     const int n = lp.n;
-    const int TL = n / 16;
-    const size_t smem = static_cast<size_t>(2 * P::NS + P::NA) * n * sizeof(float);
-    auto kern = rows_pipe_kernel<M, P>;
+    const int TL = n / (16 * C);
+    const size_t smem = static_cast<size_t>(pipe_smem<P>(n, C));
+    auto kern = rows_pipe_kernel<M, P, C>;
     static int limit = smem_optin(kern);
     if (limit < 0 || smem > static_cast<size_t>(limit)) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TL, smem);
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    int grid = sms * per_sm;
-    if (grid > nlines) grid = nlines;
-    prof_begin(prof, kind, st);
     const PackedStencil pw = packed_stencil(lp);
-    kern<<<grid, TL, smem, st>>>(lp, pw, op, nlines, static_cast<long long>(n), red);
-    prof_end(prof, st);
-    return cudaGetLastError();
+    const long long ld = n;
+    if constexpr (C == 1) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TL, smem);
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        int grid = sms * per_sm;
+        if (grid > nlines) grid = nlines;
+        prof_begin(prof, kind, st);
+        kern<<<grid, TL, smem, st>>>(lp, pw, op, nlines, ld, red);
+        prof_end(prof, st);
+        return cudaGetLastError();
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(TL);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(C * 1024);
+        int clusters = 0;
+        cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+        if (e != cudaSuccess) return e;
+        if (clusters < 1) return cudaErrorInvalidConfiguration;
+        if (clusters > nlines) clusters = nlines;
+        cfg.gridDim = dim3(C * clusters);
+        prof_begin(prof, kind, st);
+        e = cudaLaunchKernelEx(&cfg, kern, lp, pw, op, nlines, ld, red);
+        prof_end(prof, st);
+        return e;
+    }
 }
 
 // ---- pipelined FP32 columns ----
@@ -429,11 +476,15 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
         if constexpr (std::is_same<T, float>::value && !std::is_same<typename PipeOf<Op>::type, void>::value) {
             using P = typename PipeOf<Op>::type;
             const P pop = pipe_build<P>(kind, a);
-            if (pipe_eligible(pop, lp.n)) {
-                switch (lp.M) {
-                    case 2: return rows_pipe<2>(lp, pop, nlines, red, st, prof, pk);
-                    case 4: return rows_pipe<4>(lp, pop, nlines, red, st, prof, pk);
-                    case 6: return rows_pipe<6>(lp, pop, nlines, red, st, prof, pk);
+            const int C = pipe_cluster(pop, lp.n);
+            if (C > 0) {
+                switch (lp.M * 8 + C) {
+                    case 2 * 8 + 1: return rows_pipe<2, P, 1>(lp, pop, nlines, red, st, prof, pk);
+                    case 2 * 8 + 2: return rows_pipe<2, P, 2>(lp, pop, nlines, red, st, prof, pk);
+                    case 4 * 8 + 1: return rows_pipe<4, P, 1>(lp, pop, nlines, red, st, prof, pk);
+                    case 4 * 8 + 2: return rows_pipe<4, P, 2>(lp, pop, nlines, red, st, prof, pk);
+                    case 6 * 8 + 1: return rows_pipe<6, P, 1>(lp, pop, nlines, red, st, prof, pk);
+                    case 6 * 8 + 2: return rows_pipe<6, P, 2>(lp, pop, nlines, red, st, prof, pk);
                 }
             }
         }
@@ -593,16 +644,30 @@ template <typename T>
 cudaError_t sweep_vch(int axis, const LineParams<T>& lp, int kind, const OpArgs<T>& a, int nx, int ny,
                       ColScratch<T>* cs, unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof);
 
+// The 2D iteration passes 1-4, each instantiated in a translation unit of its own
+// (kernels_p1.cu .. kernels_p4.cu) so that they compile in parallel with the rest.
+#define MOLT_DECLARE_PASS(fn)                                                                                   \
+    template <typename T>                                                                                     \
+    cudaError_t fn(int axis, const LineParams<T>& lp, int kind, const OpArgs<T>& a, int nx, int ny,            \
+                   ColScratch<T>* cs, unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof);
+MOLT_DECLARE_PASS(sweep_p1)
+MOLT_DECLARE_PASS(sweep_p2)
+MOLT_DECLARE_PASS(sweep_p3)
+MOLT_DECLARE_PASS(sweep_p4)
+MOLT_DECLARE_PASS(sweep_v1)
+MOLT_DECLARE_PASS(sweep_v2)
+#undef MOLT_DECLARE_PASS
+
 template <typename T>
 cudaError_t sweep(int axis, const LineParams<T>& lp, int kind, const OpArgs<T>& a, int nx, int ny, ColScratch<T>* cs,
                   unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof) {
     using namespace detail;
     switch (kind) {
         case OP_COPY: return dispatch<T, OpCopy<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
-        case OP_P1: return dispatch<T, OpP1<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
-        case OP_P2: return dispatch<T, OpP2<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
-        case OP_P3: return dispatch<T, OpP3<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
-        case OP_P4: return dispatch<T, OpP4<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
+        case OP_P1: return sweep_p1<T>(axis, lp, kind, a, nx, ny, cs, red, st, launches, prof);
+        case OP_P2: return sweep_p2<T>(axis, lp, kind, a, nx, ny, cs, red, st, launches, prof);
+        case OP_P3: return sweep_p3<T>(axis, lp, kind, a, nx, ny, cs, red, st, launches, prof);
+        case OP_P4: return sweep_p4<T>(axis, lp, kind, a, nx, ny, cs, red, st, launches, prof);
         case OP_1A: return dispatch<T, Op1a<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
         case OP_1B: return dispatch<T, Op1b<T>>(axis, lp, a, nx, ny, cs, red, st, launches, prof, kind);
         case OP_V1:
@@ -649,6 +714,23 @@ cudaError_t lincomb(T* out, long long n, const T* x0, double c0, const T* x1, do
 }
 
 namespace detail {
+// One row j per blockIdx.y; the row weights a[k][j] are loaded once per thread.
+template <typename T>
+__global__ void add_separable_kernel(T* y, int nx, const Separable s) {
+    const int j = blockIdx.y;
+    double aj[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) aj[k] = k < s.terms ? s.a[k][j] : 0.0;
+    T* row = y + static_cast<size_t>(j) * nx;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x) {
+        double acc = static_cast<double>(row[i]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < s.terms) acc = fma(aj[k], s.b[k][i], acc);
+        row[i] = static_cast<T>(acc);
+    }
+}
+
 template <typename T>
 __global__ void cubic_kernel(T* out, long long n, const T* x, T a2, T a1) {
     const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
@@ -658,6 +740,15 @@ __global__ void cubic_kernel(T* out, long long n, const T* x, T a2, T a1) {
     }
 }
 }  // namespace detail
+
+template <typename T>
+cudaError_t add_separable(T* y, int nx, int ny, const Separable& s, cudaStream_t st, long long* launches) {
+    if (s.terms < 1 || s.terms > 4 || ny > 65535) return cudaErrorInvalidValue;
+    const int bx = nx >= 2048 ? 8 : (nx + 255) / 256;
+    detail::add_separable_kernel<T><<<dim3(bx, ny), 256, 0, st>>>(y, nx, s);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t cubic(T* out, long long n, const T* x, double a2, double a1, cudaStream_t st, long long* launches) {
@@ -732,4 +823,5 @@ cudaError_t max_abs_diff(const T* a, const T* b, long long n, unsigned long long
     template cudaError_t molt::energy_mass<T>(const T*, int, int, int, double, double, double, int, double*,    \
                                               double*, cudaStream_t, long long*);                               \
     template cudaError_t molt::cubic<T>(T*, long long, const T*, double, double, cudaStream_t, long long*);    \
+    template cudaError_t molt::add_separable<T>(T*, int, int, const molt::Separable&, cudaStream_t, long long*); \
     template cudaError_t molt::max_abs_diff<T>(const T*, const T*, long long, unsigned long long*, cudaStream_t);

@@ -164,6 +164,15 @@ cudaError_t loop_init(LoopState* ls, unsigned long long* red, cudaStream_t st);
 cudaError_t loop_check(cudaGraphConditionalHandle h, LoopState* ls, unsigned long long* red, double tol,
                        int max_iter, int fp32, cudaStream_t st);
 
+// y[j][i] += sum_k a[k][j] b[k][i] (k < terms <= 4), the sum in FP64, for a [ny][nx] field.
+struct Separable {
+    const double* a[4];
+    const double* b[4];
+    int terms;
+};
+template <typename T>
+cudaError_t add_separable(T* y, int nx, int ny, const Separable& s, cudaStream_t st, long long* launches);
+
 // out = x (x (x + a2) + a1), n elements (the pointwise cubic f of Eq. CahnHilliard_v).
 template <typename T>
 cudaError_t cubic(T* out, long long n, const T* x, double a2, double a1, cudaStream_t st, long long* launches);

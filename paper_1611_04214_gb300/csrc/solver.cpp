@@ -1,11 +1,12 @@
 // C ABI of the library (include/molt.h): handles, stage solves and time schemes.
 //
-// Stored variable.  The kernels work on w = v - s with v = u + 1 (Sec. 3): s = 1 (w = u) on
-// periodic and Neumann grids, where every line inverse maps constants to themselves so the
-// constant part of v never needs to be carried through FP32 arithmetic; s = 0 (w = v) on
-// Dirichlet grids, whose inverses hold v = 0 on the walls.  The fixed-point map keeps the same
-// form in w because D = I - H annihilates constants and all right-hand-side combinations
-// below have coefficients summing to one.
+// Stored variable.  The kernels work on w = v - 1 = u with v = u + 1 (Sec. 3), so the constant
+// part of v never passes through FP32 arithmetic and every field is rounded relative to |u|, not
+// |v|.  On periodic and Neumann grids every line inverse maps constants to themselves, so the
+// fixed-point map keeps the same form in w: D = I - H annihilates constants and all right-hand-side
+// combinations below have coefficients summing to one.  Dirichlet inverses hold v = 0 on the
+// walls and do not map 1 to itself; there the constant part adds one fixed field per stage
+// coefficient to Y (add_dirichlet_offset), and the iteration is otherwise the same.
 //
 // Stage solve (v - tau F(v) = r):  parameters from the regime switch of Sec. 3.1.2 (with
 // dt -> tau as in Sec. 4.1-4.2), inner factor = larger c.
@@ -196,6 +197,7 @@ struct Solver final : molt_solver {
     unsigned long long* red_host = nullptr;  // pinned [2]
     unsigned* wait_status = nullptr;         // device [1]: set by kernels whose bounded waits ran out
     unsigned* wait_status_host = nullptr;    // pinned [1]
+    double* dprof = nullptr;                 // device [kProfiles][max(nx, ny)]: Dirichlet offset profiles
     double* partials = nullptr;              // device [reduce_blocks]
     double* result = nullptr;                // device [1]
     double* result_host = nullptr;           // pinned [1]
@@ -203,7 +205,7 @@ struct Solver final : molt_solver {
 
     size_t count() const { return static_cast<size_t>(g.nx) * g.ny; }
     bool fp32() const { return sizeof(T) == 4; }
-    T shift() const { return bc == molt::BC_DIRICHLET ? T(0) : T(1); }
+    T shift() const { return T(1); }     // stored w = v - 1 (see the file comment)
 
     ~Solver() override {
         drop_graphs();
@@ -251,7 +253,8 @@ struct Solver final : molt_solver {
         cs.capacity_fields = 2;
         const size_t sc = static_cast<size_t>(2) * tiles * nlines;
         if (!alloc(&cs.aggL, sc) || !alloc(&cs.aggR, sc) || !alloc(&cs.carL, sc) || !alloc(&cs.carR, sc) ||
-            !alloc(&red, 2) || !alloc(&partials, static_cast<size_t>(molt::reduce_blocks())) || !alloc(&result, 1))
+            !alloc(&red, 2) || !alloc(&partials, static_cast<size_t>(molt::reduce_blocks())) || !alloc(&result, 1) ||
+            !alloc(&dprof, static_cast<size_t>(kProfiles) * std::max(g.nx, g.ny)))
             return fail(MOLT_ERR_OOM, "device scratch allocation failed");
         if (!alloc(&ls, 1)) return fail(MOLT_ERR_OOM, "device loop state allocation failed");
         if (!alloc(&wait_status, 1)) return fail(MOLT_ERR_OOM, "device status allocation failed");
@@ -328,11 +331,16 @@ struct Solver final : molt_solver {
 
     // out = M_o^{-1} M_i^{-1} F(v) for v stored in w_in, without derivatives (Remark Laplacian /
     // biLaplacian): -(eps^2/(c_i c_o)) E_o E_i v + (1/c_i) M_o^{-1} E_i f(v-1).  E kills constants
-    // on periodic / Neumann grids, so E_i v = E_i w there; f(v-1) = w^3 - w for w = v - 1 and
-    // v^3 - 3v^2 + 2v for w = v.  Scratch: f1..f6.
+    // on periodic / Neumann grids, so E_i v = E_i w there; on Dirichlet grids v = w + 1 is formed
+    // first.  f(v-1) = w^3 - w for w = v - 1.  Scratch: f1..f6.
     cudaError_t inverse_of_F(const StageParams& sp, const T* w_in, T* out, cudaStream_t st) {
         cudaError_t e;
-        if ((e = e_op(sp.c_in, w_in, f4, st)) != cudaSuccess) return e;        // E_i v
+        const T* v_in = w_in;
+        if (bc == molt::BC_DIRICHLET) {   // Dirichlet E does not kill constants: form v = w + 1
+            if ((e = lin(f5, w_in, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 1.0, st)) != cudaSuccess) return e;
+            v_in = f5;
+        }
+        if ((e = e_op(sp.c_in, v_in, f4, st)) != cudaSuccess) return e;        // E_i v
         if ((e = e_op(sp.c_out, f4, f5, st)) != cudaSuccess) return e;         // E_o E_i v
         const bool shifted = shift() == T(1);
         if ((e = molt::cubic<T>(f6, static_cast<long long>(count()), w_in, shifted ? 0.0 : -3.0,
@@ -342,6 +350,75 @@ struct Solver final : molt_solver {
         if ((e = mm_inv(sp.c_out, f4, f6, st)) != cudaSuccess) return e;      // M_o^{-1} E_i f
         return lin(out, f5, -(p.eps * p.eps) / (sp.c_in * sp.c_out), f6, 1.0 / sp.c_in, nullptr, 0, nullptr, 0, 0,
                    st);
+    }
+
+    // Dirichlet grids: the fixed field the constant part of v adds to a stage (see the file comment).
+    // With K the fused passes in w and K_v the same passes in v (where G(1) = lambda - 2 =: g0),
+    //   w_new = v_new - 1 = [Y_w + M_o^{-1} M_i^{-1} 1 + K_v(1) - 1] + K(w),
+    // and the bracket's fixed part C is a sum of products of line profiles, from the passes applied
+    // to v = 1 (T = g0 phi_iy, S = phi_iy, U, P, Q1, Q2 with phi_a = H_a 1):
+    //   2D: C = psi1 (psi2 + H_oy p1 - a2) - phi_ix H_oy a2 + phi_ox (H_oy p0 - phi_iy) - psi2,
+    //       a2 = 1 - phi_iy, p1 = (2 beta g0 - 1) phi_iy + 1 - beta g0, p0 = (1 - beta g0) phi_iy,
+    //       psi1 = H_ox phi_ix, psi2 = H_oy phi_iy;
+    //   1D: C = (1 + beta g0) psi1 - beta g0 phi_o - 1, psi1 = H_o phi_i.
+    // C vanishes away from the walls (all profiles -> 1).  The profiles are FP64 sweeps of single
+    // lines, and Y += C is formed per point in FP64.
+    static constexpr int kProfiles = 16;
+    cudaError_t add_dirichlet_offset(const StageParams& sp, T* y, cudaStream_t st) {
+        const int L = std::max(g.nx, g.ny);
+        auto P = [&](int k) { return dprof + static_cast<size_t>(k) * L; };
+        auto params = [&](double c, int axis, molt::LineParams<double>* out) {
+            const int n = axis == 0 ? g.nx : g.ny;
+            const char* e = nullptr;
+            return molt::build_line_params(c, grid_h(n, axis == 0 ? g.Lx : g.Ly, bc), n, p.quad_order, bc, out, &e);
+        };
+        auto sweep1 = [&](const molt::LineParams<double>& lp, const double* in, double* out) {
+            molt::OpArgs<double> a;
+            a.in0 = in;
+            a.out0 = out;
+            return molt::sweep<double>(0, lp, molt::OP_COPY, a, lp.n, 1, nullptr, nullptr, st, &launches, nullptr);
+        };
+        auto lin1 = [&](double* out, int n, const double* x0, double c0, const double* x1, double c1, double c4) {
+            return molt::lincomb<double>(out, n, x0, c0, x1, c1, nullptr, 0, nullptr, 0, c4, st, &launches);
+        };
+        const double bg = sp.beta * (sp.lam - 2.0);   // beta g0
+        molt::LineParams<double> lix, lox;
+        if (!params(sp.c_in, 0, &lix) || !params(sp.c_out, 0, &lox)) return cudaErrorInvalidValue;
+        const int nx = g.nx, ny = g.ny;
+        cudaError_t e;
+        // x profiles: 0 = 1, 1 = phi_ix, 2 = phi_ox, 3 = psi1
+        if ((e = lin1(P(0), nx, nullptr, 0, nullptr, 0, 1.0)) != cudaSuccess ||
+            (e = sweep1(lix, P(0), P(1))) != cudaSuccess || (e = sweep1(lox, P(0), P(2))) != cudaSuccess ||
+            (e = sweep1(lox, P(1), P(3))) != cudaSuccess)
+            return e;
+        if (g.dim == 1) {
+            // beta_0 = (1 + beta g0) psi1 - beta g0 phi_o - 1 in profile 4, alpha_0 = 1 (profile 0)
+            if ((e = lin1(P(4), nx, P(3), 1.0 + bg, P(2), -bg, -1.0)) != cudaSuccess) return e;
+            molt::Separable sep{{P(0)}, {P(4)}, 1};
+            return molt::add_separable<T>(y, nx, 1, sep, st, &launches);
+        }
+        molt::LineParams<double> liy, loy;
+        if (!params(sp.c_in, 1, &liy) || !params(sp.c_out, 1, &loy)) return cudaErrorInvalidValue;
+        // y profiles: 5 = 1, 6 = phi_iy, 7 = a2, 8 = p1, 9 = p0, 10 = psi2, 11 = H_oy a2, 12 = H_oy p1,
+        // 13 = H_oy p0
+        if ((e = lin1(P(5), ny, nullptr, 0, nullptr, 0, 1.0)) != cudaSuccess ||
+            (e = sweep1(liy, P(5), P(6))) != cudaSuccess ||
+            (e = lin1(P(7), ny, P(6), -1.0, nullptr, 0, 1.0)) != cudaSuccess ||
+            (e = lin1(P(8), ny, P(6), 2.0 * bg - 1.0, nullptr, 0, 1.0 - bg)) != cudaSuccess ||
+            (e = lin1(P(9), ny, P(6), 1.0 - bg, nullptr, 0, 0.0)) != cudaSuccess ||
+            (e = sweep1(loy, P(6), P(10))) != cudaSuccess || (e = sweep1(loy, P(7), P(11))) != cudaSuccess ||
+            (e = sweep1(loy, P(8), P(12))) != cudaSuccess || (e = sweep1(loy, P(9), P(13))) != cudaSuccess)
+            return e;
+        // row weights of the four products: 14 = psi2 + H_oy p1 - a2 (with psi1), 15 = -H_oy a2 (with
+        // phi_ix), 13 = H_oy p0 - phi_iy (with phi_ox), 10 = -psi2 (with 1)
+        if ((e = molt::lincomb<double>(P(14), ny, P(10), 1.0, P(12), 1.0, P(7), -1.0, nullptr, 0, 0.0, st,
+                                       &launches)) != cudaSuccess ||
+            (e = lin1(P(15), ny, P(11), -1.0, nullptr, 0, 0.0)) != cudaSuccess ||
+            (e = lin1(P(13), ny, P(13), 1.0, P(6), -1.0, 0.0)) != cudaSuccess ||
+            (e = lin1(P(10), ny, P(10), -1.0, nullptr, 0, 0.0)) != cudaSuccess)
+            return e;
+        molt::Separable sep{{P(14), P(15), P(13), P(10)}, {P(3), P(1), P(2), P(0)}, 4};
+        return molt::add_separable<T>(y, nx, ny, sep, st, &launches);
     }
 
     // Everything one fixed-point iteration of a stage launches (line parameters by value).
@@ -555,6 +632,8 @@ struct Solver final : molt_solver {
             if ((e = mm_inv(sp.c_in, rhs, f2, st)) != cudaSuccess) return cuda_fail(e, "rhs inverse");
             if ((e = mm_inv(sp.c_out, f2, Y, st)) != cudaSuccess) return cuda_fail(e, "rhs inverse");
         }
+        if (!given && bc == molt::BC_DIRICHLET && (e = add_dirichlet_offset(sp, Y, st)) != cudaSuccess)
+            return cuda_fail(e, "Dirichlet offset");
         if (exec_mode == MOLT_EXEC_GRAPH && !prof.on) {
             LoopGraph* lg = loop_graph(tau, ps);
             if (lg) {

@@ -304,13 +304,20 @@ rows_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, i
 }
 
 // =========================================================================================
-// Rows, FP32, persistent and pipelined.  A block owns one line per iteration with K = 16
-// positions per thread (TL = n / 16 threads) and loops over lines blockIdx.x, +gridDim.x, ...
-// The staged input fields of the next line arrive by cp.async (16-byte chunks, swizzled) into
-// the other half of a double buffer while the current line is swept; the epilogue's auxiliary
-// fields of the current line are fetched the same way during the sweep.  Window reads and the
-// epilogue work on 128-bit chunks; outputs are stored from registers.
-// Requires n % 512 == 0, 1024 <= n <= 8192, 16-byte aligned rows.
+// Rows, FP32, persistent and pipelined.  A line of n nodes is split over a cluster of C blocks
+// (C = 1 or 2; the cluster's blocks are consecutive in x): block rank r owns the slice
+// [r n/C, (r+1) n/C) with K = 16 positions per thread (TL = n / (16 C) threads).  Clusters loop
+// over lines cluster_id, + number of clusters, ...  The staged input fields of the next line's
+// slice, with one 16-byte chunk of halo on each side, arrive by cp.async (16-byte chunks,
+// swizzled within 128-byte lines) into the other half of a double buffer while the current line
+// is swept; the epilogue's auxiliary fields of the current slice are fetched the same way.
+// Window reads and the epilogue work on 128-bit chunks; outputs are stored from registers.
+// With C > 1 the blocks of a cluster exchange their slice segments (decay, left and right
+// aggregates) through distributed shared memory once per line, so every block composes the
+// carry entering its slice and the line totals of the boundary solve from the same values in the
+// same order.  C = 2 serves lines whose staged fields do not fit one block (16384 nodes, or four
+// staged fields of 8192 nodes).
+// Requires n % (512 C) == 0, 1024 <= n <= 8192 C, TL <= 512, 16-byte aligned rows.
 // =========================================================================================
 __device__ __forceinline__ float comp4(const float4& v, int e) {
     return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
@@ -322,7 +329,32 @@ __device__ __forceinline__ void set4(float4& v, int e, float x) {
     else v.w = x;
 }
 
-template <int M, class Op>
+// Thread-block cluster primitives (sm_90 and later).
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Load a float from the shared memory of block `rank` of this cluster at the address of `local`.
+__device__ __forceinline__ float ld_cluster_f32(const float* local, unsigned rank) {
+    unsigned remote;
+    float v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(static_cast<unsigned>(__cvta_generic_to_shared(local))), "r"(rank));
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote) : "memory");
+    return v;
+}
+
+// Index of local chunk lc (-1 .. nchl) in a staged slice: the nchl swizzled chunks of the slice
+// from the buffer's start (so every group of 8 chunks is one aligned 128-byte line of the swizzle),
+// then the left and the right halo chunk.
+__device__ __forceinline__ int staged_index(int lc, int nchl) {
+    return lc < 0 ? nchl : (lc >= nchl ? nchl + 1 : swz(lc));
+}
+
+template <int M, class Op, int C>
 __global__ void __launch_bounds__(512, 1)
 rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_constant__ PackedStencil pw, const Op op,
                  int nlines, long long ld, unsigned long long* red_slots) {
@@ -336,61 +368,75 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
     float4* sm = reinterpret_cast<float4*>(sm_rows_pipe);
     __shared__ T s_scan[16][2 + 2 * NF];   // per-warp segments: D_f, D_b, A_f[NF], A_b[NF]
     __shared__ T s_bnd[2 * NF];            // carries / B values of the line (FP64 solve)
+    __shared__ T s_xch[2][1 + 2 * NF];     // this block's slice segment, by line parity (C > 1)
 
     const int n = lp.n;
-    const int nch = n / V;
+    const int nch = n / V;                 // chunks of the line
+    const int nchl = nch / C;              // chunks of this block's slice
+    const int rank = C > 1 ? static_cast<int>(cluster_rank()) : 0;
+    const int c0 = rank * nchl;            // first chunk of the slice
+    const int slice0 = c0 * V;             // first position of the slice
     const int TL = blockDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wpl = TL >> 5;
     const bool periodic = lp.bc == BC_PERIODIC;
     const T d = lp.d;
-    const int start = tid * K;
+    const int lstart = tid * K;            // first position of the thread's chunk within the slice
+    const int start = slice0 + lstart;     // ... within the line
     T D = T(1);
 #pragma unroll
     for (int k = 0; k < K; ++k) D *= d;
     const T pl = dev_exp(-lp.nu * T(periodic ? start : start - 1));
     const T pr = dev_exp(-lp.nu * T(periodic ? n - start - K : n - start - K - 1));
 
-    auto stage_buf = [&](int sb, int f) { return sm + (static_cast<size_t>(sb) * NS + f) * nch; };
-    auto aux_buf = [&](int f) { return sm + (static_cast<size_t>(2 * NS) + f) * nch; };
+    const int sbuf = nchl + 8;             // staged chunks per field: slice, two halo chunks, padding to
+                                           // a multiple of 8 chunks (128-byte aligned buffers)
+    auto stage_buf = [&](int sb, int f) { return sm + (static_cast<size_t>(sb) * NS + f) * sbuf; };
+    auto aux_buf = [&](int f) { return sm + static_cast<size_t>(2 * NS) * sbuf + static_cast<size_t>(f) * nchl; };
     auto issue_staged = [&](int ln, int sb) {
 #pragma unroll
         for (int f = 0; f < NS; ++f) {
             const float4* src = reinterpret_cast<const float4*>(op.s[f] + ln * ld);
             float4* dst = stage_buf(sb, f);
-            for (int c = tid; c < nch; c += TL) cp_async16(dst + swz(c), src + c);
+            for (int c = tid; c < nchl + 2; c += TL) {
+                const int lc = c - 1;
+                int gc = c0 + lc;
+                if (periodic) gc = gc < 0 ? gc + nch : (gc >= nch ? gc - nch : gc);
+                else gc = gc < 0 ? 0 : (gc >= nch ? nch - 1 : gc);
+                cp_async16(dst + staged_index(lc, nchl), src + gc);
+            }
         }
     };
 
+    const int cid = C > 1 ? static_cast<int>(blockIdx.x) / C : static_cast<int>(blockIdx.x);
+    const int ncl = C > 1 ? static_cast<int>(gridDim.x) / C : static_cast<int>(gridDim.x);
     RedAcc<T> red{T(0), T(0)};
-    int line = blockIdx.x;
+    int line = cid;
     if (line < nlines) issue_staged(line, 0);
     cp_async_commit();
-    for (int it = 0; line < nlines; ++it, line += gridDim.x) {
+    for (int it = 0; line < nlines; ++it, line += ncl) {
         const int sb = it & 1;
         cp_async_wait<0>();          // this line's staged fields (the only group in flight)
         __syncthreads();             // ... visible to all; every warp is done with the last line
-        // auxiliary fields of this line, then the staged fields of the next line
+        // auxiliary fields of this slice, then the staged fields of the next line
 #pragma unroll
         for (int f = 0; f < NA; ++f) {
-            const float4* src = reinterpret_cast<const float4*>(op.a[f] + line * ld);
+            const float4* src = reinterpret_cast<const float4*>(op.a[f] + line * ld) + c0;
             float4* dst = aux_buf(f);
-            for (int c = tid; c < nch; c += TL) cp_async16(dst + swz(c), src + c);
+            for (int c = tid; c < nchl; c += TL) cp_async16(dst + swz(c), src + c);
         }
         cp_async_commit();
-        const int next = line + gridDim.x;
+        const int next = line + ncl;
         if (next < nlines) issue_staged(next, sb ^ 1);
         cp_async_commit();
 
-        // ---- window (prologue applied) from chunks start/V - 1 .. start/V + KC ----
+        // ---- window (prologue applied) from local chunks lstart/V - 1 .. lstart/V + KC ----
         T fw[NF][WC * V];
 #pragma unroll
         for (int j = 0; j < WC; ++j) {
-            int c = start / V - 1 + j;
-            if (periodic) c = c < 0 ? c + nch : (c >= nch ? c - nch : c);
-            else c = c < 0 ? 0 : (c >= nch ? nch - 1 : c);
+            const int idx = staged_index(lstart / V - 1 + j, nchl);
             float4 raw[NS];
 #pragma unroll
-            for (int f = 0; f < NS; ++f) raw[f] = stage_buf(sb, f)[swz(c)];
+            for (int f = 0; f < NS; ++f) raw[f] = stage_buf(sb, f)[idx];
 #pragma unroll
             for (int e = 0; e < V; ++e) {
                 T sv[NS], fv[NF];
@@ -403,10 +449,13 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
         }
         T JL[kPack ? 1 : NF][K], JR[kPack ? 1 : NF][K], aL[NF], aR[NF];
         unsigned long long JL2[kPack ? K : 1], JR2[kPack ? K : 1];   // packed J (then outputs)
+        // field q at line position p of this block's slice (wall stencils only)
         auto at_field = [&](int p, int q) {
+            const int pl_ = p - slice0;
             T sv[NS], fv[NF];
 #pragma unroll
-            for (int f = 0; f < NS; ++f) sv[f] = reinterpret_cast<const T*>(stage_buf(sb, f) + swz(p / V))[p % V];
+            for (int f = 0; f < NS; ++f)
+                sv[f] = reinterpret_cast<const T*>(stage_buf(sb, f) + staged_index(pl_ / V, nchl))[pl_ % V];
             op.prologue(sv, fv);
             return fv[q];
         };
@@ -462,7 +511,7 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
             }
             if (!periodic && (start == 0 || start + K == n)) {
                 // chunks touching a wall: the shifted wall stencils, field by field (as
-                // local_integrals), node values gathered from the staged line
+                // local_integrals), node values gathered from the staged slice
                 const int N = lp.N, jb = N - H + 1;
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
@@ -565,6 +614,7 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
         }
         __syncthreads();
         // ---- warp 0 scans the warp segments (log depth) and solves the boundary system ----
+        T exF[NF], exB[NF], totF[NF], totB[NF], exDf = T(1), exDb = T(1);
         if (warp == 0) {
             const bool has = lane < wpl;
             T fD = has ? s_scan[lane][0] : T(1);
@@ -589,7 +639,6 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
                 if (lane >= o) fD = pfD * fD;
                 if (lane + o < 32) bD = pbD * bD;
             }
-            T exF[NF], exB[NF], totF[NF], totB[NF];
 #pragma unroll
             for (int q = 0; q < NF; ++q) {
                 exF[q] = __shfl_up_sync(kFull, fA[q], 1);
@@ -599,8 +648,61 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
                 if (lane == 0) exF[q] = T(0);
                 if (lane + 1 >= wpl) exB[q] = T(0);
             }
+            if constexpr (C > 1) {
+                exDf = __shfl_up_sync(kFull, fD, 1);      // decay of the warps before this one
+                exDb = __shfl_down_sync(kFull, bD, 1);    // ... and after it
+                if (lane == 0) exDf = T(1);
+                if (lane + 1 >= wpl) exDb = T(1);
+                const T Dc = __shfl_sync(kFull, fD, 31);  // decay over the slice
+                if (lane == 0) {
+                    s_xch[it & 1][0] = Dc;
+#pragma unroll
+                    for (int q = 0; q < NF; ++q) {
+                        s_xch[it & 1][1 + q] = totF[q];
+                        s_xch[it & 1][1 + NF + q] = totB[q];
+                    }
+                }
+            }
+        }
+        if constexpr (C > 1) {
+            // the slice segments of the cluster's blocks, read by every block in rank order
+            cluster_barrier();
+            if (warp == 0) {
+                T Ef[NF], Eb[NF], IN[NF], I0[NF];
+#pragma unroll
+                for (int q = 0; q < NF; ++q) Ef[q] = Eb[q] = IN[q] = I0[q] = T(0);
+#pragma unroll
+                for (int r = 0; r < C; ++r) {                     // forward: ranks in order
+                    const T Dr = ld_cluster_f32(&s_xch[it & 1][0], r);
+#pragma unroll
+                    for (int q = 0; q < NF; ++q) {
+                        const T Fr = ld_cluster_f32(&s_xch[it & 1][1 + q], r);
+                        if (r < rank) Ef[q] = fma(Ef[q], Dr, Fr);
+                        IN[q] = fma(IN[q], Dr, Fr);
+                    }
+                }
+#pragma unroll
+                for (int r = C - 1; r >= 0; --r) {                // backward: ranks in reverse
+                    const T Dr = ld_cluster_f32(&s_xch[it & 1][0], r);
+#pragma unroll
+                    for (int q = 0; q < NF; ++q) {
+                        const T Br = ld_cluster_f32(&s_xch[it & 1][1 + NF + q], r);
+                        if (r > rank) Eb[q] = fma(Eb[q], Dr, Br);
+                        I0[q] = fma(I0[q], Dr, Br);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < NF; ++q) {
+                    exF[q] = fma(Ef[q], exDf, exF[q]);   // carry entering the warp from the line start
+                    exB[q] = fma(Eb[q], exDb, exB[q]);   // ... and from the line end
+                    totF[q] = IN[q];
+                    totB[q] = I0[q];
+                }
+            }
+        }
+        if (warp == 0) {
             __syncwarp();
-            if (has) {
+            if (lane < wpl) {
 #pragma unroll
                 for (int q = 0; q < NF; ++q) {
                     s_scan[lane][2 + q] = exF[q];
@@ -677,7 +779,7 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
         }
 #pragma unroll
         for (int kc = 0; kc < KC; ++kc) {
-            const int c = start / V + kc;
+            const int c = lstart / V + kc;          // local chunk
             float4 sraw[NS], araw[NA > 0 ? NA : 1], outv[NO];
 #pragma unroll
             for (int f = 0; f < NS; ++f) sraw[f] = stage_buf(sb, f)[swz(c)];
@@ -701,10 +803,12 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
                 for (int o = 0; o < NO; ++o) set4(outv[o], e, ov[o]);
             }
 #pragma unroll
-            for (int o = 0; o < NO; ++o) reinterpret_cast<float4*>(op.o[o] + line * ld)[c] = outv[o];
+            for (int o = 0; o < NO; ++o) reinterpret_cast<float4*>(op.o[o] + line * ld)[c0 + c] = outv[o];
         }
     }
     cp_async_wait<0>();
+    // no block of a cluster leaves while another may still read its exchange slots
+    if constexpr (C > 1) cluster_barrier();
     if (Op::kReduce) block_reduce_store<T>(red, red_slots);
 }
 

@@ -18,8 +18,11 @@ from paper_1611_04214_gb300.inputs import uniform_noise  # noqa: E402
 
 from _parity import check_fp32  # noqa: E402
 
-# converged cases whose contraction factor puts 1e-6 below the FP32 rounding floor
-BATCH_RHO_LIMITED: set = set()
+# converged cases whose contraction factor puts 1e-6 below the FP32 rounding floor (rho measured by
+# the oracle on the same run)
+BATCH_RHO_LIMITED = {
+    "batch_instance4_64x24_neumann_be_2steps_converged",   # rho = 0.991
+}
 
 
 @pytest.fixture(scope="module", autouse=True)
