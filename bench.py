@@ -296,6 +296,7 @@ def batched_leg(args, sample: int = 16):
            "fixed_point": {"tol": BATCH["tol"], "max_iter": args.batch_iters}}
     with Batch([(int(s), int(s), L, L, float(e)) for s, e in zip(sides, eps)], bc=BATCH["bc"], quad_order=BATCH["M"],
                tol=BATCH["tol"], max_iter=args.batch_iters) as b:
+        out["schedule"] = b.autotune(dts) if not args.no_autotune else None
         u = torch.tensor(b.pack(u0), device="cuda")
         b.step(u, dts, "be", raise_on_nonconvergence=False)          # warm-up (builds the graph)
         torch.cuda.synchronize()
@@ -502,7 +503,45 @@ def sweep_microbench(reps: int = 10):
                     "gpts_per_s": n * n / (ms * 1e-3) / 1e9, "gbs_algorithmic": gbs, "frac_of_peak": gbs / peak})
         del fin, fout
         torch.cuda.empty_cache()
+    out.append(tc_sweep_case(peak, reps))
     return out
+
+
+def tc_sweep_case(peak, reps: int = 10, n: int = 8192):
+    """The tensor-core row sweep (FP16 split products, molt_helmholtz_rows_tc) on the same 8192^2
+    periodic x case as the FP32 row sweep, with its largest difference from the FP32 sweep."""
+    import torch
+
+    from paper_1611_04214_gb300.molt import Solver
+    h = 2 * 3.141592653589793 / n
+    c = (h / 0.08) ** 2
+    g = torch.Generator(device="cuda").manual_seed(1)
+    fin = torch.rand((n, n), generator=g, device="cuda", dtype=torch.float32) * 2
+    fout = torch.empty_like(fin)
+    ref = torch.empty_like(fin)
+    try:
+        with Solver(nx=n, ny=n, bc="periodic", quad_order=4, precision="fp32", eps=0.02) as s:
+            s.helmholtz_apply(0, c, fin, ref)
+            for _ in range(2):
+                s.helmholtz_rows_tc(c, fin, fout)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                s.helmholtz_rows_tc(c, fin, fout)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            diff = ((fout - ref).abs().max() / ref.abs().max()).item()
+    except Exception as exc:
+        return {"n": n, "variant": "tensor_core_fp16_split", "error": f"{type(exc).__name__}: {exc}"}
+    finally:
+        del fin, fout, ref
+        torch.cuda.empty_cache()
+    gbs = 8 * n * n / (ms * 1e-3) / 1e9
+    return {"n": n, "precision": "fp32 (fp16 split products)", "bc": "periodic", "axis": "x",
+            "variant": "tensor_core_fp16_split", "ms": ms, "gpts_per_s": n * n / (ms * 1e-3) / 1e9,
+            "gbs_algorithmic": gbs, "frac_of_peak": gbs / peak, "max_rel_diff_vs_fp32_sweep": diff}
 
 
 CONFIG2 = dict(name="ch2d_1024_neumann_bdf2_converged", n=1024, eps=0.05, dt=1e-4, steps=200, tol=1e-6,
@@ -638,6 +677,8 @@ def run_ours(args, rank, world, dist):
     solver = Solver(nx=n, ny=n, bc=WORKLOAD["bc"], eps=WORKLOAD["eps"], quad_order=WORKLOAD["M"],
                     precision=args.precision, tol=1e-6, max_iter=args.iters, Lx=WORKLOAD["L"], Ly=WORKLOAD["L"])
     dtype = solver.dtype
+    # the product's launch choices for this grid: every sweep's kernel family timed once
+    tuning = solver.autotune() if not args.no_autotune else None
     u = torch.tensor(u0, dtype=dtype, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -771,7 +812,8 @@ def run_ours(args, rank, world, dist):
                   "final_residual": last.residual, "hbm_frac_step_algorithmic": hbm_frac_step,
                   "ms_per_step_graph_mode": graph_ms, "fp32_vs_fp64": fp64, "batched": batched,
                   "sweep_microbench": sweeps_mb, "vector_ch": vch, "kernels": kernels,
-                  "converged_l2_resident": converged, "oracle_parity": parity, "fma_probe": fp64_probe}
+                  "converged_l2_resident": converged, "oracle_parity": parity, "fma_probe": fp64_probe,
+                  "autotune": tuning}
         if parity and "config3_crop1024_fp32" in parity:
             result["config3_crop_err_vs_oracle"] = {p_: parity[f"config3_crop1024_{p_}"]["max_rel_err_v"]
                                                     for p_ in ("fp32", "fp64")}
@@ -793,6 +835,7 @@ def main():
     ap.add_argument("--skip-vch", action="store_true", help="skip the vector Cahn-Hilliard leg")
     ap.add_argument("--skip-converged", action="store_true", help="skip the converged 1024^2 Neumann BDF2 leg")
     ap.add_argument("--skip-oracle", action="store_true", help="skip the host-core oracle (cpu_baseline, parity)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel families (no molt_autotune)")
     ap.add_argument("--vch-workload", default="mixture", choices=sorted(VCH_WORKLOADS),
                     help="vector-model workload of the vector_ch leg")
     ap.add_argument("--vch-only", action="store_true",

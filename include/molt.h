@@ -156,6 +156,61 @@ molt_status molt_mass(molt_solver* solver, const void* u_dev, double* mass, void
 molt_status molt_helmholtz_apply(molt_solver* solver, int axis, double c, const void* in_dev,
                                  void* out_dev, void* stream);
 
+/* The same H_c along x (every row) computed on the tensor cores: the chunked form of the
+ * recurrences of Eq. IL / IR as products of 128 x (128 + M) decay-times-quadrature matrices with one
+ * window of 128 + M node values per 128-node chunk, on FP16 high / low splits of both operands
+ * (three products, FP32 accumulation), followed by an FP32 carry scan per line with the FP64
+ * periodic boundary correction (Eq. homogeneous).  An experiment on the split-precision
+ * chunked-recurrence variant; molt_helmholtz_apply remains the production sweep.
+ * Needs an FP32 solver on a periodic grid with nx a power of two in [1024, 8192] and ny a multiple
+ * of 8192 / nx; in_dev and out_dev distinct.  Allocates about 0.45 MB of operand workspace on
+ * first use and rebuilds the operands (host FP64, one synchronizing upload) whenever c changes.
+ * Errors: MOLT_ERR_ARG, MOLT_ERR_UNSUPPORTED, MOLT_ERR_OOM, MOLT_ERR_CUDA (including a product
+ * that did not complete within its one-second wait, reported through the solver's status word
+ * at its next step). */
+molt_status molt_helmholtz_rows_tc(molt_solver* solver, double c, const void* in_dev, void* out_dev, void* stream);
+
+/* ---- Autotuner (no counterpart in the paper) ------------------------------------------------
+ * Each sweep of a step can run on several kernel families; molt_autotune times every one that is
+ * available for the solver's grid and keeps the fastest for the solver's later sweeps.
+ *   rows:    MOLT_LAUNCH_ROWS_ONE_BLOCK (the pipelined kernel, one block per line),
+ *            MOLT_LAUNCH_ROWS_CLUSTER2 (the pipelined kernel on a two-block cluster per line),
+ *            MOLT_LAUNCH_ROWS_GENERAL (the general row kernel),
+ *            MOLT_LAUNCH_ROWS_TENSOR_CORE (single H_c sweeps only: the chunked recurrence on the
+ *            tensor cores of molt_helmholtz_rows_tc; eligible only when its largest difference from
+ *            the FP32 sweep on the tuning data is within 1e-6 of the result's largest magnitude);
+ *   columns: MOLT_LAUNCH_COLS_TMA (TMA tiles), MOLT_LAUNCH_COLS_CP_ASYNC (cp.async tiles),
+ *            MOLT_LAUNCH_COLS_GENERAL (the general column kernels).
+ * The scan-versus-chunk choice of the row sweeps is the ROWS_* against ROWS_TENSOR_CORE choice. */
+enum {
+    MOLT_LAUNCH_DEFAULT = 0,
+    MOLT_LAUNCH_ROWS_ONE_BLOCK = 1,
+    MOLT_LAUNCH_ROWS_CLUSTER2 = 2,
+    MOLT_LAUNCH_ROWS_GENERAL = 3,
+    MOLT_LAUNCH_COLS_TMA = 4,
+    MOLT_LAUNCH_COLS_CP_ASYNC = 5,
+    MOLT_LAUNCH_COLS_GENERAL = 6,
+    MOLT_LAUNCH_ROWS_TENSOR_CORE = 7
+};
+
+typedef struct {
+    int pass;          /* 0 = single H_c sweeps (rhs inverses), 1..4 = 2D iteration passes, 5, 6 = 1D passes */
+    int axis;          /* 0 = rows (x), 1 = columns (y) */
+    int chosen;        /* MOLT_LAUNCH_* kept for this sweep (0: none available; the default stays) */
+    int candidates;    /* entries of launch[] and ms[] filled */
+    int launch[4];     /* the MOLT_LAUNCH_* timed */
+    double ms[4];      /* device ms per sweep; -1 = not available for this grid; negative = not eligible */
+    double tc_rel_diff; /* tensor-core candidate: largest difference from the FP32 sweep / largest |H f| */
+} molt_tuning;
+
+/* Time the candidates of every sweep of a step (FP32 solvers; FP64 solvers keep their one kernel
+ * family and report no entries) on hash-uniform test data in the solver's own work fields, and keep
+ * the fastest.  Up to `capacity` entries go to `entries` (may be NULL); *count (may be NULL)
+ * receives the number of sweeps tuned.  The solver's time history is cleared (its work fields were
+ * overwritten) and its cached loop graphs are rebuilt on next use.  Synchronizes `stream`.  Errors:
+ * MOLT_ERR_ARG, MOLT_ERR_CUDA. */
+molt_status molt_autotune(molt_solver* solver, void* stream, molt_tuning* entries, int capacity, int* count);
+
 /* Host-only diagnostic: the local quadrature weights of Sec. 3.2 for one stencil.
  * Writes M+1 weights of J^L (side = 0) or J^R (side = 1) for node offsets
  * offsets[0..M] (integers relative to the node) at nu = alpha*h > 0, including the
@@ -261,6 +316,23 @@ typedef struct {
 molt_status molt_step_adaptive(molt_solver* solver, void* u_dev, double dt, const molt_adaptive* params,
                                void* stream, molt_adaptive_info* info);
 
+/* One adaptive step of the vector model (Sec. 5.2) under Algorithm 1 as Sec. 6.2.2 runs it, in
+ * place on the two device fields u1, u2 (distinct, the solver's grid and precision), starting
+ * with a trial size dt.  Estimators (params.estimator):
+ *   MOLT_LTE_RICHARDSON: one vector BE step of dt and two of dt/2, eta = (1/2) max over both
+ *     components of |u_dt - u_dt/2|; the two-half-step state is kept.
+ *   MOLT_LTE_BDF2: one vector BE step and one variable-step BDF2 step (the formula of
+ *     molt_step_adaptive) over the same interval from the state before the previous accepted
+ *     step; eta = max over both components of |u_BDF2 - u_BE|; the BDF2 state is kept.  Without
+ *     that history (the first call, or after molt_vch_step, molt_reset_history, molt_set_params,
+ *     molt_set_bc) the Richardson estimate is used.
+ * Accept / reject and the next step size follow the rule documented at molt_step_adaptive.
+ * Allocates six more work fields on first use.  Errors: MOLT_ERR_ARG, MOLT_ERR_UNSUPPORTED (another
+ * estimator), MOLT_ERR_NOT_CONVERGED (dt_min reached; the fields are unchanged), MOLT_ERR_CUDA,
+ * MOLT_ERR_OOM. */
+molt_status molt_vch_step_adaptive(molt_solver* solver, void* u1_dev, void* u2_dev, double dt,
+                                   const molt_adaptive* params, void* stream, molt_adaptive_info* info);
+
 /* ---- Batched instances ----------------------------------------------------------------
  * Many independent 2D problems, each with its own grid size, eps and time step, stepped
  * together in FP32.  Every instance follows Sec. 2-5 exactly as molt_step does (stage
@@ -304,6 +376,23 @@ molt_status molt_batch_set_execution(molt_batch* batch, molt_execution mode);
  * schemes, MOLT_ERR_ARG, MOLT_ERR_CUDA. */
 molt_status molt_batch_step(molt_batch* batch, float* u_dev, const double* dt, molt_scheme scheme, void* stream,
                             int* iters, double* residual, int* status);
+
+/* Schedule autotuner of the batched passes (no counterpart in the paper).  Every batched kernel
+ * walks its work list (row items, column tiles, carry items) from its block index in steps of the
+ * grid size, so one launch runs either one block per work item or a persistent grid of a few
+ * blocks per SM looping over the items.  This call times one fixed-point iteration of every
+ * instance under each of 4 x 4 schedules (rows x columns: one block per item, 2, 4 or 8 blocks per
+ * SM), with the stage parameters of the steps dt (host array of `count`), and keeps the fastest
+ * for later steps.  ms_table (16 entries, row schedule major; may be NULL) receives the times,
+ * grid_rows / grid_cols (may be NULL) the chosen grids (0 = one block per item).  It overwrites
+ * the batch's work fields and forgets the BDF2 history; synchronizes `stream`.  Errors:
+ * MOLT_ERR_ARG, MOLT_ERR_CUDA. */
+molt_status molt_batch_autotune(molt_batch* batch, const double* dt, void* stream, double* ms_table, int* grid_rows,
+                                int* grid_cols);
+
+/* Set the schedule of the batched passes directly: grid_rows / grid_cols blocks per row / column
+ * launch (0 = one block per work item).  Results do not depend on it.  Errors: MOLT_ERR_ARG. */
+molt_status molt_batch_set_schedule(molt_batch* batch, int grid_rows, int grid_cols);
 
 /* Last error message of `solver` (or of the last failed create/ABI call when NULL). */
 const char* molt_last_error(const molt_solver* solver);

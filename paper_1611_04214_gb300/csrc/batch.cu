@@ -102,76 +102,93 @@ __device__ __forceinline__ void load_lp(LineParams<float>& dst, const LineParams
     __syncthreads();
 }
 
+// Every batched kernel walks its work list from item blockIdx.x in steps of gridDim.x, so one
+// launch may run one block per item or a persistent grid that loops over the items (the grid size
+// is the batch's schedule, chosen by molt_batch_autotune).  The block barrier at the end of each
+// item keeps the next item's shared-memory writes behind this item's reads.
+
 template <int M, class Op>
 __global__ void __launch_bounds__(kRowThreads)
-rows_batch_kernel(const RowItem* __restrict__ items, const Inst* __restrict__ inst,
+rows_batch_kernel(const RowItem* __restrict__ items, int nitems, const Inst* __restrict__ inst,
                   const LineParams<float>* __restrict__ lps, int slot, const Stage* __restrict__ stages,
                   const int* __restrict__ done, const Op op0, unsigned long long* red) {
-    const RowItem it = items[blockIdx.x];
-    if (done != nullptr && done[it.inst]) return;
     __shared__ LineParams<float> slp;
-    load_lp(slp, lps + 4 * it.inst + slot);
-    const Inst in = inst[it.inst];
-    Op op = op0;
-    place(op, in.off);
-    coeffs(op, stages[it.inst]);
-    op.ls = in.nx;
-    op.ps = 1;
     extern __shared__ __align__(16) unsigned char sm_rows_batch[];
-    rows_body<float, M, kRowK, Op>(slp, op, in.ny, it.tl_log2, it.lpb, it.pitch, it.line0,
-                                   reinterpret_cast<float*>(sm_rows_batch), red + 2 * it.inst);
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const RowItem it = items[i];
+        if (done != nullptr && done[it.inst]) continue;
+        load_lp(slp, lps + 4 * it.inst + slot);
+        const Inst in = inst[it.inst];
+        Op op = op0;
+        place(op, in.off);
+        coeffs(op, stages[it.inst]);
+        op.ls = in.nx;
+        op.ps = 1;
+        rows_body<float, M, kRowK, Op>(slp, op, in.ny, it.tl_log2, it.lpb, it.pitch, it.line0,
+                                       reinterpret_cast<float*>(sm_rows_batch), red + 2 * it.inst);
+        __syncthreads();
+    }
 }
 
 template <int M, class Op>
 __global__ void __launch_bounds__(32 * kColWY)
-cols_agg_batch_kernel(const ColItem* __restrict__ items, const Inst* __restrict__ inst,
+cols_agg_batch_kernel(const ColItem* __restrict__ items, int nitems, const Inst* __restrict__ inst,
                       const LineParams<float>* __restrict__ lps, int slot, const Stage* __restrict__ stages,
                       const int* __restrict__ done, const Op op0, float* aggL, float* aggR) {
-    const ColItem it = items[blockIdx.x];
-    if (done != nullptr && done[it.inst]) return;
     __shared__ LineParams<float> slp;
-    load_lp(slp, lps + 4 * it.inst + slot);
-    const Inst in = inst[it.inst];
-    Op op = op0;
-    place(op, in.off);
-    coeffs(op, stages[it.inst]);
-    op.ls = 1;
-    op.ps = in.nx;
-    cols_agg_body<float, M, kColKY, kColWY, Op>(slp, op, in.nx, aggL + in.soff, aggR + in.soff, in.tiles, it.strip,
-                                                it.tile);
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const ColItem it = items[i];
+        if (done != nullptr && done[it.inst]) continue;
+        load_lp(slp, lps + 4 * it.inst + slot);
+        const Inst in = inst[it.inst];
+        Op op = op0;
+        place(op, in.off);
+        coeffs(op, stages[it.inst]);
+        op.ls = 1;
+        op.ps = in.nx;
+        cols_agg_body<float, M, kColKY, kColWY, Op>(slp, op, in.nx, aggL + in.soff, aggR + in.soff, in.tiles,
+                                                    it.strip, it.tile);
+        __syncthreads();
+    }
 }
 
 __global__ void __launch_bounds__(kCarryThreads)
-carry_batch_kernel(const CarryItem* __restrict__ items, const Inst* __restrict__ inst,
+carry_batch_kernel(const CarryItem* __restrict__ items, int nitems, const Inst* __restrict__ inst,
                    const LineParams<float>* __restrict__ lps, int slot, const int* __restrict__ done, int nf,
                    const float* aggL, const float* aggR, float* carL, float* carR) {
-    const CarryItem it = items[blockIdx.x];
-    if (done != nullptr && done[it.inst]) return;
     __shared__ LineParams<float> slp;
-    load_lp(slp, lps + 4 * it.inst + slot);
-    const Inst in = inst[it.inst];
-    carry_body<float>(slp, in.nx, nf, in.tiles, kColR, aggL + in.soff, aggR + in.soff, carL + in.soff,
-                      carR + in.soff, it.idx0 + static_cast<int>(threadIdx.x));
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const CarryItem it = items[i];
+        if (done != nullptr && done[it.inst]) continue;
+        load_lp(slp, lps + 4 * it.inst + slot);
+        const Inst in = inst[it.inst];
+        carry_body<float>(slp, in.nx, nf, in.tiles, kColR, aggL + in.soff, aggR + in.soff, carL + in.soff,
+                          carR + in.soff, it.idx0 + static_cast<int>(threadIdx.x));
+        __syncthreads();
+    }
 }
 
 template <int M, class Op>
 __global__ void __launch_bounds__(32 * kColWY)
-cols_final_batch_kernel(const ColItem* __restrict__ items, const Inst* __restrict__ inst,
+cols_final_batch_kernel(const ColItem* __restrict__ items, int nitems, const Inst* __restrict__ inst,
                         const LineParams<float>* __restrict__ lps, int slot, const Stage* __restrict__ stages,
                         const int* __restrict__ done, const Op op0, const float* carL, const float* carR,
                         unsigned long long* red) {
-    const ColItem it = items[blockIdx.x];
-    if (done != nullptr && done[it.inst]) return;
     __shared__ LineParams<float> slp;
-    load_lp(slp, lps + 4 * it.inst + slot);
-    const Inst in = inst[it.inst];
-    Op op = op0;
-    place(op, in.off);
-    coeffs(op, stages[it.inst]);
-    op.ls = 1;
-    op.ps = in.nx;
-    cols_final_body<float, M, kColKY, kColWY, Op>(slp, op, in.nx, carL + in.soff, carR + in.soff, in.tiles, it.strip,
-                                                  it.tile, red + 2 * it.inst);
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const ColItem it = items[i];
+        if (done != nullptr && done[it.inst]) continue;
+        load_lp(slp, lps + 4 * it.inst + slot);
+        const Inst in = inst[it.inst];
+        Op op = op0;
+        place(op, in.off);
+        coeffs(op, stages[it.inst]);
+        op.ls = 1;
+        op.ps = in.nx;
+        cols_final_body<float, M, kColKY, kColWY, Op>(slp, op, in.nx, carL + in.soff, carR + in.soff, in.tiles,
+                                                      it.strip, it.tile, red + 2 * it.inst);
+        __syncthreads();
+    }
 }
 
 __global__ void loop_init_batch_kernel(LoopState* ls, unsigned long long* red, int* done, int n) {
@@ -259,6 +276,7 @@ struct molt_batch {
     std::vector<Inst> inst_h;
     long long total = 0, scratch = 0;
     int row_smem = 0, n_row = 0, n_col = 0, n_carry[2] = {0, 0};
+    int grid_rows = 0, grid_cols = 0;   // schedule: blocks per row / column launch (0 = one per item)
     // device
     Inst* inst = nullptr;
     LineParams<float>* lps = nullptr;   // [count][4] (slots LIX, LOX, LIY, LOY)
@@ -330,10 +348,13 @@ bool balloc(molt_batch* b, U** p, size_t n) {
     return true;
 }
 
+// Grid of a pass over n work items under the batch's schedule (0 = one block per item).
+inline int pass_grid(int nitems, int cap) { return cap > 0 && cap < nitems ? cap : (nitems > 0 ? nitems : 1); }
+
 template <int M, class Op>
 cudaError_t rows_pass(molt_batch* b, int slot, const Op& op, bool skip, cudaStream_t st) {
-    rows_batch_kernel<M, Op><<<b->n_row, kRowThreads, b->row_smem, st>>>(b->rows, b->inst, b->lps, slot, b->stages,
-                                                                          skip ? b->done : nullptr, op, b->red);
+    rows_batch_kernel<M, Op><<<pass_grid(b->n_row, b->grid_rows), kRowThreads, b->row_smem, st>>>(
+        b->rows, b->n_row, b->inst, b->lps, slot, b->stages, skip ? b->done : nullptr, op, b->red);
     b->launches += 1;
     return cudaGetLastError();
 }
@@ -343,12 +364,13 @@ cudaError_t cols_pass(molt_batch* b, int slot, const Op& op, bool skip, cudaStre
     constexpr int NF = Op::NF;
     const int* dn = skip ? b->done : nullptr;
     const dim3 blk(32, kColWY);
-    cols_agg_batch_kernel<M, Op><<<b->n_col, blk, 0, st>>>(b->cols, b->inst, b->lps, slot, b->stages, dn, op, b->aggL,
-                                                           b->aggR);
-    carry_batch_kernel<<<b->n_carry[NF - 1], kCarryThreads, 0, st>>>(b->carry[NF - 1], b->inst, b->lps, slot, dn, NF,
-                                                                      b->aggL, b->aggR, b->carL, b->carR);
-    cols_final_batch_kernel<M, Op><<<b->n_col, blk, 0, st>>>(b->cols, b->inst, b->lps, slot, b->stages, dn, op,
-                                                             b->carL, b->carR, b->red);
+    const int nc = b->n_carry[NF - 1];
+    cols_agg_batch_kernel<M, Op><<<pass_grid(b->n_col, b->grid_cols), blk, 0, st>>>(
+        b->cols, b->n_col, b->inst, b->lps, slot, b->stages, dn, op, b->aggL, b->aggR);
+    carry_batch_kernel<<<pass_grid(nc, b->grid_cols), kCarryThreads, 0, st>>>(
+        b->carry[NF - 1], nc, b->inst, b->lps, slot, dn, NF, b->aggL, b->aggR, b->carL, b->carR);
+    cols_final_batch_kernel<M, Op><<<pass_grid(b->n_col, b->grid_cols), blk, 0, st>>>(
+        b->cols, b->n_col, b->inst, b->lps, slot, b->stages, dn, op, b->carL, b->carR, b->red);
     b->launches += 3;
     return cudaGetLastError();
 }
@@ -745,6 +767,72 @@ molt_status molt_batch_step(molt_batch* b, float* u, const double* dt, molt_sche
     }
     if (worst != MOLT_OK) molt::set_abi_error("an instance reached max_iter before the fixed-point tolerance");
     return worst;
+}
+
+molt_status molt_batch_set_schedule(molt_batch* b, int grid_rows, int grid_cols) {
+    if (!b || grid_rows < 0 || grid_cols < 0) return batch_fail(MOLT_ERR_ARG, "null batch or negative grid");
+    b->grid_rows = grid_rows;
+    b->grid_cols = grid_cols;
+    b->drop_graphs();
+    return MOLT_OK;
+}
+
+molt_status molt_batch_autotune(molt_batch* b, const double* dt, void* stream, double* ms_table, int* grid_rows,
+                                int* grid_cols) {
+    if (!b || !dt) return batch_fail(MOLT_ERR_ARG, "null batch or dt");
+    std::vector<double> tau(dt, dt + b->count);
+    for (int i = 0; i < b->count; ++i)
+        if (!(tau[i] > 0.0) || !std::isfinite(tau[i]))
+            return batch_fail(MOLT_ERR_ARG, "instance " + std::to_string(i) + ": dt must be finite and > 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    molt_status s = load_params(b, tau, st);
+    if (s != MOLT_OK) return s;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // candidate schedules: one block per work item, or persistent grids of 2, 4, 8 blocks per SM
+    const int caps[4] = {0, 2 * sms, 4 * sms, 8 * sms};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best = INFINITY;
+    int best_r = 0, best_c = 0;
+    // time one fixed-point iteration of every instance under each pair of schedules, from the same
+    // finite fields each time
+    for (int ir = 0; ir < 4 && e == cudaSuccess; ++ir) {
+        for (int ic = 0; ic < 4 && e == cudaSuccess; ++ic) {
+            b->grid_rows = caps[ir];
+            b->grid_cols = caps[ic];
+            float ms = 0.0f;
+            if ((e = lin(b, b->w, nullptr, 0.0, nullptr, 0.0, 0.05, st)) != cudaSuccess ||
+                (e = lin(b, b->Y, nullptr, 0.0, nullptr, 0.0, 0.05, st)) != cudaSuccess || loop_init(b, st) != cudaSuccess)
+                break;
+            for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = lin(b, b->f[k], nullptr, 0.0, nullptr, 0.0, 0.01 * k, st);
+            if (e != cudaSuccess || (e = iteration_any(b, st)) != cudaSuccess) break;   // warm-up
+            if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = iteration_any(b, st);
+            if (e != cudaSuccess || (e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+                (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+                break;
+            const double per = ms / 3.0;
+            if (ms_table) ms_table[4 * ir + ic] = per;
+            if (per < best) {
+                best = per;
+                best_r = caps[ir];
+                best_c = caps[ic];
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    b->grid_rows = best_r;
+    b->grid_cols = best_c;
+    b->drop_graphs();          // graphs captured the previous schedule
+    b->have_prev = false;      // the work fields were overwritten
+    if (e != cudaSuccess) return batch_fail(MOLT_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    if (grid_rows) *grid_rows = best_r;
+    if (grid_cols) *grid_cols = best_c;
+    return MOLT_OK;
 }
 
 }  // extern "C"

@@ -215,11 +215,13 @@ P pipe_build(int kind, const OpArgs<float>& a) {
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-// Shared memory of one block of the pipelined row kernel: the double-buffered staged fields of
-// its slice with a halo chunk on each side (padded to 8 chunks), and the auxiliary fields.
+// Shared memory of one block of the pipelined row kernels: the double-buffered staged fields and
+// the auxiliary fields of its line (C = 1), or of its slice with a halo chunk on each side padded
+// to 8 chunks (the cluster kernel, C = 2).
 template <class P>
 long long pipe_smem(int n, int C) {
     const long long nchl = n / 4 / C;
+    if (C == 1) return (2LL * P::NS + P::NA) * n * 4;
     return (2LL * P::NS * (nchl + 8) + static_cast<long long>(P::NA) * nchl) * 16;
 }
 
@@ -253,12 +255,12 @@ cudaError_t rows_pipe(const LineParams<float>& lp, const P& op, int nlines, unsi
     const int n = lp.n;
     const int TL = n / (16 * C);
     const size_t smem = static_cast<size_t>(pipe_smem<P>(n, C));
-    auto kern = rows_pipe_kernel<M, P, C>;
-    static int limit = smem_optin(kern);
-    if (limit < 0 || smem > static_cast<size_t>(limit)) return cudaErrorInvalidValue;
     const PackedStencil pw = packed_stencil(lp);
     const long long ld = n;
     if constexpr (C == 1) {
+        auto kern = rows_pipe_kernel<M, P>;
+        static int limit = smem_optin(kern);
+        if (limit < 0 || smem > static_cast<size_t>(limit)) return cudaErrorInvalidValue;
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -271,6 +273,9 @@ cudaError_t rows_pipe(const LineParams<float>& lp, const P& op, int nlines, unsi
         prof_end(prof, st);
         return cudaGetLastError();
     } else {
+        auto kern = rows_cluster_kernel<M, P, C>;
+        static int limit = smem_optin(kern);
+        if (limit < 0 || smem > static_cast<size_t>(limit)) return cudaErrorInvalidValue;
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -473,10 +478,15 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
     set_strides<T>(op, axis == 0 ? nx : 1, axis == 0 ? 1 : nx);
     if (launches) *launches += 1;
     if (axis == 0) {
+        if (a.variant >= LAUNCH_COLS_TMA) return cudaErrorInvalidValue;
         if constexpr (std::is_same<T, float>::value && !std::is_same<typename PipeOf<Op>::type, void>::value) {
             using P = typename PipeOf<Op>::type;
             const P pop = pipe_build<P>(kind, a);
-            const int C = pipe_cluster(pop, lp.n);
+            int C = a.variant == LAUNCH_ROWS_GENERAL ? 0 : pipe_cluster(pop, lp.n);
+            if (a.variant == LAUNCH_ROWS_ONE_BLOCK || a.variant == LAUNCH_ROWS_CLUSTER2) {
+                C = a.variant == LAUNCH_ROWS_ONE_BLOCK ? 1 : 2;
+                if (pipe_cluster(pop, lp.n) == 0 || !pipe_fits<P>(lp.n, C)) return cudaErrorInvalidValue;
+            }
             if (C > 0) {
                 switch (lp.M * 8 + C) {
                     case 2 * 8 + 1: return rows_pipe<2, P, 1>(lp, pop, nlines, red, st, prof, pk);
@@ -488,6 +498,7 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
                 }
             }
         }
+        if (a.variant == LAUNCH_ROWS_ONE_BLOCK || a.variant == LAUNCH_ROWS_CLUSTER2) return cudaErrorInvalidValue;
         if constexpr ((Op::kAxes & 1) != 0) {
             switch (lp.M) {
                 case 2: return rows<T, 2>(lp, op, nlines, red, st, prof, pk);
@@ -496,12 +507,20 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
             }
         }
     } else {
+        if (a.variant != LAUNCH_DEFAULT && a.variant < LAUNCH_COLS_TMA) return cudaErrorInvalidValue;
+        if (a.variant == LAUNCH_ROWS_TENSOR_CORE) return cudaErrorInvalidValue;
         if constexpr (std::is_same<T, float>::value && !std::is_same<typename ColPipeOf<Op>::type, void>::value) {
             using P = typename ColPipeOf<Op>::type;
             const P pop = col_pipe_build<P>(kind, a);
-            if (col_pipe_eligible(pop, lp.n, nlines)) {
+            const bool eligible = col_pipe_eligible(pop, lp.n, nlines);
+            if (!eligible && (a.variant == LAUNCH_COLS_TMA || a.variant == LAUNCH_COLS_CP_ASYNC))
+                return cudaErrorInvalidValue;
+            if (eligible && a.variant != LAUNCH_COLS_GENERAL) {
                 ColMaps maps;
-                if (cols_tma_enabled() && col_tma_maps(pop, nlines, lp.n, kColR + lp.M, &maps)) {
+                const bool want_tma = a.variant == LAUNCH_COLS_TMA || (a.variant == LAUNCH_DEFAULT && cols_tma_enabled());
+                const bool have_maps = want_tma && col_tma_maps(pop, nlines, lp.n, kColR + lp.M, &maps);
+                if (a.variant == LAUNCH_COLS_TMA && !have_maps) return cudaErrorInvalidValue;
+                if (have_maps) {
                     switch (lp.M) {
                         case 2: return cols_tma<2>(lp, maps, pop, nlines, cs, red, st, launches, prof, pk);
                         case 4: return cols_tma<4>(lp, maps, pop, nlines, cs, red, st, launches, prof, pk);
@@ -515,6 +534,7 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
                 }
             }
         }
+        if (a.variant == LAUNCH_COLS_TMA || a.variant == LAUNCH_COLS_CP_ASYNC) return cudaErrorInvalidValue;
         if constexpr ((Op::kAxes & 2) != 0) {
             switch (lp.M) {
                 case 2: return cols<T, 2>(lp, op, nlines, cs, red, st, launches, prof, pk);
@@ -714,6 +734,18 @@ cudaError_t lincomb(T* out, long long n, const T* x0, double c0, const T* x1, do
 }
 
 namespace detail {
+template <typename T>
+__global__ void fill_pattern_kernel(T* p, long long n, unsigned seed, double lo, double hi) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        unsigned long long z = static_cast<unsigned long long>(i) + 0x9E3779B97F4A7C15ull * (seed + 1ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        p[i] = static_cast<T>(lo + (hi - lo) * static_cast<double>(z >> 11) * (1.0 / 9007199254740992.0));
+    }
+}
+
 // One row j per blockIdx.y; the row weights a[k][j] are loaded once per thread.
 template <typename T>
 __global__ void add_separable_kernel(T* y, int nx, const Separable s) {
@@ -740,6 +772,12 @@ __global__ void cubic_kernel(T* out, long long n, const T* x, T a2, T a1) {
     }
 }
 }  // namespace detail
+
+template <typename T>
+cudaError_t fill_pattern(T* p, long long n, unsigned seed, double lo, double hi, cudaStream_t st) {
+    detail::fill_pattern_kernel<T><<<152 * 4, 256, 0, st>>>(p, n, seed, lo, hi);
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t add_separable(T* y, int nx, int ny, const Separable& s, cudaStream_t st, long long* launches) {
@@ -824,4 +862,5 @@ cudaError_t max_abs_diff(const T* a, const T* b, long long n, unsigned long long
                                               double*, cudaStream_t, long long*);                               \
     template cudaError_t molt::cubic<T>(T*, long long, const T*, double, double, cudaStream_t, long long*);    \
     template cudaError_t molt::add_separable<T>(T*, int, int, const molt::Separable&, cudaStream_t, long long*); \
+    template cudaError_t molt::fill_pattern<T>(T*, long long, unsigned, double, double, cudaStream_t);         \
     template cudaError_t molt::max_abs_diff<T>(const T*, const T*, long long, unsigned long long*, cudaStream_t);

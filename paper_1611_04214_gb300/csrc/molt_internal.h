@@ -110,7 +110,18 @@ struct OpArgs {
     T g2 = 0, g1 = 0, beta = 0, shift = 0;
     T vs = 0;       // vector CH: s = (c1 + c2)/tau
     int comp = 0;   // vector CH: component of the pass
+    int variant = 0;   // launch choice (Launch); 0 = the default for the line length and field count
 };
+
+// Kernel choices of one sweep, picked by the solver's autotuner (the values of molt_launch in
+// include/molt.h).  Rows: the pipelined kernel on one block per line or on a two-block cluster per
+// line, or the general row kernel; columns: TMA tiles, cp.async tiles or the general kernels.
+enum Launch { LAUNCH_DEFAULT = 0, LAUNCH_ROWS_ONE_BLOCK = 1, LAUNCH_ROWS_CLUSTER2 = 2, LAUNCH_ROWS_GENERAL = 3,
+              LAUNCH_COLS_TMA = 4, LAUNCH_COLS_CP_ASYNC = 5, LAUNCH_COLS_GENERAL = 6, LAUNCH_ROWS_TENSOR_CORE = 7 };
+
+// Fill n values with a hash of (seed, index) mapped uniformly to [lo, hi) (autotuner test data).
+template <typename T>
+cudaError_t fill_pattern(T* p, long long n, unsigned seed, double lo, double hi, cudaStream_t st);
 
 // Optional per-kernel event timing (diagnostic; off unless a solver enables it).
 // Slots: rows kernel of op k = k; column aggregate kernel = 8 + k; column carry = 16;
@@ -172,6 +183,14 @@ struct Separable {
 };
 template <typename T>
 cudaError_t add_separable(T* y, int nx, int ny, const Separable& s, cudaStream_t st, long long* launches);
+
+// Tensor-core row sweep of H_c on periodic FP32 lines (rows_tc.cu): workspace bytes, the line
+// lengths and line counts it takes, the one-time operand build for a line inverse, the sweep.
+size_t rows_tc_workspace_bytes();
+bool rows_tc_supported(int n, int nlines, int M);
+cudaError_t rows_tc_prepare(const LineParams<double>& lp, void* workspace, cudaStream_t st);
+cudaError_t rows_tc(const LineParams<double>& lp, const void* workspace, const float* in, float* out, int nlines,
+                    unsigned* status, cudaStream_t st);
 
 // out = x (x (x + a2) + a1), n elements (the pointwise cubic f of Eq. CahnHilliard_v).
 template <typename T>

@@ -25,6 +25,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -163,6 +164,8 @@ struct molt_solver {
     double dt_adapt_prev = 0.0;    // and that step's size
     bool vch_have_prev = false;    // vector CH BDF2: previous level held
     double vch_dt_prev = 0.0;
+    bool vch_adapt_have_prev = false;   // vector BE-BDF2 estimate: state before the last accepted step
+    double vch_adapt_dt_prev = 0.0;     // and that step's size
     virtual ~molt_solver() { prof.release(); }
     virtual molt_status step(void* u, double dt, int scheme, cudaStream_t st, molt_step_info* info) = 0;
     virtual molt_status run_host(void* u_host, double dt, int scheme, int nsteps, cudaStream_t st,
@@ -172,12 +175,33 @@ struct molt_solver {
                                  molt_adaptive_info* info) = 0;
     virtual molt_status vch_step(void* u1, void* u2, double dt, int scheme, cudaStream_t st,
                                  molt_step_info* info) = 0;
+    virtual molt_status vch_adaptive(void* u1, void* u2, double dt, const molt_adaptive& a, cudaStream_t st,
+                                     molt_adaptive_info* info) = 0;
     virtual molt_status apply(int axis, double c, const void* in, void* out, cudaStream_t st) = 0;
+    virtual molt_status apply_tc(double c, const void* in, void* out, cudaStream_t st) = 0;
+    virtual molt_status autotune(cudaStream_t st, molt_tuning* out, int capacity, int* nout) = 0;
     virtual molt_status init() = 0;
     virtual void drop_graphs() = 0;
 };
 
 namespace {
+
+// Step-size control of Algorithm 1 (Sec. 5), with r = eta / lte_tol and q = N_it / N_maxit.
+// A step is accepted when r <= 1 and q < 1.  The next size is dt times a factor: the LTE proposal
+// theta / sqrt(r), capped at gamma while q < 0.7 and at 1 while q < 1 for an accepted step; a
+// rejected step retries with dt / gamma when the LTE was met (so the iteration hit its cap) or
+// r > 2, and with the LTE proposal for 1 < r <= 2.  The result is clipped to [dt_min, dt_max].
+// Returns whether the step is accepted.
+bool step_size_rule(double eta, int n_it, double dt, const molt_adaptive& a, double* next, int max_iter) {
+    const double r = eta / a.lte_tol, q = static_cast<double>(n_it) / max_iter;
+    const double proposal = eta == 0.0 ? INFINITY : a.theta / std::sqrt(r);
+    const bool accept = r <= 1.0 && q < 1.0;
+    double factor;
+    if (accept) factor = std::min(proposal, q < 0.7 ? a.gamma : 1.0);
+    else factor = (r <= 1.0 || r > 2.0) ? 1.0 / a.gamma : proposal;
+    *next = std::min(std::max(dt * factor, a.dt_min), a.dt_max);
+    return accept;
+}
 
 template <typename T>
 struct Solver final : molt_solver {
@@ -283,16 +307,75 @@ struct Solver final : molt_solver {
         return true;
     }
 
+    // Launch choice of each (pass kind, axis), set by the autotuner (molt_autotune); 0 = default.
+    int tune[10][2] = {};
+
     cudaError_t sweep(int axis, const molt::LineParams<T>& lp, int kind, const molt::OpArgs<T>& a,
                       cudaStream_t st) {
+        if (a.variant == 0 && kind >= 0 && kind < 10 && tune[kind][axis] != 0 &&
+            tune[kind][axis] != molt::LAUNCH_ROWS_TENSOR_CORE) {
+            molt::OpArgs<T> b = a;
+            b.variant = tune[kind][axis];
+            return molt::sweep<T>(axis, lp, kind, b, g.nx, g.ny, &cs, red, st, &launches, &prof);
+        }
         return molt::sweep<T>(axis, lp, kind, a, g.nx, g.ny, &cs, red, st, &launches, &prof);
     }
 
-    cudaError_t copy_sweep(int axis, const molt::LineParams<T>& lp, const T* in, T* out, cudaStream_t st) {
+    // One H_c sweep; c (when given) lets the tuned tensor-core row sweep build its operands.
+    cudaError_t copy_sweep(int axis, const molt::LineParams<T>& lp, const T* in, T* out, cudaStream_t st,
+                           double c = 0.0) {
+        if (axis == 0 && c > 0.0 && tune[molt::OP_COPY][0] == molt::LAUNCH_ROWS_TENSOR_CORE && in != out) {
+            const cudaError_t e = tc_sweep(c, in, out, st);
+            if (e != cudaErrorNotReady) return e;   // not ready during stream capture: the scan kernel
+        }
         molt::OpArgs<T> a;
         a.in0 = in;
         a.out0 = out;
         return sweep(axis, lp, molt::OP_COPY, a, st);
+    }
+
+    // Tensor-core row sweep with operands cached per c (four slots); the operands are built (host
+    // FP64, one synchronizing upload) outside stream capture only.
+    struct TcSlot {
+        double c = 0.0;
+        void* work = nullptr;
+    };
+    TcSlot tc_slots[4];
+    int tc_next = 0;
+    cudaError_t tc_sweep(double c, const T* in, T* out, cudaStream_t st) {
+        if constexpr (!std::is_same<T, float>::value) {
+            return cudaErrorInvalidValue;
+        } else {
+            const double h = grid_h(g.nx, g.Lx, bc);
+            molt::LineParams<double> lpd;
+            const char* err = nullptr;
+            if (!molt::build_line_params(c, h, g.nx, p.quad_order, bc, &lpd, &err)) return cudaErrorInvalidValue;
+            TcSlot* slot = nullptr;
+            for (TcSlot& t : tc_slots)
+                if (t.work && t.c == c) slot = &t;
+            if (!slot) {
+                cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+                if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+                    cudaGetLastError();
+                    return cudaErrorNotReady;
+                }
+                slot = &tc_slots[tc_next];
+                tc_next = (tc_next + 1) % 4;
+                if (!slot->work) {
+                    if (cudaMalloc(&slot->work, molt::rows_tc_workspace_bytes()) != cudaSuccess)
+                        return cudaErrorMemoryAllocation;
+                    allocs.push_back(slot->work);
+                }
+                slot->c = c;
+                const cudaError_t e = molt::rows_tc_prepare(lpd, slot->work, st);
+                if (e != cudaSuccess) {
+                    slot->c = 0.0;
+                    return e;
+                }
+            }
+            launches += 1;
+            return molt::rows_tc(lpd, slot->work, in, out, g.ny, wait_status, st);
+        }
     }
 
     cudaError_t lin(T* out, const T* x0, double c0, const T* x1 = nullptr, double c1 = 0, const T* x2 = nullptr,
@@ -305,11 +388,11 @@ struct Solver final : molt_solver {
     cudaError_t mm_inv(double c, const T* in, T* out, cudaStream_t st) {
         molt::LineParams<T> lx, ly;
         if (!line_params(c, 0, &lx)) return cudaErrorInvalidValue;
-        if (g.dim == 1) return copy_sweep(0, lx, in, out, st);
+        if (g.dim == 1) return copy_sweep(0, lx, in, out, st, c);
         if (!line_params(c, 1, &ly)) return cudaErrorInvalidValue;
         cudaError_t e = copy_sweep(1, ly, in, f1, st);
         if (e != cudaSuccess) return e;
-        return copy_sweep(0, lx, f1, out, st);
+        return copy_sweep(0, lx, f1, out, st, c);
     }
 
     // out = E_c in with E = M^{-1} - I + D_x D_y, i.e. 2 H_x H_y - H_x - H_y in 2D and H - I in 1D
@@ -319,13 +402,13 @@ struct Solver final : molt_solver {
         if (!line_params(c, 0, &lx)) return cudaErrorInvalidValue;
         cudaError_t e;
         if (g.dim == 1) {
-            if ((e = copy_sweep(0, lx, in, f1, st)) != cudaSuccess) return e;
+            if ((e = copy_sweep(0, lx, in, f1, st, c)) != cudaSuccess) return e;
             return lin(out, f1, 1.0, in, -1.0, nullptr, 0, nullptr, 0, 0, st);
         }
         if (!line_params(c, 1, &ly)) return cudaErrorInvalidValue;
         if ((e = copy_sweep(1, ly, in, f1, st)) != cudaSuccess) return e;      // H_y
-        if ((e = copy_sweep(0, lx, f1, f2, st)) != cudaSuccess) return e;      // H_x H_y
-        if ((e = copy_sweep(0, lx, in, f3, st)) != cudaSuccess) return e;      // H_x
+        if ((e = copy_sweep(0, lx, f1, f2, st, c)) != cudaSuccess) return e;   // H_x H_y
+        if ((e = copy_sweep(0, lx, in, f3, st, c)) != cudaSuccess) return e;   // H_x
         return lin(out, f2, 2.0, f3, -1.0, f1, -1.0, nullptr, 0, 0, st);
     }
 
@@ -967,26 +1050,8 @@ struct Solver final : molt_solver {
             double diff;
             std::memcpy(&diff, &red_host[0], sizeof(double));
             const double eta = (sdc || bdf) ? diff : 0.5 * diff;   // the factor 1/2 is Richardson's
-            const double ratio = eta == 0.0 ? INFINITY : std::sqrt(a.lte_tol / eta);
-            bool ok;
             double next;
-            if (eta <= a.lte_tol) {
-                const double frac = static_cast<double>(n_it) / p.max_iter;
-                if (frac < 0.7) {
-                    ok = true;
-                    next = dt * std::min(a.theta * ratio, a.gamma);
-                } else if (frac < 1.0) {
-                    ok = true;
-                    next = dt * std::min(a.theta * ratio, 1.0);
-                } else {
-                    ok = false;
-                    next = dt / a.gamma;
-                }
-            } else {
-                ok = false;
-                next = eta / a.lte_tol > 2.0 ? dt / a.gamma : dt * a.theta * ratio;
-            }
-            next = std::min(std::max(next, a.dt_min), a.dt_max);
+            const bool ok = step_size_rule(eta, n_it, dt, a, &next, p.max_iter);
             if (ok) {
                 if (want_bdf && (e = lin(adapt_prev, u, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
                     return cuda_fail(e, "adaptive history");
@@ -1063,12 +1128,144 @@ struct Solver final : molt_solver {
         std::swap(vp1, wn);   // v^n becomes the previous level
         std::swap(vp2, vn2);
         vch_have_prev = true;
+        vch_adapt_have_prev = false;
         vch_dt_prev = dt;
         if ((e = lin(u1, w, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, zx, st)) != cudaSuccess ||
             (e = lin(u2, vw2, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, zy, st)) != cudaSuccess)
             return cuda_fail(e, "vector CH store");
         if (info) info->status = ms;
         return ms;
+    }
+
+    // Vector CH: one stage solve v - tau F(v) = a_n v^n + a_p v^{n-1} for both components, from the
+    // state (u1, u2) (also the first guess) and the optional earlier state (p1, p2), all in the
+    // physical variable u; the result goes to (o1, o2), which may alias (u1, u2).
+    T *va1 = nullptr, *va2 = nullptr, *vb1 = nullptr, *vb2 = nullptr, *vq1 = nullptr, *vq2 = nullptr;
+    molt_status vch_stage_from(const T* u1, const T* u2, double an, const T* p1, const T* p2, double ap, double tau,
+                               T* o1, T* o2, cudaStream_t st, int* iters) {
+        const double zx = -0.5, zy = -0.86602540378443864676;
+        cudaError_t e;
+        if ((e = lin(w, u1, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, -zx, st)) != cudaSuccess ||
+            (e = lin(vw2, u2, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, -zy, st)) != cudaSuccess ||
+            (e = lin(r, u1, an, p1, p1 ? ap : 0.0, nullptr, 0, nullptr, 0, -zx * (an + (p1 ? ap : 0.0)), st)) !=
+                cudaSuccess ||
+            (e = lin(vr2, u2, an, p2, p2 ? ap : 0.0, nullptr, 0, nullptr, 0, -zy * (an + (p2 ? ap : 0.0)), st)) !=
+                cudaSuccess)
+            return cuda_fail(e, "vector stage load");
+        Passes ps;
+        double c_in, c_out;
+        if (!make_vch_passes(tau, &ps, &c_in, &c_out)) return MOLT_ERR_ARG;
+        if ((e = mm_inv(c_in, r, f2, st)) != cudaSuccess || (e = mm_inv(c_out, f2, Y, st)) != cudaSuccess ||
+            (e = mm_inv(c_in, vr2, f2, st)) != cudaSuccess || (e = mm_inv(c_out, f2, vY2, st)) != cudaSuccess)
+            return cuda_fail(e, "vector stage rhs inverse");
+        double res, tu;
+        molt_status ms = stage(tau, nullptr, st, iters, &res, &tu, true, &ps);
+        if (ms != MOLT_OK && ms != MOLT_ERR_NOT_CONVERGED) return ms;
+        if ((e = lin(o1, w, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, zx, st)) != cudaSuccess ||
+            (e = lin(o2, vw2, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, zy, st)) != cudaSuccess)
+            return cuda_fail(e, "vector stage store");
+        return MOLT_OK;
+    }
+
+    double max_diff(const T* a, const T* b, cudaStream_t st, cudaError_t* err) {
+        double v = 0.0;
+        if ((*err = molt::max_abs_diff<T>(a, b, static_cast<long long>(count()), red, st)) != cudaSuccess ||
+            (*err = cudaMemcpyAsync(red_host, red, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess ||
+            (*err = cudaStreamSynchronize(st)) != cudaSuccess)
+            return 0.0;
+        std::memcpy(&v, &red_host[0], sizeof(double));
+        return v;
+    }
+
+    // Algorithm 1 (Sec. 5) for the vector model, as Sec. 6.2.2 runs it: the Richardson estimate of
+    // BE, or BE-BDF2 with the variable-step BDF2 of the scalar controller; without history (the
+    // first step) BE-BDF2 takes the Richardson estimate (the vector model has no SDC2 here).
+    molt_status vch_adaptive(void* u1v, void* u2v, double dt, const molt_adaptive& a, cudaStream_t st,
+                             molt_adaptive_info* out) override {
+        T* u1 = static_cast<T*>(u1v);
+        T* u2 = static_cast<T*>(u2v);
+        if (a.estimator != MOLT_LTE_RICHARDSON && a.estimator != MOLT_LTE_BDF2)
+            return fail(MOLT_ERR_UNSUPPORTED, "vector adaptive steps support the Richardson and BE-BDF2 estimates");
+        if (g.dim == 2 && g.nx > molt::max_row_length<T>(2))
+            return fail(MOLT_ERR_UNSUPPORTED, "2D steps need x lines within the two-field row kernels' length");
+        if (!vw2) {
+            T** fields[] = {&vw2, &vY2, &vn2, &vp2, &vr2, &vg4, &vg5, &vg6, &vp1};
+            for (T** f : fields)
+                if (!alloc(f, count())) return fail(MOLT_ERR_OOM, "vector CH workspace");
+        }
+        if (!va1) {
+            T** fields[] = {&va1, &va2, &vb1, &vb2, &vq1, &vq2};
+            for (T** f : fields)
+                if (!alloc(f, count())) return fail(MOLT_ERR_OOM, "vector adaptive workspace");
+        }
+        const bool want_bdf = a.estimator == MOLT_LTE_BDF2;
+        cudaError_t e = cudaSuccess;
+        int rejections = 0;
+        for (;;) {
+            const bool bdf = want_bdf && vch_adapt_have_prev;
+            int n_it = 0, it;
+            molt_status ms;
+            double diff;
+            if (bdf) {
+                // BE into (va), variable-step BDF2 into (vb) from the same start
+                if ((ms = vch_stage_from(u1, u2, 1.0, nullptr, nullptr, 0.0, dt, va1, va2, st, &it)) != MOLT_OK &&
+                    ms != MOLT_ERR_NOT_CONVERGED)
+                    return ms;
+                n_it = it;
+                const double om = dt / vch_adapt_dt_prev;
+                const double tau = dt * (1.0 + om) / (1.0 + 2.0 * om);
+                const double an = (1.0 + om) * (1.0 + om) / (1.0 + 2.0 * om), ap = -om * om / (1.0 + 2.0 * om);
+                if ((ms = vch_stage_from(u1, u2, an, vq1, vq2, ap, tau, vb1, vb2, st, &it)) != MOLT_OK &&
+                    ms != MOLT_ERR_NOT_CONVERGED)
+                    return ms;
+                n_it = std::max(n_it, it);
+                diff = std::max(max_diff(vb1, va1, st, &e), e == cudaSuccess ? max_diff(vb2, va2, st, &e) : 0.0);
+            } else {
+                // one BE step into (va), two half steps into (vb)
+                if ((ms = vch_stage_from(u1, u2, 1.0, nullptr, nullptr, 0.0, dt, va1, va2, st, &it)) != MOLT_OK &&
+                    ms != MOLT_ERR_NOT_CONVERGED)
+                    return ms;
+                n_it = it;
+                if ((ms = vch_stage_from(u1, u2, 1.0, nullptr, nullptr, 0.0, 0.5 * dt, vb1, vb2, st, &it)) != MOLT_OK &&
+                    ms != MOLT_ERR_NOT_CONVERGED)
+                    return ms;
+                n_it = std::max(n_it, it);
+                if ((ms = vch_stage_from(vb1, vb2, 1.0, nullptr, nullptr, 0.0, 0.5 * dt, vb1, vb2, st, &it)) !=
+                        MOLT_OK &&
+                    ms != MOLT_ERR_NOT_CONVERGED)
+                    return ms;
+                n_it = std::max(n_it, it);
+                diff = std::max(max_diff(va1, vb1, st, &e), e == cudaSuccess ? max_diff(va2, vb2, st, &e) : 0.0);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "vector adaptive estimate");
+            const double eta = bdf ? diff : 0.5 * diff;   // the factor 1/2 is Richardson's
+            double next;
+            const bool ok = step_size_rule(eta, n_it, dt, a, &next, p.max_iter);
+            if (ok) {
+                if (want_bdf && ((e = lin(vq1, u1, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess ||
+                                 (e = lin(vq2, u2, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess))
+                    return cuda_fail(e, "vector adaptive history");
+                if ((e = lin(u1, vb1, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess ||
+                    (e = lin(u2, vb2, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0, st)) != cudaSuccess)
+                    return cuda_fail(e, "vector adaptive store");
+                vch_adapt_have_prev = want_bdf;
+                vch_adapt_dt_prev = dt;
+                vch_have_prev = false;
+                if (out) {
+                    out->dt_used = dt;
+                    out->dt_next = next;
+                    out->eta = eta;
+                    out->rejections = rejections;
+                    out->max_iters = n_it;
+                }
+                return MOLT_OK;
+            }
+            ++rejections;
+            if (dt <= a.dt_min)
+                return fail(MOLT_ERR_NOT_CONVERGED, "adaptive step: dt_min reached without meeting the LTE tolerance");
+            dt = next;
+        }
     }
 
     molt_status apply(int axis, double c, const void* in, void* out, cudaStream_t st) override {
@@ -1081,6 +1278,138 @@ struct Solver final : molt_solver {
         cudaError_t e = copy_sweep(axis, lp, static_cast<const T*>(in), static_cast<T*>(out), st);
         if (e != cudaSuccess) return cuda_fail(e, "sweep");
         return MOLT_OK;
+    }
+
+    molt_status apply_tc(double c, const void* in, void* out, cudaStream_t st) override {
+        if (!fp32() || bc != molt::BC_PERIODIC || !molt::rows_tc_supported(g.nx, g.ny, p.quad_order))
+            return fail(MOLT_ERR_UNSUPPORTED, "tensor-core row sweeps need FP32, periodic lines of 1024..8192 nodes "
+                                              "(a power of two) and a multiple of 8192/nx lines");
+        if (!(c > 0.0) || !std::isfinite(c)) return fail(MOLT_ERR_ARG, "c must be positive and finite");
+        if (in == out) return fail(MOLT_ERR_ARG, "tensor-core row sweeps cannot run in place");
+        const cudaError_t e = tc_sweep(c, static_cast<const T*>(in), static_cast<T*>(out), st);
+        if (e == cudaErrorNotReady) return fail(MOLT_ERR_UNSUPPORTED, "operands are not built during stream capture");
+        if (e != cudaSuccess) return cuda_fail(e, "tensor-core row sweep");
+        return MOLT_OK;
+    }
+
+    // The autotuner (molt_autotune): times every available launch of each sweep of a step on this
+    // grid and keeps the fastest.  Test data: hash-uniform fields in [-0.5, 0.5).
+    molt_status autotune(cudaStream_t st, molt_tuning* out, int capacity, int* nout) override {
+        *nout = 0;
+        if (!fp32()) return MOLT_OK;   // FP64 sweeps have one kernel family
+        cudaError_t e;
+        T* fl[7] = {w, f1, f2, f3, f4, f5, f6};
+        for (int k = 0; k < 7; ++k)
+            if ((e = molt::fill_pattern<T>(fl[k], static_cast<long long>(count()), 11u + k, -0.5, 0.5, st)) !=
+                cudaSuccess)
+                return cuda_fail(e, "autotune data");
+        if ((e = molt::fill_pattern<T>(Y, static_cast<long long>(count()), 7u, -0.5, 0.5, st)) != cudaSuccess)
+            return cuda_fail(e, "autotune data");
+        const double hx = grid_h(g.nx, g.Lx, bc), hy = g.dim == 2 ? grid_h(g.ny, g.Ly, bc) : hx;
+        const double cx = (hx / 0.3) * (hx / 0.3), cy = (hy / 0.3) * (hy / 0.3);
+        molt::LineParams<T> lx, ly;
+        if (!line_params(cx, 0, &lx) || (g.dim == 2 && !line_params(cy, 1, &ly))) return MOLT_ERR_ARG;
+        const StageParams sp = stage_params(1e-3, p.eps);
+        Passes ps;
+        if (!make_passes(sp, &ps)) return MOLT_ERR_ARG;
+        struct Entry { int pass, kind, axis; };
+        static const Entry k2d[] = {{0, molt::OP_COPY, 0}, {0, molt::OP_COPY, 1}, {1, molt::OP_P1, 1},
+                                    {2, molt::OP_P2, 0},   {3, molt::OP_P3, 1},   {4, molt::OP_P4, 0}};
+        static const Entry k1d[] = {{0, molt::OP_COPY, 0}, {5, molt::OP_1A, 0}, {6, molt::OP_1B, 0}};
+        const Entry* ebeg = g.dim == 2 ? k2d : k1d;
+        const Entry* eend = g.dim == 2 ? k2d + 6 : k1d + 3;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            if (e0) cudaEventDestroy(e0);
+            return fail(MOLT_ERR_CUDA, "autotune events");
+        }
+        molt_status result = MOLT_OK;
+        for (const Entry* ep = ebeg; ep != eend; ++ep) {
+            const Entry& en = *ep;
+            molt::OpArgs<T> a;
+            a.g2 = ps.g2;
+            a.g1 = ps.g1;
+            a.beta = ps.beta;
+            a.shift = ps.s;
+            switch (en.kind) {
+                case molt::OP_COPY: a.in0 = f1; a.out0 = f2; break;
+                case molt::OP_P1: a.in0 = w; a.out0 = f1; a.out1 = f2; break;
+                case molt::OP_P2: a.in0 = w; a.in1 = f1; a.in2 = f2; a.out0 = f3; a.out1 = f4; break;
+                case molt::OP_P3: a.in0 = f3; a.in1 = f4; a.out0 = f5; a.out1 = f6; break;
+                case molt::OP_P4: a.in0 = f5; a.in1 = f6; a.in2 = f4; a.in3 = Y; a.out0 = f1; break;
+                case molt::OP_1A: a.in0 = w; a.out0 = f1; break;
+                default: a.in0 = f1; a.in1 = Y; a.out0 = f2; break;   // OP_1B
+            }
+            const molt::LineParams<T>& lp = en.axis == 0 ? lx : ly;
+            std::vector<int> cand = en.axis == 0
+                ? std::vector<int>{molt::LAUNCH_ROWS_ONE_BLOCK, molt::LAUNCH_ROWS_CLUSTER2, molt::LAUNCH_ROWS_GENERAL}
+                : std::vector<int>{molt::LAUNCH_COLS_TMA, molt::LAUNCH_COLS_CP_ASYNC, molt::LAUNCH_COLS_GENERAL};
+            const bool tc_ok = en.kind == molt::OP_COPY && en.axis == 0 && bc == molt::BC_PERIODIC &&
+                               molt::rows_tc_supported(g.nx, g.ny, p.quad_order);
+            if (tc_ok) cand.push_back(molt::LAUNCH_ROWS_TENSOR_CORE);
+            molt_tuning rec{};
+            rec.pass = en.pass;
+            rec.axis = en.axis;
+            rec.candidates = static_cast<int>(cand.size());
+            double best = INFINITY;
+            int chosen = 0;
+            for (size_t ci = 0; ci < cand.size(); ++ci) {
+                rec.launch[ci] = cand[ci];
+                rec.ms[ci] = -1.0;
+                auto run = [&]() -> cudaError_t {
+                    if (cand[ci] == molt::LAUNCH_ROWS_TENSOR_CORE) return tc_sweep(cx, a.in0, a.out0, st);
+                    molt::OpArgs<T> b = a;
+                    b.variant = cand[ci];
+                    return molt::sweep<T>(en.axis, lp, en.kind, b, g.nx, g.ny, &cs, red, st, nullptr, nullptr);
+                };
+                if (run() != cudaSuccess) {            // not available for this grid
+                    cudaGetLastError();
+                    continue;
+                }
+                float ms = 0.0f;
+                constexpr int reps = 5;
+                if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+                for (int r = 0; r < reps && e == cudaSuccess; ++r) e = run();
+                if (e != cudaSuccess || (e = cudaEventRecord(e1, st)) != cudaSuccess ||
+                    (e = cudaEventSynchronize(e1)) != cudaSuccess || (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+                    break;
+                double per = static_cast<double>(ms) / reps;
+                if (cand[ci] == molt::LAUNCH_ROWS_TENSOR_CORE) {
+                    // kept only where it is as accurate as the FP32 sweep bar: 1e-6 of max|H f|
+                    molt::OpArgs<T> b = a;
+                    b.out0 = f3;
+                    double dref = 0.0, dmax = 0.0;
+                    if ((e = molt::sweep<T>(0, lp, molt::OP_COPY, b, g.nx, g.ny, &cs, red, st, nullptr, nullptr)) !=
+                            cudaSuccess ||
+                        (e = molt::fill_pattern<T>(f5, static_cast<long long>(count()), 0u, 0.0, 0.0, st)) != cudaSuccess)
+                        break;
+                    dmax = max_diff(f2, f3, st, &e);
+                    if (e == cudaSuccess) dref = max_diff(f3, f5, st, &e);
+                    if (e != cudaSuccess) break;
+                    rec.tc_rel_diff = dmax / dref;
+                    if (!(dmax <= 1e-6 * dref)) per = -per;   // recorded, not eligible
+                }
+                rec.ms[ci] = per;
+                if (per > 0.0 && per < best) {
+                    best = per;
+                    chosen = cand[ci];
+                }
+            }
+            if (e != cudaSuccess) {
+                result = cuda_fail(e, "autotune");
+                break;
+            }
+            rec.chosen = chosen;
+            tune[en.kind][en.axis] = chosen;
+            if (*nout < capacity && out) out[*nout] = rec;
+            ++*nout;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaMemsetAsync(red, 0, 2 * sizeof(unsigned long long), st);
+        drop_graphs();   // graphs captured the previous choices
+        have_prev = have_prev2 = have_sdc = have_adapt_prev = vch_have_prev = vch_adapt_have_prev = false;
+        return result;
     }
 };
 
@@ -1165,6 +1494,7 @@ molt_status molt_set_params(molt_solver* s, const molt_params* p) {
     s->have_sdc = false;
     s->have_adapt_prev = false;
     s->vch_have_prev = false;
+    s->vch_adapt_have_prev = false;
     s->drop_graphs();
     return MOLT_OK;
 }
@@ -1179,6 +1509,7 @@ molt_status molt_set_bc(molt_solver* s, int bc) {
     s->have_sdc = false;
     s->have_adapt_prev = false;
     s->vch_have_prev = false;
+    s->vch_adapt_have_prev = false;
     s->drop_graphs();
     return MOLT_OK;
 }
@@ -1199,6 +1530,7 @@ molt_status molt_reset_history(molt_solver* s) {
     s->have_sdc = false;
     s->have_adapt_prev = false;
     s->vch_have_prev = false;
+    s->vch_adapt_have_prev = false;
     return MOLT_OK;
 }
 
@@ -1237,6 +1569,33 @@ molt_status molt_helmholtz_apply(molt_solver* s, int axis, double c, const void*
     if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
     if (!in_dev || !out_dev) { s->err = "null field"; return MOLT_ERR_ARG; }
     return s->apply(axis, c, in_dev, out_dev, static_cast<cudaStream_t>(stream));
+}
+
+molt_status molt_vch_step_adaptive(molt_solver* s, void* u1, void* u2, double dt, const molt_adaptive* a,
+                                   void* stream, molt_adaptive_info* info) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    if (!u1 || !u2 || u1 == u2 || !a) { s->err = "null or equal fields, or null parameters"; return MOLT_ERR_ARG; }
+    if (!(dt > 0.0) || !(a->lte_tol > 0.0) || !(a->dt_min > 0.0) || a->dt_max < a->dt_min || !(a->theta > 0.0) ||
+        !(a->gamma > 1.0)) {
+        s->err = "bad adaptive parameters";
+        return MOLT_ERR_ARG;
+    }
+    return s->vch_adaptive(u1, u2, std::min(std::max(dt, a->dt_min), a->dt_max), *a, static_cast<cudaStream_t>(stream),
+                           info);
+}
+
+molt_status molt_autotune(molt_solver* s, void* stream, molt_tuning* entries, int capacity, int* count) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    int n = 0;
+    const molt_status st = s->autotune(static_cast<cudaStream_t>(stream), entries, capacity < 0 ? 0 : capacity, &n);
+    if (count) *count = n;
+    return st;
+}
+
+molt_status molt_helmholtz_rows_tc(molt_solver* s, double c, const void* in_dev, void* out_dev, void* stream) {
+    if (!s) return set_global_error(MOLT_ERR_ARG, "null solver");
+    if (!in_dev || !out_dev) { s->err = "null field"; return MOLT_ERR_ARG; }
+    return s->apply_tc(c, in_dev, out_dev, static_cast<cudaStream_t>(stream));
 }
 
 molt_status molt_quadrature_weights(double nu, int M, const int* offsets, int side, double* weights) {

@@ -304,8 +304,414 @@ rows_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, i
 }
 
 // =========================================================================================
-// Rows, FP32, persistent and pipelined.  A line of n nodes is split over a cluster of C blocks
-// (C = 1 or 2; the cluster's blocks are consecutive in x): block rank r owns the slice
+// Rows, FP32, persistent and pipelined.  A block owns one line per iteration with K = 16
+// positions per thread (TL = n / 16 threads) and loops over lines blockIdx.x, +gridDim.x, ...
+// The staged input fields of the next line arrive by cp.async (16-byte chunks, swizzled) into
+// the other half of a double buffer while the current line is swept; the epilogue's auxiliary
+// fields of the current line are fetched the same way during the sweep.  Window reads and the
+// epilogue work on 128-bit chunks; outputs are stored from registers.
+// Requires n % 512 == 0, 1024 <= n <= 8192, 16-byte aligned rows, and the staged lines in
+// shared memory.
+// =========================================================================================
+__device__ __forceinline__ float comp4(const float4& v, int e) {
+    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void set4(float4& v, int e, float x) {
+    if (e == 0) v.x = x;
+    else if (e == 1) v.y = x;
+    else if (e == 2) v.z = x;
+    else v.w = x;
+}
+
+template <int M, class Op>
+__global__ void __launch_bounds__(512, 1)
+rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_constant__ PackedStencil pw, const Op op,
+                 int nlines, long long ld, unsigned long long* red_slots) {
+    using T = float;
+    constexpr int K = 16, V = 4, KC = K / V, H = M / 2, WC = KC + 2;
+    constexpr int NS = Op::NS, NA = Op::NA, NF = Op::NF, NO = Op::NO;
+    // two swept fields (pass 2): their stencil and recurrence steps run as fma.rn.f32x2 pairs
+    constexpr bool kPack = NF == 2;
+    using PL = Lanes<2>;
+    extern __shared__ __align__(128) unsigned char sm_rows_pipe[];
+    float4* sm = reinterpret_cast<float4*>(sm_rows_pipe);
+    __shared__ T s_scan[16][2 + 2 * NF];   // per-warp segments: D_f, D_b, A_f[NF], A_b[NF]
+    __shared__ T s_bnd[2 * NF];            // carries / B values of the line (FP64 solve)
+
+    const int n = lp.n;
+    const int nch = n / V;
+    const int TL = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wpl = TL >> 5;
+    const bool periodic = lp.bc == BC_PERIODIC;
+    const T d = lp.d;
+    const int start = tid * K;
+    T D = T(1);
+#pragma unroll
+    for (int k = 0; k < K; ++k) D *= d;
+    const T pl = dev_exp(-lp.nu * T(periodic ? start : start - 1));
+    const T pr = dev_exp(-lp.nu * T(periodic ? n - start - K : n - start - K - 1));
+
+    auto stage_buf = [&](int sb, int f) { return sm + (static_cast<size_t>(sb) * NS + f) * nch; };
+    auto aux_buf = [&](int f) { return sm + (static_cast<size_t>(2 * NS) + f) * nch; };
+    auto issue_staged = [&](int ln, int sb) {
+#pragma unroll
+        for (int f = 0; f < NS; ++f) {
+            const float4* src = reinterpret_cast<const float4*>(op.s[f] + ln * ld);
+            float4* dst = stage_buf(sb, f);
+            for (int c = tid; c < nch; c += TL) cp_async16(dst + swz(c), src + c);
+        }
+    };
+
+    RedAcc<T> red{T(0), T(0)};
+    int line = blockIdx.x;
+    if (line < nlines) issue_staged(line, 0);
+    cp_async_commit();
+    for (int it = 0; line < nlines; ++it, line += gridDim.x) {
+        const int sb = it & 1;
+        cp_async_wait<0>();          // this line's staged fields (the only group in flight)
+        __syncthreads();             // ... visible to all; every warp is done with the last line
+        // auxiliary fields of this line, then the staged fields of the next line
+#pragma unroll
+        for (int f = 0; f < NA; ++f) {
+            const float4* src = reinterpret_cast<const float4*>(op.a[f] + line * ld);
+            float4* dst = aux_buf(f);
+            for (int c = tid; c < nch; c += TL) cp_async16(dst + swz(c), src + c);
+        }
+        cp_async_commit();
+        const int next = line + gridDim.x;
+        if (next < nlines) issue_staged(next, sb ^ 1);
+        cp_async_commit();
+
+        // ---- window (prologue applied) from chunks start/V - 1 .. start/V + KC ----
+        T fw[NF][WC * V];
+#pragma unroll
+        for (int j = 0; j < WC; ++j) {
+            int c = start / V - 1 + j;
+            if (periodic) c = c < 0 ? c + nch : (c >= nch ? c - nch : c);
+            else c = c < 0 ? 0 : (c >= nch ? nch - 1 : c);
+            float4 raw[NS];
+#pragma unroll
+            for (int f = 0; f < NS; ++f) raw[f] = stage_buf(sb, f)[swz(c)];
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                T sv[NS], fv[NF];
+#pragma unroll
+                for (int f = 0; f < NS; ++f) sv[f] = comp4(raw[f], e);
+                op.prologue(sv, fv);
+#pragma unroll
+                for (int q = 0; q < NF; ++q) fw[q][j * V + e] = fv[q];
+            }
+        }
+        T JL[kPack ? 1 : NF][K], JR[kPack ? 1 : NF][K], aL[NF], aR[NF];
+        unsigned long long JL2[kPack ? K : 1], JR2[kPack ? K : 1];   // packed J (then outputs)
+        auto at_field = [&](int p, int q) {
+            T sv[NS], fv[NF];
+#pragma unroll
+            for (int f = 0; f < NS; ++f) sv[f] = reinterpret_cast<const T*>(stage_buf(sb, f) + swz(p / V))[p % V];
+            op.prologue(sv, fv);
+            return fv[q];
+        };
+        // J^L_j, J^R_j of the wall positions of a non-periodic line (shifted wall stencils, Sec. 3.2
+        // reading), from the thread's own window: nodes 0..M of the first chunk sit at window
+        // indices H + o, nodes N-M..N of the last chunk at K - 1 - M + H + o.  Same operations in
+        // the same order as local_integrals.
+        auto wall_integrals = [&](const T* win, T (&jlo)[K], T (&jro)[K]) {
+            if (start == 0) {
+#pragma unroll
+                for (int k = 0; k < H; ++k) {   // j = k < H
+                    T jl = T(0), jr = T(0);
+#pragma unroll
+                    for (int o = 0; o <= M; ++o) {
+                        const T v = win[H + o];
+                        if (k >= 1) jl = fma(lp.wlA[k - 1][o], v, jl);
+                        jr = fma(lp.wrA[k][o], v, jr);
+                    }
+                    jlo[k] = jl;
+                    jro[k] = jr;
+                }
+            }
+            if (start + K == n) {
+#pragma unroll
+                for (int k = K - H; k < K; ++k) {   // j = start + k >= jb = n - H
+                    T jl = T(0), jr = T(0);
+#pragma unroll
+                    for (int o = 0; o <= M; ++o) {
+                        const T v = win[K - 1 - M + H + o];
+                        jl = fma(lp.wlB[k - (K - H)][o], v, jl);
+                        if (k < K - 1) jr = fma(lp.wrB[k - (K - H)][o], v, jr);
+                    }
+                    jlo[k] = jl;
+                    jro[k] = jr;
+                }
+            }
+        };
+        if constexpr (kPack) {
+            unsigned long long win2[K + M];
+#pragma unroll
+            for (int i = 0; i < K + M; ++i) win2[i] = PL::pack(fw[0][V - H + i], fw[1][V - H + i]);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                unsigned long long jl = PL::fma(pw.wl[0], win2[k], PL::zero());
+                unsigned long long jr = PL::fma(pw.wr[0], win2[k], PL::zero());
+#pragma unroll
+                for (int o = 1; o <= M; ++o) {
+                    jl = PL::fma(pw.wl[o], win2[k + o], jl);
+                    jr = PL::fma(pw.wr[o], win2[k + o], jr);
+                }
+                JL2[k] = jl;
+                JR2[k] = jr;
+            }
+            if (!periodic && (start == 0 || start + K == n)) {
+                // chunks touching a wall: the shifted wall stencils, field by field (as
+                // local_integrals), node values gathered from the staged line
+                const int N = lp.N, jb = N - H + 1;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int j = start + k;
+                    if (j >= H && j < jb) continue;
+                    T jl[2] = {T(0), T(0)}, jr[2] = {T(0), T(0)};
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+                        for (int o = 0; o <= M; ++o) {
+                            if (j < H) {
+                                const T v = at_field(o, q);
+                                if (j >= 1) jl[q] = fma(lp.wlA[j - 1][o], v, jl[q]);
+                                jr[q] = fma(lp.wrA[j][o], v, jr[q]);
+                            } else {
+                                const T v = at_field(N - M + o, q);
+                                jl[q] = fma(lp.wlB[j - jb][o], v, jl[q]);
+                                if (j < N) jr[q] = fma(lp.wrB[j - jb][o], v, jr[q]);
+                            }
+                        }
+                    }
+                    JL2[k] = PL::pack(jl[0], jl[1]);
+                    JR2[k] = PL::pack(jr[0], jr[1]);
+                }
+            }
+            const unsigned long long d2 = PL::splat(d);
+            unsigned long long a = PL::zero(), b = PL::zero();
+#pragma unroll
+            for (int k = 0; k < K; ++k) a = PL::fma(d2, a, JL2[k]);
+#pragma unroll
+            for (int k = K - 1; k >= 0; --k) b = PL::fma(d2, b, JR2[k]);
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                aL[q] = PL::get(a, q);
+                aR[q] = PL::get(b, q);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                T win[K + M];
+#pragma unroll
+                for (int i = 0; i < K + M; ++i) win[i] = fw[q][V - H + i];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {   // interior stencil (as local_integrals)
+                    T jl = T(0), jr = T(0);
+#pragma unroll
+                    for (int o = 0; o <= M; ++o) {
+                        jl = fma(lp.wl[o], win[k + o], jl);
+                        jr = fma(lp.wr[o], win[k + o], jr);
+                    }
+                    JL[q][k] = jl;
+                    JR[q][k] = jr;
+                }
+                if (!periodic) wall_integrals(win, JL[q], JR[q]);
+                chunk_aggregates<T, K>(d, K, JL[q], JR[q], aL[q], aR[q]);
+            }
+        }
+
+        // ---- scan of the chunk segments: shuffles inside each warp ----
+        T Df = D, Db = D, Af[NF], Ab[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            Af[q] = aL[q];
+            Ab[q] = aR[q];
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T dpf = __shfl_up_sync(kFull, Df, o);
+            const T dpb = __shfl_down_sync(kFull, Db, o);
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                const T apf = __shfl_up_sync(kFull, Af[q], o);
+                const T apb = __shfl_down_sync(kFull, Ab[q], o);
+                if (lane >= o) Af[q] = fma(apf, Df, Af[q]);
+                if (lane + o < 32) Ab[q] = fma(apb, Db, Ab[q]);
+            }
+            if (lane >= o) Df = dpf * Df;
+            if (lane + o < 32) Db = dpb * Db;
+        }
+        T Dxf = __shfl_up_sync(kFull, Df, 1), Dxb = __shfl_down_sync(kFull, Db, 1);
+        T Axf[NF], Axb[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            Axf[q] = __shfl_up_sync(kFull, Af[q], 1);
+            Axb[q] = __shfl_down_sync(kFull, Ab[q], 1);
+            if (lane == 0) Axf[q] = T(0);
+            if (lane == 31) Axb[q] = T(0);
+        }
+        if (lane == 0) Dxf = T(1);
+        if (lane == 31) Dxb = T(1);
+        if (lane == 31) {
+            s_scan[warp][0] = Df;
+#pragma unroll
+            for (int q = 0; q < NF; ++q) s_scan[warp][2 + q] = Af[q];
+        }
+        if (lane == 0) {
+            s_scan[warp][1] = Db;
+#pragma unroll
+            for (int q = 0; q < NF; ++q) s_scan[warp][2 + NF + q] = Ab[q];
+        }
+        __syncthreads();
+        // ---- warp 0 scans the warp segments (log depth) and solves the boundary system ----
+        if (warp == 0) {
+            const bool has = lane < wpl;
+            T fD = has ? s_scan[lane][0] : T(1);
+            T bD = has ? s_scan[lane][1] : T(1);
+            T fA[NF], bA[NF];
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                fA[q] = has ? s_scan[lane][2 + q] : T(0);
+                bA[q] = has ? s_scan[lane][2 + NF + q] : T(0);
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const T pfD = __shfl_up_sync(kFull, fD, o);
+                const T pbD = __shfl_down_sync(kFull, bD, o);
+#pragma unroll
+                for (int q = 0; q < NF; ++q) {
+                    const T pf = __shfl_up_sync(kFull, fA[q], o);
+                    const T pb = __shfl_down_sync(kFull, bA[q], o);
+                    if (lane >= o) fA[q] = fma(pf, fD, fA[q]);
+                    if (lane + o < 32) bA[q] = fma(pb, bD, bA[q]);
+                }
+                if (lane >= o) fD = pfD * fD;
+                if (lane + o < 32) bD = pbD * bD;
+            }
+            T exF[NF], exB[NF], totF[NF], totB[NF];
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                exF[q] = __shfl_up_sync(kFull, fA[q], 1);
+                exB[q] = __shfl_down_sync(kFull, bA[q], 1);
+                totF[q] = __shfl_sync(kFull, fA[q], 31);
+                totB[q] = __shfl_sync(kFull, bA[q], 0);
+                if (lane == 0) exF[q] = T(0);
+                if (lane + 1 >= wpl) exB[q] = T(0);
+            }
+            __syncwarp();
+            if (has) {
+#pragma unroll
+                for (int q = 0; q < NF; ++q) {
+                    s_scan[lane][2 + q] = exF[q];
+                    s_scan[lane][2 + NF + q] = exB[q];
+                }
+            }
+            // one FP64 2x2 boundary solve per line and field (Eq. homogeneous and analogues);
+            // lane q solves field q
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                if (lane == q) {
+                    const double I0 = static_cast<double>(totB[q]);
+                    const double IN = static_cast<double>(totF[q]);
+                    double a, b;
+                    if (periodic) {
+                        a = IN * lp.inv1mmu;
+                        b = I0 * lp.inv1mmu;
+                    } else {
+                        a = lp.bAA * I0 + lp.bAB * IN;
+                        b = lp.bBA * I0 + lp.bBB * IN;
+                    }
+                    s_bnd[q] = static_cast<T>(a);
+                    s_bnd[NF + q] = static_cast<T>(b);
+                }
+            }
+        }
+        __syncthreads();
+        T pF[NF], pB[NF], xl[NF], xr[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            pF[q] = s_scan[warp][2 + q];
+            pB[q] = s_scan[warp][2 + NF + q];
+            xl[q] = s_bnd[q];
+            xr[q] = s_bnd[NF + q];
+        }
+        const bool wallL = !periodic && start == 0, wallR = !periodic && start + K == n;
+        T cl[NF], cr[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            const T ax = fma(pF[q], Dxf, Axf[q]);
+            const T bx = fma(pB[q], Dxb, Axb[q]);
+            cl[q] = wallL ? T(0) : fma(pl, xl[q], ax);   // at a wall, P^L_0 = B_a is injected instead
+            cr[q] = wallR ? T(0) : fma(pr, xr[q], bx);   // ... and P^R_N = B_b
+        }
+        if constexpr (kPack) {
+            if (wallL) JL2[0] = PL::add(JL2[0], PL::pack(xl[0], xl[1]));
+            if (wallR) JR2[K - 1] = PL::add(JR2[K - 1], PL::pack(xr[0], xr[1]));
+            const unsigned long long d2 = PL::splat(d);
+            unsigned long long p = PL::pack(cr[0], cr[1]);
+#pragma unroll
+            for (int k = K - 1; k >= 0; --k) {
+                p = PL::fma(d2, p, JR2[k]);
+                JR2[k] = p;
+            }
+            unsigned long long qq = PL::pack(cl[0], cl[1]);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                qq = PL::fma(d2, qq, JL2[k]);
+                JR2[k] = PL::add(JR2[k], qq);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                if (wallL) JL[q][0] += xl[q];
+                if (wallR) JR[q][K - 1] += xr[q];
+                chunk_finish<T, K>(d, K, cl[q], cr[q], JL[q], JR[q]);
+            }
+        }
+
+        // ---- epilogue on this thread's own chunks ----
+        if constexpr (NA > 0) {
+            cp_async_wait<1>();      // this line's auxiliary group is complete
+            __syncthreads();
+        }
+#pragma unroll
+        for (int kc = 0; kc < KC; ++kc) {
+            const int c = start / V + kc;
+            float4 sraw[NS], araw[NA > 0 ? NA : 1], outv[NO];
+#pragma unroll
+            for (int f = 0; f < NS; ++f) sraw[f] = stage_buf(sb, f)[swz(c)];
+#pragma unroll
+            for (int f = 0; f < NA; ++f) araw[f] = aux_buf(f)[swz(c)];
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                T h[NF], sv[NS], av[NA > 0 ? NA : 1], ov[NO];
+#pragma unroll
+                for (int q = 0; q < NF; ++q) {
+                    if constexpr (kPack) h[q] = PL::get(JR2[kc * V + e], q);
+                    else h[q] = JR[q][kc * V + e];
+                }
+#pragma unroll
+                for (int f = 0; f < NS; ++f) sv[f] = comp4(sraw[f], e);
+#pragma unroll
+                for (int f = 0; f < NA; ++f) av[f] = comp4(araw[f], e);
+                if constexpr (NA == 0) av[0] = T(0);
+                op.epilogue(h, sv, av, ov, red);
+#pragma unroll
+                for (int o = 0; o < NO; ++o) set4(outv[o], e, ov[o]);
+            }
+#pragma unroll
+            for (int o = 0; o < NO; ++o) reinterpret_cast<float4*>(op.o[o] + line * ld)[c] = outv[o];
+        }
+    }
+    cp_async_wait<0>();
+    if (Op::kReduce) block_reduce_store<T>(red, red_slots);
+}
+
+// =========================================================================================
+// Rows, FP32, persistent and pipelined, one line split over a cluster of C blocks (the kernel above
+// when C = 1; C = 2 here; the cluster's blocks are consecutive in x): block rank r owns the slice
 // [r n/C, (r+1) n/C) with K = 16 positions per thread (TL = n / (16 C) threads).  Clusters loop
 // over lines cluster_id, + number of clusters, ...  The staged input fields of the next line's
 // slice, with one 16-byte chunk of halo on each side, arrive by cp.async (16-byte chunks,
@@ -319,16 +725,6 @@ rows_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, i
 // staged fields of 8192 nodes).
 // Requires n % (512 C) == 0, 1024 <= n <= 8192 C, TL <= 512, 16-byte aligned rows.
 // =========================================================================================
-__device__ __forceinline__ float comp4(const float4& v, int e) {
-    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
-}
-__device__ __forceinline__ void set4(float4& v, int e, float x) {
-    if (e == 0) v.x = x;
-    else if (e == 1) v.y = x;
-    else if (e == 2) v.z = x;
-    else v.w = x;
-}
-
 // Thread-block cluster primitives (sm_90 and later).
 __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
@@ -356,8 +752,8 @@ __device__ __forceinline__ int staged_index(int lc, int nchl) {
 
 template <int M, class Op, int C>
 __global__ void __launch_bounds__(512, 1)
-rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_constant__ PackedStencil pw, const Op op,
-                 int nlines, long long ld, unsigned long long* red_slots) {
+rows_cluster_kernel(const __grid_constant__ LineParams<float> lp, const __grid_constant__ PackedStencil pw, const Op op,
+                    int nlines, long long ld, unsigned long long* red_slots) {
     using T = float;
     constexpr int K = 16, V = 4, KC = K / V, H = M / 2, WC = KC + 2;
     constexpr int NS = Op::NS, NA = Op::NA, NF = Op::NF, NO = Op::NO;

@@ -29,7 +29,8 @@ EXPORTS = [
     "molt_column_tma_launches", "molt_batch_create", "molt_batch_destroy", "molt_batch_points",
     "molt_batch_offsets", "molt_batch_set_execution", "molt_batch_step", "molt_selftest_bounded_wait",
     "molt_step_adaptive",
-    "molt_vch_step", "molt_fma_throughput_probe",
+    "molt_vch_step", "molt_fma_throughput_probe", "molt_helmholtz_rows_tc", "molt_vch_step_adaptive",
+    "molt_batch_autotune", "molt_batch_set_schedule", "molt_autotune",
 ]
 EXECUTION = {"host_loop": 0, "graph": 1}
 PROFILE_SLOTS = 32
@@ -44,6 +45,16 @@ class _Adaptive(ctypes.Structure):
 class _AdaptiveInfo(ctypes.Structure):
     _fields_ = [("dt_used", ctypes.c_double), ("dt_next", ctypes.c_double), ("eta", ctypes.c_double),
                 ("rejections", ctypes.c_int), ("max_iters", ctypes.c_int)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("pass_", ctypes.c_int), ("axis", ctypes.c_int), ("chosen", ctypes.c_int),
+                ("candidates", ctypes.c_int), ("launch", ctypes.c_int * 4), ("ms", ctypes.c_double * 4),
+                ("tc_rel_diff", ctypes.c_double)]
+
+
+LAUNCH_NAMES = {0: "default", 1: "rows_one_block", 2: "rows_cluster2", 3: "rows_general", 4: "cols_tma",
+                5: "cols_cp_async", 6: "cols_general", 7: "rows_tensor_core"}
 
 
 class MoltError(RuntimeError):
@@ -92,6 +103,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_energy": ([P, VP, ctypes.POINTER(D), VP], I),
         "molt_mass": ([P, VP, ctypes.POINTER(D), VP], I),
         "molt_helmholtz_apply": ([P, I, D, VP, VP, VP], I),
+        "molt_helmholtz_rows_tc": ([P, D, VP, VP, VP], I),
         "molt_quadrature_weights": ([D, I, ctypes.POINTER(I), I, ctypes.POINTER(D)], I),
         "molt_last_error": ([P], ctypes.c_char_p),
         "molt_kernel_launches": ([P], ctypes.c_longlong),
@@ -106,11 +118,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_fma_throughput_probe": ([I, ctypes.POINTER(D)], I),
         "molt_step_adaptive": ([P, VP, D, ctypes.POINTER(_Adaptive), VP, ctypes.POINTER(_AdaptiveInfo)], I),
         "molt_vch_step": ([P, VP, VP, D, I, VP, ctypes.POINTER(_StepInfo)], I),
+        "molt_vch_step_adaptive": ([P, VP, VP, D, ctypes.POINTER(_Adaptive), VP, ctypes.POINTER(_AdaptiveInfo)], I),
         "molt_batch_create": ([ctypes.POINTER(VP), I, VP, I, I, D, I], I),
         "molt_batch_destroy": ([VP], I),
         "molt_batch_points": ([VP], ctypes.c_longlong),
         "molt_batch_offsets": ([VP, ctypes.POINTER(ctypes.c_longlong)], I),
         "molt_batch_set_execution": ([VP, I], I),
+        "molt_batch_autotune": ([VP, ctypes.POINTER(D), VP, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "molt_batch_set_schedule": ([VP, I, I], I),
+        "molt_autotune": ([P, VP, ctypes.POINTER(_Tuning), I, ctypes.POINTER(I)], I),
         "molt_batch_step": ([VP, VP, ctypes.POINTER(D), I, VP, ctypes.POINTER(I), ctypes.POINTER(D),
                              ctypes.POINTER(I)], I),
     }
@@ -328,6 +344,11 @@ class Solver:
         _check(self._lib.molt_helmholtz_apply(self._h, int(axis), float(c), self._field(inp), self._field(out),
                                               _stream_handle(stream)), self._h)
 
+    def helmholtz_rows_tc(self, c: float, inp, out, stream=None):
+        """H_c along x on the tensor cores (FP16 split products; see include/molt.h)."""
+        _check(self._lib.molt_helmholtz_rows_tc(self._h, float(c), self._field(inp), self._field(out),
+                                                _stream_handle(stream)), self._h)
+
     def step_adaptive(self, u, dt: float, lte_tol: float, dt_min: float, dt_max: float, theta: float = 0.8,
                       gamma: float = 1.3, estimator: str = "richardson", stream=None) -> dict:
         """One accepted step of adaptive size (Algorithm 1) with the "richardson" (BE), "sdc2"
@@ -339,6 +360,30 @@ class Solver:
                                             _stream_handle(stream), ctypes.byref(info)), self._h)
         return {"dt_used": info.dt_used, "dt_next": info.dt_next, "eta": info.eta,
                 "rejections": info.rejections, "max_iters": info.max_iters}
+
+    def vch_step_adaptive(self, u1, u2, dt: float, lte_tol: float, dt_min: float, dt_max: float,
+                          theta: float = 0.8, gamma: float = 1.3, estimator: str = "bdf2", stream=None) -> dict:
+        """One accepted adaptive step of the vector model (Algorithm 1) with the "richardson" or
+        "bdf2" (BE-BDF2) estimate; returns dt_used, dt_next, eta, rejections, max_iters."""
+        a = _Adaptive(lte_tol, dt_min, dt_max, theta, gamma, LTE_ESTIMATOR[estimator])
+        info = _AdaptiveInfo()
+        _check(self._lib.molt_vch_step_adaptive(self._h, self._field(u1), self._field(u2), float(dt), ctypes.byref(a),
+                                                _stream_handle(stream), ctypes.byref(info)), self._h)
+        return {"dt_used": info.dt_used, "dt_next": info.dt_next, "eta": info.eta,
+                "rejections": info.rejections, "max_iters": info.max_iters}
+
+    def autotune(self, stream=None) -> list:
+        """Time the kernel families of every sweep of a step and keep the fastest (molt_autotune);
+        returns one dict per sweep: pass, axis, chosen, and the ms of each candidate (-1: unavailable)."""
+        arr = (_Tuning * 16)()
+        n = ctypes.c_int(0)
+        _check(self._lib.molt_autotune(self._h, _stream_handle(stream), arr, 16, ctypes.byref(n)), self._h)
+        out = []
+        for t in arr[:min(n.value, 16)]:
+            out.append({"pass": t.pass_, "axis": "x" if t.axis == 0 else "y", "chosen": LAUNCH_NAMES[t.chosen],
+                        "ms": {LAUNCH_NAMES[t.launch[i]]: t.ms[i] for i in range(t.candidates)},
+                        "tc_rel_diff": t.tc_rel_diff if 7 in list(t.launch[:t.candidates]) else None})
+        return out
 
     def kernel_launches(self) -> int:
         return int(self._lib.molt_kernel_launches(self._h))
@@ -404,6 +449,21 @@ class Batch:
 
     def set_execution(self, mode: str):
         _check(self._lib.molt_batch_set_execution(self._h, EXECUTION[mode]))
+
+    def autotune(self, dt, stream=None) -> dict:
+        """Pick the launch schedule of the batched passes by timing (molt_batch_autotune); returns the
+        chosen grids (0 = one block per work item) and the 4 x 4 table of ms per iteration."""
+        dts = (ctypes.c_double * self.count)(*[float(x) for x in dt])
+        table = (ctypes.c_double * 16)()
+        gr, gc = ctypes.c_int(0), ctypes.c_int(0)
+        _check(self._lib.molt_batch_autotune(self._h, dts, _stream_handle(stream), table, ctypes.byref(gr),
+                                             ctypes.byref(gc)))
+        return {"grid_rows": gr.value, "grid_cols": gc.value, "ms_per_iteration": [list(table[4 * i:4 * i + 4])
+                                                                                   for i in range(4)]}
+
+    def set_schedule(self, grid_rows: int, grid_cols: int):
+        """Blocks per row / column launch of the batched passes (0 = one block per work item)."""
+        _check(self._lib.molt_batch_set_schedule(self._h, int(grid_rows), int(grid_cols)))
 
     def pack(self, fields):
         """Host arrays (one per instance, shape (ny, nx)) -> one packed float32 numpy array."""

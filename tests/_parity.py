@@ -43,8 +43,13 @@ def record(case: str, err: float, target: float, bar: float, kind: str, rho=None
 def check_fp32(case: str, got, ref, scale: float, rho=None, rho_limited_w=None, **extra):
     """Assert max|got - ref| <= 1e-6 * scale, or, for a case named rho-limited (rho_limited_w =
     max|w| of its stored variable), <= 8 ulp * max|w| / (1 - rho).  Records the achieved error."""
-    err = float(np.abs(np.asarray(got, dtype=np.float64) - np.asarray(ref, dtype=np.float64)).max())
+    diff = np.abs(np.asarray(got, dtype=np.float64) - np.asarray(ref, dtype=np.float64))
+    err = float(diff.max())
     target = FP32_REL * scale
+    if diff.ndim == 2 and min(diff.shape) > 16:   # where the largest difference sits (for the record)
+        j, i = np.unravel_index(int(np.argmax(diff)), diff.shape)
+        extra.setdefault("argmax_from_walls", int(min(j, i, diff.shape[0] - 1 - j, diff.shape[1] - 1 - i)))
+        extra.setdefault("err_beyond_8_nodes_of_the_edges", float(diff[8:-8, 8:-8].max()))
     if rho_limited_w is None:
         record(case, err, target, target, "strict", rho, **extra)
         assert err <= target, (case, err, target, rho)

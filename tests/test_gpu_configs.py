@@ -166,3 +166,24 @@ def test_config2_crop_converged_steps(precision):
     else:
         check_fp32(case, got, ref, scale, rho, rho_limited_w=np.abs(ref).max(), iters_gpu=ig, iters_oracle=io)
     assert energy(prob, got) <= energy(prob, u0.astype(np.float32).astype(np.float64))
+
+
+def test_autotuned_solver_keeps_parity():
+    # After molt_autotune (whatever kernel families it keeps on this GPU) the SDIRK3 workload's
+    # 1024 x 288 periodic block still meets the FP32 bar against the oracle, and every sweep of a
+    # step was tuned.
+    from paper_1611_04214_gb300.molt import Solver
+    rows, cols = 288, 1024
+    u0, Lx, Ly = _config3_block(rows, cols, "periodic")
+    with Solver(nx=cols, ny=rows, Lx=Lx, Ly=Ly, bc="periodic", eps=EPS3, quad_order=M3, precision="fp32",
+                tol=1e-30, max_iter=ITERS3) as s:
+        table = s.autotune()
+        assert [(t["pass"], t["axis"]) for t in table] == [(0, "x"), (0, "y"), (1, "y"), (2, "x"), (3, "y"), (4, "x")]
+        assert all(t["chosen"] != "default" for t in table), table
+        record("autotune_1024x288_periodic", 0.0, 0.0, 0.0, "autotune", None, table=table)
+        u = torch.tensor(u0.astype(np.float32), device="cuda")
+        iters = s.step(u, DT3, "sdirk3", raise_on_nonconvergence=False).iters
+        got = u.double().cpu().numpy()
+    ref, io = _oracle_fixed(rows, cols, "periodic", 1)
+    assert [iters] == io
+    check_fp32("config3_rows1024x288_sdirk3_periodic_autotuned", got, ref, np.abs(ref + 1).max())

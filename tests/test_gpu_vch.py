@@ -205,3 +205,31 @@ def test_vch_fp32_three_phase_mixture_fixed_iterations(bc):
         got = np.stack([g1.double().cpu().numpy(), g2.double().cpu().numpy()])
     check_fp32(f"vch_fp32_mixture_crop96x80_{bc}_bdf2_40it", got, np.stack([r1, r2]),
                max(np.abs(r1).max(), np.abs(r2).max()))
+
+
+@pytest.mark.parametrize("estimator", ["richardson", "bdf2"])
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+def test_vch_adaptive_matches_oracle(estimator, bc):
+    # Algorithm 1 for the vector model (Sec. 6.2.2) in FP64 on a 48 x 40 grid: the GPU controller
+    # takes the oracle's decisions, step sizes and rejections step for step, and its fields match.
+    from oracle.vch import vch_adaptive_step
+    from paper_1611_04214_gb300.molt import Solver
+    nx, ny = 48, 40
+    prob = Problem(nx=nx, ny=ny, bc=bc, eps=0.32, M=4, tol=1e-12, max_iter=400)
+    u1, u2 = _state(nx, ny, bc, seed=5)
+    hist, dt = {}, 2e-4
+    o1, o2 = u1.copy(), u2.copy()
+    g1 = torch.tensor(u1, device="cuda")
+    g2 = torch.tensor(u2, device="cuda")
+    with Solver(nx=nx, ny=ny, bc=bc, eps=0.32, quad_order=4, precision="fp64", tol=1e-12, max_iter=400) as s:
+        for _ in range(5):
+            gi = s.vch_step_adaptive(g1, g2, dt, 1e-4, 1e-8, 0.1, estimator=estimator)
+            o1, o2, oi = vch_adaptive_step(VchSolver(prob), o1, o2, dt, 1e-4, 1e-8, 0.1, estimator=estimator,
+                                           history=hist if estimator == "bdf2" else None)
+            assert gi["rejections"] == oi.rejections
+            assert abs(gi["dt_used"] - oi.dt_used) <= 1e-12 * oi.dt_used
+            assert abs(gi["dt_next"] - oi.dt_next) <= 1e-6 * oi.dt_next
+            assert abs(gi["eta"] - oi.eta) <= 1e-6 * oi.eta + 1e-14
+            dt = oi.dt_next
+        got = (g1.cpu().numpy(), g2.cpu().numpy())
+    assert max(np.abs(got[0] - o1).max(), np.abs(got[1] - o2).max()) < 1e-10
