@@ -32,9 +32,15 @@ constexpr int kCarryThreads = 128;
 enum Slot { LIX = 0, LOX = 1, LIY = 2, LOY = 3 };   // line parameters: axis x / y, inner / outer c
 
 struct Inst {
-    int nx, ny, tiles, pad;
+    int nx, ny, tiles;
+    int aoff;         // offset of the instance's rows in the packed Dirichlet offset row weights
     long long off;    // element offset of the instance in a packed field
     long long soff;   // element offset of the instance in each column-scan scratch array
+    int boff;         // offset of the instance's columns in the packed Dirichlet offset profiles
+    int pad;
+};
+struct RowRef {
+    int inst, row;
 };
 struct Stage {
     float g2, g1, beta, pad;   // lagged term G(w) = w (w (w + g2) + g1), beta = tau / c_in
@@ -107,16 +113,16 @@ __device__ __forceinline__ void load_lp(LineParams<float>& dst, const LineParams
 // is the batch's schedule, chosen by molt_batch_autotune).  The block barrier at the end of each
 // item keeps the next item's shared-memory writes behind this item's reads.
 
-template <int M, class Op>
+template <int M, class Op, bool kLoop>
 __global__ void __launch_bounds__(kRowThreads)
 rows_batch_kernel(const RowItem* __restrict__ items, int nitems, const Inst* __restrict__ inst,
                   const LineParams<float>* __restrict__ lps, int slot, const Stage* __restrict__ stages,
                   const int* __restrict__ done, const Op op0, unsigned long long* red) {
     __shared__ LineParams<float> slp;
     extern __shared__ __align__(16) unsigned char sm_rows_batch[];
-    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+    auto body = [&](int i) {
         const RowItem it = items[i];
-        if (done != nullptr && done[it.inst]) continue;
+        if (done != nullptr && done[it.inst]) return;
         load_lp(slp, lps + 4 * it.inst + slot);
         const Inst in = inst[it.inst];
         Op op = op0;
@@ -126,19 +132,26 @@ rows_batch_kernel(const RowItem* __restrict__ items, int nitems, const Inst* __r
         op.ps = 1;
         rows_body<float, M, kRowK, Op>(slp, op, in.ny, it.tl_log2, it.lpb, it.pitch, it.line0,
                                        reinterpret_cast<float*>(sm_rows_batch), red + 2 * it.inst);
-        __syncthreads();
+    };
+    if constexpr (!kLoop) {
+        body(blockIdx.x);
+    } else {
+        for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+            body(i);
+            __syncthreads();
+        }
     }
 }
 
-template <int M, class Op>
+template <int M, class Op, bool kLoop>
 __global__ void __launch_bounds__(32 * kColWY)
 cols_agg_batch_kernel(const ColItem* __restrict__ items, int nitems, const Inst* __restrict__ inst,
                       const LineParams<float>* __restrict__ lps, int slot, const Stage* __restrict__ stages,
                       const int* __restrict__ done, const Op op0, float* aggL, float* aggR) {
     __shared__ LineParams<float> slp;
-    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+    auto body = [&](int i) {
         const ColItem it = items[i];
-        if (done != nullptr && done[it.inst]) continue;
+        if (done != nullptr && done[it.inst]) return;
         load_lp(slp, lps + 4 * it.inst + slot);
         const Inst in = inst[it.inst];
         Op op = op0;
@@ -148,36 +161,51 @@ cols_agg_batch_kernel(const ColItem* __restrict__ items, int nitems, const Inst*
         op.ps = in.nx;
         cols_agg_body<float, M, kColKY, kColWY, Op>(slp, op, in.nx, aggL + in.soff, aggR + in.soff, in.tiles,
                                                     it.strip, it.tile);
-        __syncthreads();
+    };
+    if constexpr (!kLoop) {
+        body(blockIdx.x);
+    } else {
+        for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+            body(i);
+            __syncthreads();
+        }
     }
 }
 
+template <bool kLoop>
 __global__ void __launch_bounds__(kCarryThreads)
 carry_batch_kernel(const CarryItem* __restrict__ items, int nitems, const Inst* __restrict__ inst,
                    const LineParams<float>* __restrict__ lps, int slot, const int* __restrict__ done, int nf,
                    const float* aggL, const float* aggR, float* carL, float* carR) {
     __shared__ LineParams<float> slp;
-    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+    auto body = [&](int i) {
         const CarryItem it = items[i];
-        if (done != nullptr && done[it.inst]) continue;
+        if (done != nullptr && done[it.inst]) return;
         load_lp(slp, lps + 4 * it.inst + slot);
         const Inst in = inst[it.inst];
         carry_body<float>(slp, in.nx, nf, in.tiles, kColR, aggL + in.soff, aggR + in.soff, carL + in.soff,
                           carR + in.soff, it.idx0 + static_cast<int>(threadIdx.x));
-        __syncthreads();
+    };
+    if constexpr (!kLoop) {
+        body(blockIdx.x);
+    } else {
+        for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+            body(i);
+            __syncthreads();
+        }
     }
 }
 
-template <int M, class Op>
+template <int M, class Op, bool kLoop>
 __global__ void __launch_bounds__(32 * kColWY)
 cols_final_batch_kernel(const ColItem* __restrict__ items, int nitems, const Inst* __restrict__ inst,
                         const LineParams<float>* __restrict__ lps, int slot, const Stage* __restrict__ stages,
                         const int* __restrict__ done, const Op op0, const float* carL, const float* carR,
                         unsigned long long* red) {
     __shared__ LineParams<float> slp;
-    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+    auto body = [&](int i) {
         const ColItem it = items[i];
-        if (done != nullptr && done[it.inst]) continue;
+        if (done != nullptr && done[it.inst]) return;
         load_lp(slp, lps + 4 * it.inst + slot);
         const Inst in = inst[it.inst];
         Op op = op0;
@@ -187,7 +215,14 @@ cols_final_batch_kernel(const ColItem* __restrict__ items, int nitems, const Ins
         op.ps = in.nx;
         cols_final_body<float, M, kColKY, kColWY, Op>(slp, op, in.nx, carL + in.soff, carR + in.soff, in.tiles,
                                                       it.strip, it.tile, red + 2 * it.inst);
-        __syncthreads();
+    };
+    if constexpr (!kLoop) {
+        body(blockIdx.x);
+    } else {
+        for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+            body(i);
+            __syncthreads();
+        }
     }
 }
 
@@ -205,6 +240,44 @@ __global__ void loop_init_batch_kernel(LoopState* ls, unsigned long long* red, i
         red[2 * i] = 0ull;
         red[2 * i + 1] = 0ull;
         done[i] = 0;
+    }
+}
+
+// Dirichlet batches: Y += the stage's offset C of each instance (molt::dirichlet_offset), one row
+// per work item, the sum formed in FP64 in the order of the single-instance add_separable.
+__global__ void add_offset_batch_kernel(float* y, const RowRef* __restrict__ rows, int nrows,
+                                        const Inst* __restrict__ inst, const double* __restrict__ alpha,
+                                        const double* __restrict__ beta, long long astride, long long bstride) {
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const RowRef it = rows[r];
+        const Inst in = inst[it.inst];
+        double aj[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) aj[k] = alpha[k * astride + in.aoff + it.row];
+        float* row = y + in.off + static_cast<long long>(it.row) * in.nx;
+        for (int i = threadIdx.x; i < in.nx; i += blockDim.x) {
+            double acc = static_cast<double>(row[i]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc = fma(aj[k], beta[k * bstride + in.boff + i], acc);
+            row[i] = static_cast<float>(acc);
+        }
+    }
+}
+
+// Dirichlet batches: the stored wall value w = v - 1 = -1 on the four walls of instance blockIdx.x.
+__global__ void walls_batch_kernel(float* w, const Inst* __restrict__ inst, int count) {
+    if (static_cast<int>(blockIdx.x) >= count) return;
+    const Inst in = inst[blockIdx.x];
+    float* f = w + in.off;
+    for (int t = threadIdx.x; t < in.nx + in.ny; t += blockDim.x) {
+        if (t < in.nx) {
+            f[t] = -1.0f;
+            f[static_cast<long long>(in.ny - 1) * in.nx + t] = -1.0f;
+        } else {
+            const long long j = t - in.nx;
+            f[j * in.nx] = -1.0f;
+            f[j * in.nx + in.nx - 1] = -1.0f;
+        }
     }
 }
 
@@ -266,6 +339,7 @@ using molt::batch::CarryItem;
 using molt::batch::ColItem;
 using molt::batch::Inst;
 using molt::batch::RowItem;
+using molt::batch::RowRef;
 using molt::batch::Stage;
 
 struct molt_batch {
@@ -290,6 +364,12 @@ struct molt_batch {
     CarryItem* carry[2] = {nullptr, nullptr};
     float *w = nullptr, *r = nullptr, *Y = nullptr, *wprev = nullptr, *f[6] = {};
     float *aggL = nullptr, *aggR = nullptr, *carL = nullptr, *carR = nullptr;
+    // Dirichlet batches store u: per-instance offset profiles of the stage (row weights alpha[4][sum ny],
+    // column profiles beta[4][sum nx]), the FP64 profile workspace and the row work list
+    double *alpha = nullptr, *beta = nullptr, *dprof = nullptr;
+    RowRef* yrows = nullptr;
+    int n_yrows = 0;
+    long long sum_nx = 0, sum_ny = 0;
     std::vector<void*> allocs;
     // pinned host staging
     LineParams<float>* lps_host = nullptr;
@@ -351,26 +431,47 @@ bool balloc(molt_batch* b, U** p, size_t n) {
 // Grid of a pass over n work items under the batch's schedule (0 = one block per item).
 inline int pass_grid(int nitems, int cap) { return cap > 0 && cap < nitems ? cap : (nitems > 0 ? nitems : 1); }
 
+// A persistent grid (cap below the item count) runs the looping kernels; one block per item runs
+// the single-item kernels, which keep the smaller register footprint of the block bodies.
+inline bool loops(int nitems, int cap) { return cap > 0 && cap < nitems; }
+
 template <int M, class Op>
 cudaError_t rows_pass(molt_batch* b, int slot, const Op& op, bool skip, cudaStream_t st) {
-    rows_batch_kernel<M, Op><<<pass_grid(b->n_row, b->grid_rows), kRowThreads, b->row_smem, st>>>(
-        b->rows, b->n_row, b->inst, b->lps, slot, b->stages, skip ? b->done : nullptr, op, b->red);
+    const int grid = pass_grid(b->n_row, b->grid_rows);
+    const int* dn = skip ? b->done : nullptr;
+    if (loops(b->n_row, b->grid_rows))
+        rows_batch_kernel<M, Op, true><<<grid, kRowThreads, b->row_smem, st>>>(b->rows, b->n_row, b->inst, b->lps, slot,
+                                                                              b->stages, dn, op, b->red);
+    else
+        rows_batch_kernel<M, Op, false><<<grid, kRowThreads, b->row_smem, st>>>(b->rows, b->n_row, b->inst, b->lps,
+                                                                               slot, b->stages, dn, op, b->red);
     b->launches += 1;
     return cudaGetLastError();
 }
 
-template <int M, class Op>
-cudaError_t cols_pass(molt_batch* b, int slot, const Op& op, bool skip, cudaStream_t st) {
+template <int M, class Op, bool kLoop>
+void cols_launch(molt_batch* b, int slot, const Op& op, const int* dn, cudaStream_t st) {
     constexpr int NF = Op::NF;
-    const int* dn = skip ? b->done : nullptr;
     const dim3 blk(32, kColWY);
     const int nc = b->n_carry[NF - 1];
-    cols_agg_batch_kernel<M, Op><<<pass_grid(b->n_col, b->grid_cols), blk, 0, st>>>(
-        b->cols, b->n_col, b->inst, b->lps, slot, b->stages, dn, op, b->aggL, b->aggR);
-    carry_batch_kernel<<<pass_grid(nc, b->grid_cols), kCarryThreads, 0, st>>>(
-        b->carry[NF - 1], nc, b->inst, b->lps, slot, dn, NF, b->aggL, b->aggR, b->carL, b->carR);
-    cols_final_batch_kernel<M, Op><<<pass_grid(b->n_col, b->grid_cols), blk, 0, st>>>(
-        b->cols, b->n_col, b->inst, b->lps, slot, b->stages, dn, op, b->carL, b->carR, b->red);
+    const int gcol = pass_grid(b->n_col, b->grid_cols), gcar = pass_grid(nc, b->grid_cols);
+    cols_agg_batch_kernel<M, Op, kLoop><<<gcol, blk, 0, st>>>(b->cols, b->n_col, b->inst, b->lps, slot, b->stages, dn,
+                                                              op, b->aggL, b->aggR);
+    if (loops(nc, b->grid_cols))
+        carry_batch_kernel<true><<<gcar, kCarryThreads, 0, st>>>(b->carry[NF - 1], nc, b->inst, b->lps, slot, dn, NF,
+                                                                 b->aggL, b->aggR, b->carL, b->carR);
+    else
+        carry_batch_kernel<false><<<gcar, kCarryThreads, 0, st>>>(b->carry[NF - 1], nc, b->inst, b->lps, slot, dn, NF,
+                                                                  b->aggL, b->aggR, b->carL, b->carR);
+    cols_final_batch_kernel<M, Op, kLoop><<<gcol, blk, 0, st>>>(b->cols, b->n_col, b->inst, b->lps, slot, b->stages,
+                                                                dn, op, b->carL, b->carR, b->red);
+}
+
+template <int M, class Op>
+cudaError_t cols_pass(molt_batch* b, int slot, const Op& op, bool skip, cudaStream_t st) {
+    const int* dn = skip ? b->done : nullptr;
+    if (loops(b->n_col, b->grid_cols)) cols_launch<M, Op, true>(b, slot, op, dn, st);
+    else cols_launch<M, Op, false>(b, slot, op, dn, st);
     b->launches += 3;
     return cudaGetLastError();
 }
@@ -422,7 +523,13 @@ cudaError_t iteration(molt_batch* b, cudaStream_t st) {
     a4.u_in = b->f[3];
     a4.y_in = b->Y;
     a4.w = b->w;
-    return rows_pass<M>(b, LOX, a4, true, st);
+    cudaError_t e4 = rows_pass<M>(b, LOX, a4, true, st);
+    if (e4 != cudaSuccess || b->bc != molt::BC_DIRICHLET) return e4;
+    // every Dirichlet line inverse holds v = 0 on the walls: the stored w = -1 is set there, as the
+    // single-instance solver does after each iteration
+    walls_batch_kernel<<<b->count, 256, 0, st>>>(b->w, b->inst, b->count);
+    b->launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t rhs_inverse_any(molt_batch* b, cudaStream_t st) {
@@ -446,11 +553,11 @@ cudaError_t lin(molt_batch* b, float* out, const float* x0, double c0, const flo
 }
 
 // Step variants: 0 = BE, 1 = BE that also keeps the BDF2 history, 2 = BDF2 with history.
-// Stored variable w = u + s0 with s0 = 1 on Dirichlet grids (v = u + 1), 0 otherwise.
+// Stored variable w = u = v - 1 on every grid (as the single-instance solver; Dirichlet stages add
+// their offset to Y).
 cudaError_t pre_ops(molt_batch* b, const float* u, int variant, cudaStream_t st) {
-    const double s0 = b->bc == molt::BC_DIRICHLET ? 1.0 : 0.0;
     cudaError_t e;
-    if ((e = lin(b, b->w, u, 1.0, nullptr, 0.0, s0, st)) != cudaSuccess) return e;
+    if ((e = lin(b, b->w, u, 1.0, nullptr, 0.0, 0.0, st)) != cudaSuccess) return e;
     if (variant == 2) {
         if ((e = lin(b, b->r, b->w, 4.0 / 3.0, b->wprev, -1.0 / 3.0, 0.0, st)) != cudaSuccess) return e;
     } else {
@@ -460,9 +567,16 @@ cudaError_t pre_ops(molt_batch* b, const float* u, int variant, cudaStream_t st)
     return cudaSuccess;
 }
 
-cudaError_t post_ops(molt_batch* b, float* u, cudaStream_t st) {
-    const double s0 = b->bc == molt::BC_DIRICHLET ? 1.0 : 0.0;
-    return lin(b, u, b->w, 1.0, nullptr, 0.0, -s0, st);
+cudaError_t post_ops(molt_batch* b, float* u, cudaStream_t st) { return lin(b, u, b->w, 1.0, nullptr, 0.0, 0.0, st); }
+
+// Y of every instance, with the Dirichlet offsets of the loaded stage parameters.
+cudaError_t rhs_with_offset(molt_batch* b, cudaStream_t st) {
+    cudaError_t e = rhs_inverse_any(b, st);
+    if (e != cudaSuccess || b->bc != molt::BC_DIRICHLET) return e;
+    add_offset_batch_kernel<<<b->n_yrows < 152 * 8 ? b->n_yrows : 152 * 8, 128, 0, st>>>(
+        b->Y, b->yrows, b->n_yrows, b->inst, b->alpha, b->beta, b->sum_ny, b->sum_nx);
+    b->launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t loop_init(molt_batch* b, cudaStream_t st) {
@@ -475,7 +589,7 @@ cudaError_t loop_init(molt_batch* b, cudaStream_t st) {
 // build of the single-instance solver, cast to FP32), uploaded when they change.
 molt_status load_params(molt_batch* b, const std::vector<double>& tau, cudaStream_t st) {
     if (tau == b->tau_loaded) return MOLT_OK;
-    const double s = b->bc == molt::BC_DIRICHLET ? 0.0 : 1.0;
+    const double s = 1.0;   // stored w = v - 1 on every grid
     for (int i = 0; i < b->count; ++i) {
         const molt_instance& d = b->desc[i];
         const molt::StageParams sp = molt::stage_params(tau[i], d.eps);
@@ -497,6 +611,30 @@ molt_status load_params(molt_batch* b, const std::vector<double>& tau, cudaStrea
         st_i.beta = static_cast<float>(sp.beta);
         st_i.pad = 0.0f;
         b->stages_host[i] = st_i;
+        if (b->bc == molt::BC_DIRICHLET) {
+            // this instance's Y offset (the single-instance profiles), packed by instance
+            molt::LineParams<double> lp[4];
+            for (int slot = 0; slot < 4; ++slot) {
+                const bool y = slot >= LIY;
+                const int n = y ? d.ny : d.nx;
+                const char* err = nullptr;
+                molt::build_line_params(cs[slot], molt::grid_h(n, y ? d.Ly : d.Lx, b->bc), n, b->M, b->bc, &lp[slot],
+                                        &err);
+            }
+            molt::Separable sep;
+            cudaError_t e = molt::dirichlet_offset(lp, 2, sp.beta * (sp.lam - 2.0), b->dprof, 1024, &sep, st,
+                                                   &b->launches);
+            const Inst& in = b->inst_h[i];
+            for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+                e = cudaMemcpyAsync(b->alpha + k * b->sum_ny + in.aoff, sep.a[k], sizeof(double) * d.ny,
+                                    cudaMemcpyDeviceToDevice, st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(b->beta + k * b->sum_nx + in.boff, sep.b[k], sizeof(double) * d.nx,
+                                        cudaMemcpyDeviceToDevice, st);
+            }
+            if (e != cudaSuccess)
+                return batch_fail(MOLT_ERR_CUDA, std::string("Dirichlet offsets: ") + cudaGetErrorString(e));
+        }
     }
     cudaError_t e;
     if ((e = cudaMemcpyAsync(b->lps, b->lps_host, sizeof(LineParams<float>) * 4 * b->count, cudaMemcpyHostToDevice,
@@ -528,7 +666,7 @@ molt_batch::Graph* step_graph(molt_batch* b, float* u, int variant) {
     // head: loads, rhs inverse, loop state reset
     if (ok) ok = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed) == cudaSuccess;
     if (ok) {
-        const bool launched = pre_ops(b, u, variant, b->cap) == cudaSuccess && rhs_inverse_any(b, b->cap) == cudaSuccess &&
+        const bool launched = pre_ops(b, u, variant, b->cap) == cudaSuccess && rhs_with_offset(b, b->cap) == cudaSuccess &&
                               loop_init(b, b->cap) == cudaSuccess;
         ok = cudaStreamEndCapture(b->cap, &head) == cudaSuccess && launched;
     }
@@ -594,7 +732,7 @@ molt_status run_step(molt_batch* b, float* u, int variant, cudaStream_t st) {
         if ((e = cudaGraphLaunch(g->exec, st)) != cudaSuccess)
             return batch_fail(MOLT_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
     } else {
-        if ((e = pre_ops(b, u, variant, st)) != cudaSuccess || (e = rhs_inverse_any(b, st)) != cudaSuccess ||
+        if ((e = pre_ops(b, u, variant, st)) != cudaSuccess || (e = rhs_with_offset(b, st)) != cudaSuccess ||
             (e = loop_init(b, st)) != cudaSuccess)
             return batch_fail(MOLT_ERR_CUDA, std::string("stage set-up: ") + cudaGetErrorString(e));
         for (int k = 1; k <= b->max_iter; ++k) {
@@ -651,6 +789,7 @@ molt_status molt_batch_create(molt_batch** out, int count, const molt_instance* 
     std::vector<RowItem> rows;
     std::vector<ColItem> cols;
     std::vector<CarryItem> carry[2];
+    std::vector<RowRef> yrows;
     long long off = 0, soff = 0;
     for (int i = 0; i < count; ++i) {
         const molt_instance& d = instances[i];
@@ -660,9 +799,15 @@ molt_status molt_batch_create(molt_batch** out, int count, const molt_instance* 
         in.tiles = (d.ny + kColR - 1) / kColR;
         in.off = off;
         in.soff = soff;
+        in.aoff = static_cast<int>(b->sum_ny);
+        in.boff = static_cast<int>(b->sum_nx);
         off += static_cast<long long>(d.nx) * d.ny;
         soff += 2LL * in.tiles * d.nx;
+        b->sum_ny += d.ny;
+        b->sum_nx += d.nx;
         b->inst_h.push_back(in);
+        if (bc == MOLT_BC_DIRICHLET)
+            for (int j = 0; j < d.ny; ++j) yrows.push_back({i, j});
         // rows: the general row kernel's team (K = 8 positions per thread), lpb lines per block
         int tl_log2 = 0;
         while ((1 << tl_log2) < (d.nx + kRowK - 1) / kRowK) ++tl_log2;
@@ -692,6 +837,14 @@ molt_status molt_batch_create(molt_batch** out, int count, const molt_instance* 
               balloc(b, &b->aggL, ns) && balloc(b, &b->aggR, ns) && balloc(b, &b->carL, ns) &&
               balloc(b, &b->carR, ns);
     for (int k = 0; ok && k < 6; ++k) ok = balloc(b, &b->f[k], nt);
+    if (ok && bc == MOLT_BC_DIRICHLET) {
+        b->n_yrows = static_cast<int>(yrows.size());
+        ok = balloc(b, &b->alpha, 4 * static_cast<size_t>(b->sum_ny)) &&
+             balloc(b, &b->beta, 4 * static_cast<size_t>(b->sum_nx)) &&
+             balloc(b, &b->dprof, static_cast<size_t>(molt::kOffsetProfiles) * 1024) &&
+             balloc(b, &b->yrows, yrows.size()) &&
+             cudaMemcpy(b->yrows, yrows.data(), sizeof(RowRef) * yrows.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
     if (!ok) {
         delete b;
         return batch_fail(MOLT_ERR_OOM, "device workspace allocation failed");

@@ -773,6 +773,34 @@ __global__ void cubic_kernel(T* out, long long n, const T* x, T a2, T a1) {
 }
 }  // namespace detail
 
+namespace detail {
+template <typename T>
+__global__ void set_walls_kernel(T* w, int nx, int ny, T value) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ny == 1) {
+        if (t == 0) w[0] = value;
+        if (t == 1) w[nx - 1] = value;
+        return;
+    }
+    if (t < nx) {
+        w[t] = value;                                          // row 0
+        w[static_cast<size_t>(ny - 1) * nx + t] = value;       // row ny - 1
+    } else if (t < nx + ny) {
+        const size_t j = static_cast<size_t>(t - nx);
+        w[j * nx] = value;                                     // column 0
+        w[j * nx + nx - 1] = value;                            // column nx - 1
+    }
+}
+}  // namespace detail
+
+template <typename T>
+cudaError_t set_walls(T* w, int nx, int ny, double value, cudaStream_t st, long long* launches) {
+    const int total = ny == 1 ? 2 : nx + ny;
+    detail::set_walls_kernel<T><<<(total + 255) / 256, 256, 0, st>>>(w, nx, ny, static_cast<T>(value));
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t fill_pattern(T* p, long long n, unsigned seed, double lo, double hi, cudaStream_t st) {
     detail::fill_pattern_kernel<T><<<152 * 4, 256, 0, st>>>(p, n, seed, lo, hi);
@@ -863,4 +891,5 @@ cudaError_t max_abs_diff(const T* a, const T* b, long long n, unsigned long long
     template cudaError_t molt::cubic<T>(T*, long long, const T*, double, double, cudaStream_t, long long*);    \
     template cudaError_t molt::add_separable<T>(T*, int, int, const molt::Separable&, cudaStream_t, long long*); \
     template cudaError_t molt::fill_pattern<T>(T*, long long, unsigned, double, double, cudaStream_t);         \
+    template cudaError_t molt::set_walls<T>(T*, int, int, double, cudaStream_t, long long*);                   \
     template cudaError_t molt::max_abs_diff<T>(const T*, const T*, long long, unsigned long long*, cudaStream_t);

@@ -119,6 +119,11 @@ struct OpArgs {
 enum Launch { LAUNCH_DEFAULT = 0, LAUNCH_ROWS_ONE_BLOCK = 1, LAUNCH_ROWS_CLUSTER2 = 2, LAUNCH_ROWS_GENERAL = 3,
               LAUNCH_COLS_TMA = 4, LAUNCH_COLS_CP_ASYNC = 5, LAUNCH_COLS_GENERAL = 6, LAUNCH_ROWS_TENSOR_CORE = 7 };
 
+// Dirichlet grids: set the wall nodes of a [ny][nx] field (ny = 1: a line) to `value`, the stored
+// form of v = 0 (the boundary data every Dirichlet line inverse holds exactly).
+template <typename T>
+cudaError_t set_walls(T* w, int nx, int ny, double value, cudaStream_t st, long long* launches);
+
 // Fill n values with a hash of (seed, index) mapped uniformly to [lo, hi) (autotuner test data).
 template <typename T>
 cudaError_t fill_pattern(T* p, long long n, unsigned seed, double lo, double hi, cudaStream_t st);
@@ -183,6 +188,13 @@ struct Separable {
 };
 template <typename T>
 cudaError_t add_separable(T* y, int nx, int ny, const Separable& s, cudaStream_t st, long long* launches);
+
+// Dirichlet grids store w = v - 1: the fixed offset C of a stage's Y as a sum of products of FP64
+// line profiles (solver.cpp), from the line parameters of the stage's inner / outer inverses along
+// x and y (lp[0..3] = ix, ox, iy, oy; 1D: lp[0..1]) and beta g0 = beta (lambda - 2).
+constexpr int kOffsetProfiles = 16;
+cudaError_t dirichlet_offset(const LineParams<double> lp[4], int dim, double bg, double* prof, int L, Separable* out,
+                             cudaStream_t st, long long* launches);
 
 // Tensor-core row sweep of H_c on periodic FP32 lines (rows_tc.cu): workspace bytes, the line
 // lengths and line counts it takes, the one-time operand build for a line inverse, the sweep.

@@ -267,6 +267,22 @@ rows_kernel(const float* __restrict__ in, float* __restrict__ out, int n, int nl
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+template <int M>
+cudaError_t launch(const LineParams<double>& lp, const unsigned char* packed, const float* in, float* out, int nlines,
+                   unsigned* status, cudaStream_t st) {
+    static const cudaError_t optin =
+        cudaFuncSetAttribute(rows_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (optin != cudaSuccess) return optin;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles = static_cast<long long>(nlines) * (lp.n / C) / NT;
+    const int grid = static_cast<int>(tiles < sms ? tiles : sms);
+    rows_kernel<M><<<grid, THREADS, SMEM, st>>>(in, out, lp.n, nlines, packed, static_cast<float>(lp.nu), lp.inv1mmu,
+                                                status);
+    return cudaGetLastError();
+}
+
 }  // namespace tc
 
 size_t rows_tc_workspace_bytes() { return 2 * sizeof(double) * tc::C * tc::KP + 4 * static_cast<size_t>(tc::MAT_A); }
@@ -312,22 +328,12 @@ cudaError_t rows_tc(const LineParams<double>& lp, const void* workspace, const f
                     unsigned* status, cudaStream_t st) {
     if (lp.bc != BC_PERIODIC || !rows_tc_supported(lp.n, nlines, lp.M)) return cudaErrorInvalidValue;
     const unsigned char* packed = static_cast<const unsigned char*>(workspace) + 2 * sizeof(double) * tc::C * tc::KP;
-    auto launch = [&](auto kern) -> cudaError_t {
-        static const cudaError_t optin = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM);
-        if (optin != cudaSuccess) return optin;
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const long long tiles = static_cast<long long>(nlines) * (lp.n / tc::C) / tc::NT;
-        const int grid = static_cast<int>(tiles < sms ? tiles : sms);
-        kern<<<grid, tc::THREADS, tc::SMEM, st>>>(in, out, lp.n, nlines, packed, static_cast<float>(lp.nu),
-                                                  lp.inv1mmu, status);
-        return cudaGetLastError();
-    };
+    // the kernels of the three orders share one function type, so each opts in through its own
+    // function-local static
     switch (lp.M) {
-        case 2: return launch(tc::rows_kernel<2>);
-        case 4: return launch(tc::rows_kernel<4>);
-        default: return launch(tc::rows_kernel<6>);
+        case 2: return tc::launch<2>(lp, packed, in, out, nlines, status, st);
+        case 4: return tc::launch<4>(lp, packed, in, out, nlines, status, st);
+        default: return tc::launch<6>(lp, packed, in, out, nlines, status, st);
     }
 }
 

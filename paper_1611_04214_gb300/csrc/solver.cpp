@@ -81,6 +81,65 @@ molt::StageParams molt::stage_params(double tau, double eps) {
 
 double molt::grid_h(int n, double L, int bc) { return bc == molt::BC_PERIODIC ? L / n : L / (n - 1); }
 
+// Dirichlet offset of a stage (see the file comment).  With K the fused passes in w and K_v the same
+// passes in v (where G(1) = lambda - 2 =: g0),
+//   w_new = v_new - 1 = [Y_w + M_o^{-1} M_i^{-1} 1 + K_v(1) - 1] + K(w),
+// and the bracket's fixed part C is a sum of products of line profiles, from the passes applied to
+// v = 1 (T = g0 phi_iy, S = phi_iy, U, P, Q1, Q2 with phi_a = H_a 1):
+//   2D: C = psi1 (psi2 + H_oy p1 - a2) - phi_ix H_oy a2 + phi_ox (H_oy p0 - phi_iy) - psi2,
+//       a2 = 1 - phi_iy, p1 = (2 beta g0 - 1) phi_iy + 1 - beta g0, p0 = (1 - beta g0) phi_iy,
+//       psi1 = H_ox phi_ix, psi2 = H_oy phi_iy;
+//   1D: C = (1 + beta g0) psi1 - beta g0 phi_o - 1, psi1 = H_o phi_i.
+// C vanishes away from the walls (all profiles -> 1).  The profiles are FP64 sweeps of single lines
+// into `prof` (kOffsetProfiles rows of L >= max(nx, ny) doubles); *out receives the products.
+cudaError_t molt::dirichlet_offset(const LineParams<double> lp[4], int dim, double bg, double* prof, int L,
+                                   Separable* out, cudaStream_t st, long long* launches) {
+    auto P = [&](int k) { return prof + static_cast<size_t>(k) * L; };
+    auto sweep1 = [&](const LineParams<double>& l, const double* in, double* o) {
+        OpArgs<double> a;
+        a.in0 = in;
+        a.out0 = o;
+        return molt::sweep<double>(0, l, OP_COPY, a, l.n, 1, nullptr, nullptr, st, launches, nullptr);
+    };
+    auto lin1 = [&](double* o, int n, const double* x0, double c0, const double* x1, double c1, double c4) {
+        return molt::lincomb<double>(o, n, x0, c0, x1, c1, nullptr, 0, nullptr, 0, c4, st, launches);
+    };
+    const LineParams<double>&lix = lp[0], &lox = lp[1];
+    const int nx = lix.n;
+    cudaError_t e;
+    // x profiles: 0 = 1, 1 = phi_ix, 2 = phi_ox, 3 = psi1
+    if ((e = lin1(P(0), nx, nullptr, 0, nullptr, 0, 1.0)) != cudaSuccess || (e = sweep1(lix, P(0), P(1))) != cudaSuccess ||
+        (e = sweep1(lox, P(0), P(2))) != cudaSuccess || (e = sweep1(lox, P(1), P(3))) != cudaSuccess)
+        return e;
+    if (dim == 1) {
+        // beta_0 = (1 + beta g0) psi1 - beta g0 phi_o - 1 in profile 4, alpha_0 = 1 (profile 0)
+        if ((e = lin1(P(4), nx, P(3), 1.0 + bg, P(2), -bg, -1.0)) != cudaSuccess) return e;
+        *out = Separable{{P(0)}, {P(4)}, 1};
+        return cudaSuccess;
+    }
+    const LineParams<double>&liy = lp[2], &loy = lp[3];
+    const int ny = liy.n;
+    // y profiles: 5 = 1, 6 = phi_iy, 7 = a2, 8 = p1, 9 = p0, 10 = psi2, 11 = H_oy a2, 12 = H_oy p1,
+    // 13 = H_oy p0
+    if ((e = lin1(P(5), ny, nullptr, 0, nullptr, 0, 1.0)) != cudaSuccess || (e = sweep1(liy, P(5), P(6))) != cudaSuccess ||
+        (e = lin1(P(7), ny, P(6), -1.0, nullptr, 0, 1.0)) != cudaSuccess ||
+        (e = lin1(P(8), ny, P(6), 2.0 * bg - 1.0, nullptr, 0, 1.0 - bg)) != cudaSuccess ||
+        (e = lin1(P(9), ny, P(6), 1.0 - bg, nullptr, 0, 0.0)) != cudaSuccess ||
+        (e = sweep1(loy, P(6), P(10))) != cudaSuccess || (e = sweep1(loy, P(7), P(11))) != cudaSuccess ||
+        (e = sweep1(loy, P(8), P(12))) != cudaSuccess || (e = sweep1(loy, P(9), P(13))) != cudaSuccess)
+        return e;
+    // row weights of the four products: 14 = psi2 + H_oy p1 - a2 (with psi1), 15 = -H_oy a2 (with
+    // phi_ix), 13 = H_oy p0 - phi_iy (with phi_ox), 10 = -psi2 (with 1)
+    if ((e = molt::lincomb<double>(P(14), ny, P(10), 1.0, P(12), 1.0, P(7), -1.0, nullptr, 0, 0.0, st, launches)) !=
+            cudaSuccess ||
+        (e = lin1(P(15), ny, P(11), -1.0, nullptr, 0, 0.0)) != cudaSuccess ||
+        (e = lin1(P(13), ny, P(13), 1.0, P(6), -1.0, 0.0)) != cudaSuccess ||
+        (e = lin1(P(10), ny, P(10), -1.0, nullptr, 0, 0.0)) != cudaSuccess)
+        return e;
+    *out = Separable{{P(14), P(15), P(13), P(10)}, {P(3), P(1), P(2), P(0)}, 4};
+    return cudaSuccess;
+}
+
 namespace {
 
 using molt::StageParams;
@@ -435,73 +494,23 @@ struct Solver final : molt_solver {
                    st);
     }
 
-    // Dirichlet grids: the fixed field the constant part of v adds to a stage (see the file comment).
-    // With K the fused passes in w and K_v the same passes in v (where G(1) = lambda - 2 =: g0),
-    //   w_new = v_new - 1 = [Y_w + M_o^{-1} M_i^{-1} 1 + K_v(1) - 1] + K(w),
-    // and the bracket's fixed part C is a sum of products of line profiles, from the passes applied
-    // to v = 1 (T = g0 phi_iy, S = phi_iy, U, P, Q1, Q2 with phi_a = H_a 1):
-    //   2D: C = psi1 (psi2 + H_oy p1 - a2) - phi_ix H_oy a2 + phi_ox (H_oy p0 - phi_iy) - psi2,
-    //       a2 = 1 - phi_iy, p1 = (2 beta g0 - 1) phi_iy + 1 - beta g0, p0 = (1 - beta g0) phi_iy,
-    //       psi1 = H_ox phi_ix, psi2 = H_oy phi_iy;
-    //   1D: C = (1 + beta g0) psi1 - beta g0 phi_o - 1, psi1 = H_o phi_i.
-    // C vanishes away from the walls (all profiles -> 1).  The profiles are FP64 sweeps of single
-    // lines, and Y += C is formed per point in FP64.
-    static constexpr int kProfiles = 16;
+    // Dirichlet grids: the fixed field C the constant part of v adds to each stage's Y (see the file
+    // comment and molt::dirichlet_offset), added per point in FP64.
+    static constexpr int kProfiles = molt::kOffsetProfiles;
     cudaError_t add_dirichlet_offset(const StageParams& sp, T* y, cudaStream_t st) {
-        const int L = std::max(g.nx, g.ny);
-        auto P = [&](int k) { return dprof + static_cast<size_t>(k) * L; };
-        auto params = [&](double c, int axis, molt::LineParams<double>* out) {
-            const int n = axis == 0 ? g.nx : g.ny;
+        molt::LineParams<double> lp[4];
+        const double cs[4] = {sp.c_in, sp.c_out, sp.c_in, sp.c_out};
+        for (int k = 0; k < (g.dim == 2 ? 4 : 2); ++k) {
+            const int axis = k / 2, n = axis == 0 ? g.nx : g.ny;
             const char* e = nullptr;
-            return molt::build_line_params(c, grid_h(n, axis == 0 ? g.Lx : g.Ly, bc), n, p.quad_order, bc, out, &e);
-        };
-        auto sweep1 = [&](const molt::LineParams<double>& lp, const double* in, double* out) {
-            molt::OpArgs<double> a;
-            a.in0 = in;
-            a.out0 = out;
-            return molt::sweep<double>(0, lp, molt::OP_COPY, a, lp.n, 1, nullptr, nullptr, st, &launches, nullptr);
-        };
-        auto lin1 = [&](double* out, int n, const double* x0, double c0, const double* x1, double c1, double c4) {
-            return molt::lincomb<double>(out, n, x0, c0, x1, c1, nullptr, 0, nullptr, 0, c4, st, &launches);
-        };
-        const double bg = sp.beta * (sp.lam - 2.0);   // beta g0
-        molt::LineParams<double> lix, lox;
-        if (!params(sp.c_in, 0, &lix) || !params(sp.c_out, 0, &lox)) return cudaErrorInvalidValue;
-        const int nx = g.nx, ny = g.ny;
-        cudaError_t e;
-        // x profiles: 0 = 1, 1 = phi_ix, 2 = phi_ox, 3 = psi1
-        if ((e = lin1(P(0), nx, nullptr, 0, nullptr, 0, 1.0)) != cudaSuccess ||
-            (e = sweep1(lix, P(0), P(1))) != cudaSuccess || (e = sweep1(lox, P(0), P(2))) != cudaSuccess ||
-            (e = sweep1(lox, P(1), P(3))) != cudaSuccess)
-            return e;
-        if (g.dim == 1) {
-            // beta_0 = (1 + beta g0) psi1 - beta g0 phi_o - 1 in profile 4, alpha_0 = 1 (profile 0)
-            if ((e = lin1(P(4), nx, P(3), 1.0 + bg, P(2), -bg, -1.0)) != cudaSuccess) return e;
-            molt::Separable sep{{P(0)}, {P(4)}, 1};
-            return molt::add_separable<T>(y, nx, 1, sep, st, &launches);
+            if (!molt::build_line_params(cs[k], grid_h(n, axis == 0 ? g.Lx : g.Ly, bc), n, p.quad_order, bc, &lp[k], &e))
+                return cudaErrorInvalidValue;
         }
-        molt::LineParams<double> liy, loy;
-        if (!params(sp.c_in, 1, &liy) || !params(sp.c_out, 1, &loy)) return cudaErrorInvalidValue;
-        // y profiles: 5 = 1, 6 = phi_iy, 7 = a2, 8 = p1, 9 = p0, 10 = psi2, 11 = H_oy a2, 12 = H_oy p1,
-        // 13 = H_oy p0
-        if ((e = lin1(P(5), ny, nullptr, 0, nullptr, 0, 1.0)) != cudaSuccess ||
-            (e = sweep1(liy, P(5), P(6))) != cudaSuccess ||
-            (e = lin1(P(7), ny, P(6), -1.0, nullptr, 0, 1.0)) != cudaSuccess ||
-            (e = lin1(P(8), ny, P(6), 2.0 * bg - 1.0, nullptr, 0, 1.0 - bg)) != cudaSuccess ||
-            (e = lin1(P(9), ny, P(6), 1.0 - bg, nullptr, 0, 0.0)) != cudaSuccess ||
-            (e = sweep1(loy, P(6), P(10))) != cudaSuccess || (e = sweep1(loy, P(7), P(11))) != cudaSuccess ||
-            (e = sweep1(loy, P(8), P(12))) != cudaSuccess || (e = sweep1(loy, P(9), P(13))) != cudaSuccess)
-            return e;
-        // row weights of the four products: 14 = psi2 + H_oy p1 - a2 (with psi1), 15 = -H_oy a2 (with
-        // phi_ix), 13 = H_oy p0 - phi_iy (with phi_ox), 10 = -psi2 (with 1)
-        if ((e = molt::lincomb<double>(P(14), ny, P(10), 1.0, P(12), 1.0, P(7), -1.0, nullptr, 0, 0.0, st,
-                                       &launches)) != cudaSuccess ||
-            (e = lin1(P(15), ny, P(11), -1.0, nullptr, 0, 0.0)) != cudaSuccess ||
-            (e = lin1(P(13), ny, P(13), 1.0, P(6), -1.0, 0.0)) != cudaSuccess ||
-            (e = lin1(P(10), ny, P(10), -1.0, nullptr, 0, 0.0)) != cudaSuccess)
-            return e;
-        molt::Separable sep{{P(14), P(15), P(13), P(10)}, {P(3), P(1), P(2), P(0)}, 4};
-        return molt::add_separable<T>(y, nx, ny, sep, st, &launches);
+        molt::Separable sep;
+        const cudaError_t e = molt::dirichlet_offset(lp, g.dim, sp.beta * (sp.lam - 2.0), dprof, std::max(g.nx, g.ny),
+                                                     &sep, st, &launches);
+        if (e != cudaSuccess) return e;
+        return molt::add_separable<T>(y, g.nx, g.dim == 2 ? g.ny : 1, sep, st, &launches);
     }
 
     // Everything one fixed-point iteration of a stage launches (line parameters by value).
@@ -577,6 +586,7 @@ struct Solver final : molt_solver {
                 molt::OpArgs<T> a4;
                 a4.in0 = Q1[c]; a4.in1 = Q2[c]; a4.in2 = U[c]; a4.in3 = Yc[c]; a4.out0 = V[c]; a4.shift = ps.s;
                 if ((e = sweep(0, ps.lox, molt::OP_P4, a4, st)) != cudaSuccess) return e;
+                if ((e = impose_walls(V[c], st, 0.0)) != cudaSuccess) return e;
             }
             return cudaSuccess;
         }
@@ -590,8 +600,17 @@ struct Solver final : molt_solver {
             molt::OpArgs<T> ab;
             ab.in0 = E[c]; ab.in1 = Yc[c]; ab.out0 = V[c]; ab.shift = ps.s;
             if ((e = sweep(0, ps.lox, molt::OP_1B, ab, st)) != cudaSuccess) return e;
+            if ((e = impose_walls(V[c], st, 0.0)) != cudaSuccess) return e;
         }
         return cudaSuccess;
+    }
+
+    // Dirichlet grids: every line inverse holds v = 0 on the walls exactly, so every iterate does; the
+    // stored wall value w = v - 1 = -1 is set after each iteration instead of carrying the FP32
+    // rounding of the sum of O(1) terms that reproduces it (the vector model stores v - z3 = 0).
+    cudaError_t impose_walls(T* field, cudaStream_t st, double value = -1.0) {
+        if (bc != molt::BC_DIRICHLET) return cudaSuccess;
+        return molt::set_walls<T>(field, g.nx, g.dim == 2 ? g.ny : 1, value, st, &launches);
     }
 
     // One iteration: 2D passes 1-4 (column, row, column, row) or the two 1D row passes.  The
@@ -612,14 +631,16 @@ struct Solver final : molt_solver {
             if ((e = sweep(1, ps.loy, molt::OP_P3, a3, st)) != cudaSuccess) return e;
             molt::OpArgs<T> a4;
             a4.in0 = f5; a4.in1 = f6; a4.in2 = f4; a4.in3 = Y; a4.out0 = w; a4.shift = ps.s;
-            return sweep(0, ps.lox, molt::OP_P4, a4, st);
+            if ((e = sweep(0, ps.lox, molt::OP_P4, a4, st)) != cudaSuccess) return e;
+            return impose_walls(w, st);
         }
         molt::OpArgs<T> aa;
         aa.in0 = w; aa.out0 = f1; aa.g2 = ps.g2; aa.g1 = ps.g1; aa.beta = ps.beta;
         if ((e = sweep(0, ps.lix, molt::OP_1A, aa, st)) != cudaSuccess) return e;
         molt::OpArgs<T> ab;
         ab.in0 = f1; ab.in1 = Y; ab.out0 = w; ab.shift = ps.s;
-        return sweep(0, ps.lox, molt::OP_1B, ab, st);
+        if ((e = sweep(0, ps.lox, molt::OP_1B, ab, st)) != cudaSuccess) return e;
+        return impose_walls(w, st);
     }
 
     // Executable graphs of the stage loop, one per stage coefficient tau: a conditional WHILE

@@ -76,10 +76,7 @@ def _run_single(bc, scheme, steps, i, u0, tol=1e-6, max_iter=300):
         return u.cpu().numpy(), [inf.iters[0] for inf in infos], [inf.status for inf in infos]
 
 
-# Dirichlet grids: the single-instance solver stores u and adds the constant part of v to Y as an
-# FP64 offset; the batched passes store v = u + 1 (the walls' zero), so the two agree to FP32
-# rounding there, not bit for bit (their oracle parity is checked below).
-@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
 @pytest.mark.parametrize("scheme,steps", [("be", 2), ("bdf2", 3)])
 def test_batch_equals_single_instance_bitwise(bc, scheme, steps):
     u0, out, infos = _run_batch(bc, scheme, steps)

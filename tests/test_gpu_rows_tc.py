@@ -2,8 +2,12 @@
 the FP32 row sweep.
 
 The chunk products run on FP16 high / low splits of the operands (three products accumulated in
-FP32), so the result carries about 22 bits of each operand: it is held to 1e-6 of max|H f|, the
-bar of the FP32 sweeps, on lines of every supported length, quadrature order and decay.
+FP32 in tensor memory).  Each split represents its operand to about 2^-22 relative, and the 144
+window terms of a chunk row add in the tensor core's FP32 accumulator, so the sweep is held to
+16 * 2^-22 (3.8e-6) of max|H f|, on lines of every supported length, quadrature order and decay.
+Measured on a GB300 it sits at 1.5e-6 to 1.8e-6, against 1.4e-7 to 5.4e-7 for the FP32 sweep, so it
+misses the FP32 sweeps' 1e-6 bar: the autotuner's accuracy gate keeps it out of the production
+path (each record carries both errors).
 """
 import numpy as np
 import pytest
@@ -15,7 +19,9 @@ pytestmark = pytest.mark.gpu
 from oracle.helmholtz import helmholtz_inverse  # noqa: E402
 from paper_1611_04214_gb300.inputs import spacing, uniform_noise  # noqa: E402
 
-from _parity import check_fp32  # noqa: E402
+from _parity import record  # noqa: E402
+
+FP16_SPLIT_BAR = 16 * 2.0 ** -22
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -26,7 +32,7 @@ def _library():
     build.build_library()
 
 
-@pytest.mark.parametrize("n,nlines", [(1024, 16), (2048, 12), (8192, 3)])
+@pytest.mark.parametrize("n,nlines", [(1024, 16), (2048, 12), (8192, 8)])
 @pytest.mark.parametrize("M", [2, 4, 6])
 @pytest.mark.parametrize("nu", [0.02, 0.3, 2.0])
 def test_rows_tc_matches_oracle(n, nlines, M, nu):
@@ -45,8 +51,10 @@ def test_rows_tc_matches_oracle(n, nlines, M, nu):
         fp32 = ref32.double().cpu().numpy()
     ref = helmholtz_inverse(f.astype(np.float32).astype(np.float64), c, h, "periodic", M, axis=1)
     scale = np.abs(ref).max()
-    check_fp32(f"rows_tc_{n}x{nlines}_M{M}_nu{nu}", got, ref, scale,
-               fp32_sweep_err=float(np.abs(fp32 - ref).max() / scale))
+    err = float(np.abs(got - ref).max())
+    record(f"rows_tc_{n}x{nlines}_M{M}_nu{nu}", err, 1e-6 * scale, FP16_SPLIT_BAR * scale, "fp16-split", None,
+           fp32_sweep_err=float(np.abs(fp32 - ref).max() / scale))
+    assert err <= FP16_SPLIT_BAR * scale, (err, scale)
 
 
 def test_rows_tc_rejects_unsupported():
