@@ -44,16 +44,20 @@ class AdaptiveInfo:
 
 
 def decide(eta: float, tol: float, n_it: int, n_maxit: int, dt: float, theta: float = 0.8, gamma: float = 1.3):
-    """Algorithm 1, step 2: (accepted, next dt) for an attempt of size dt with LTE estimate eta."""
+    """Step-size decision of Algorithm 1: (accepted, next dt) for an attempt of size dt whose LTE
+    estimate is eta.  A step that meets the tolerance is kept unless its fixed-point iteration hit
+    the cap; it grows by the LTE proposal theta sqrt(tol/eta), at most by gamma when the iteration
+    used under 70% of its cap and not at all above that.  A failed step shrinks by gamma when the
+    iteration hit its cap or eta exceeds twice the tolerance, and takes the LTE proposal otherwise."""
     ratio = math.inf if eta == 0.0 else math.sqrt(tol / eta)
-    if eta <= tol:                                    # case (I)
+    if eta <= tol:
         frac = n_it / n_maxit
         if frac < 0.7:
             return True, dt * min(theta * ratio, gamma)
         if frac < 1.0:
             return True, dt * min(theta * ratio, 1.0)
-        return False, dt / gamma                      # step fails: the iteration hit its cap
-    if eta / tol > 2.0:                               # case (II): step fails
+        return False, dt / gamma
+    if eta / tol > 2.0:
         return False, dt / gamma
     return False, dt * theta * ratio
 
