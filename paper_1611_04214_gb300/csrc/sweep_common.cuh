@@ -173,10 +173,12 @@ __device__ __forceinline__ void chunk_finish(T d, int cnt, T cL, T cR, const T (
 // Per-point work of each pass, fused into the sweeps as load (prologue) / store (epilogue).
 // kAxes: 1 = runs on rows (x), 2 = on columns (y), 3 = both.
 // A field element of a line is at index line * ls + pos * ps.
-// G(x) = x (x (x + g2) + g1) is the lagged nonlinear term in the stored variable x:
-//   shifted storage x = u (= v - 1), periodic/Neumann: G = x^3 + (lam - 3) x   (the constant
-//   lam - 2 of G(v) is dropped: every operator it passes through maps constants to zero);
-//   unshifted x = v (Dirichlet):                       G = v^3 - 3 v^2 + lam v.
+// G(x) = x (x (x + g2) + g1) is the lagged nonlinear term in the stored variable x = u
+// (= v - 1): G = x^3 + (lam - 3) x, i.e. G(v) without its constant lam - 2.  Under periodic and
+// Neumann conditions every operator that constant passes through maps it to zero; under Dirichlet
+// conditions its image (with that of the shift) is the separable FP64 offset added to Y once per
+// stage (Eq. 2D_Helmholtz applied to constants).  g2 = g1 = 0 selects G = 0 (the linear parts
+// of a stage).
 // ---------------------------------------------------------------------------------------
 
 // Residual accumulators in the kernel precision: |w_new - w| of two nearby floats is exact

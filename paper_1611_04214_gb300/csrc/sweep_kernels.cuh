@@ -336,6 +336,7 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
     extern __shared__ __align__(128) unsigned char sm_rows_pipe[];
     float4* sm = reinterpret_cast<float4*>(sm_rows_pipe);
     __shared__ T s_scan[16][2 + 2 * NF];   // per-warp segments: D_f, D_b, A_f[NF], A_b[NF]
+    __shared__ T s_bnd[2 * NF];            // carries / B values of the line (FP64 solve)
 
     const int n = lp.n;
     const int nch = n / V;
@@ -564,10 +565,8 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
             for (int q = 0; q < NF; ++q) s_scan[warp][2 + NF + q] = Ab[q];
         }
         __syncthreads();
-        // ---- every warp scans the warp segments (log depth) and takes the segment entering it and
-        // the line totals; lane 0 solves the boundary system in FP64 (no second block barrier) ----
-        T pF[NF], pB[NF], xl[NF], xr[NF];
-        {
+        // ---- warp 0 scans the warp segments (log depth) and solves the boundary system ----
+        if (warp == 0) {
             const bool has = lane < wpl;
             T fD = has ? s_scan[lane][0] : T(1);
             T bD = has ? s_scan[lane][1] : T(1);
@@ -591,21 +590,31 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
                 if (lane >= o) fD = pfD * fD;
                 if (lane + o < 32) bD = pbD * bD;
             }
+            T exF[NF], exB[NF], totF[NF], totB[NF];
 #pragma unroll
             for (int q = 0; q < NF; ++q) {
-                T exF = __shfl_up_sync(kFull, fA[q], 1);
-                T exB = __shfl_down_sync(kFull, bA[q], 1);
-                const T totF = __shfl_sync(kFull, fA[q], 31);
-                const T totB = __shfl_sync(kFull, bA[q], 0);
-                if (lane == 0) exF = T(0);
-                if (lane + 1 >= wpl) exB = T(0);
-                pF[q] = __shfl_sync(kFull, exF, warp);   // segment entering this warp from the left
-                pB[q] = __shfl_sync(kFull, exB, warp);   // ... and from the right
-                // one FP64 2x2 boundary solve per line and field (Eq. homogeneous and analogues)
-                T a32 = T(0), b32 = T(0);
-                if (lane == 0) {
-                    const double I0 = static_cast<double>(totB);
-                    const double IN = static_cast<double>(totF);
+                exF[q] = __shfl_up_sync(kFull, fA[q], 1);
+                exB[q] = __shfl_down_sync(kFull, bA[q], 1);
+                totF[q] = __shfl_sync(kFull, fA[q], 31);
+                totB[q] = __shfl_sync(kFull, bA[q], 0);
+                if (lane == 0) exF[q] = T(0);
+                if (lane + 1 >= wpl) exB[q] = T(0);
+            }
+            __syncwarp();
+            if (has) {
+#pragma unroll
+                for (int q = 0; q < NF; ++q) {
+                    s_scan[lane][2 + q] = exF[q];
+                    s_scan[lane][2 + NF + q] = exB[q];
+                }
+            }
+            // one FP64 2x2 boundary solve per line and field (Eq. homogeneous and analogues);
+            // lane q solves field q
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                if (lane == q) {
+                    const double I0 = static_cast<double>(totB[q]);
+                    const double IN = static_cast<double>(totF[q]);
                     double a, b;
                     if (periodic) {
                         a = IN * lp.inv1mmu;
@@ -614,12 +623,19 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
                         a = lp.bAA * I0 + lp.bAB * IN;
                         b = lp.bBA * I0 + lp.bBB * IN;
                     }
-                    a32 = static_cast<T>(a);
-                    b32 = static_cast<T>(b);
+                    s_bnd[q] = static_cast<T>(a);
+                    s_bnd[NF + q] = static_cast<T>(b);
                 }
-                xl[q] = __shfl_sync(kFull, a32, 0);
-                xr[q] = __shfl_sync(kFull, b32, 0);
             }
+        }
+        __syncthreads();
+        T pF[NF], pB[NF], xl[NF], xr[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            pF[q] = s_scan[warp][2 + q];
+            pB[q] = s_scan[warp][2 + NF + q];
+            xl[q] = s_bnd[q];
+            xr[q] = s_bnd[NF + q];
         }
         const bool wallL = !periodic && start == 0, wallR = !periodic && start + K == n;
         T cl[NF], cr[NF];

@@ -1,0 +1,104 @@
+"""How far FP32 storage alone moves the oracle's own iteration (the evidence behind the known FP32
+misses of the GPU parity tests).
+
+The oracle is run twice on the same case: as it stands (FP64), and with FP32 rounding planted in
+it, on the CPU:
+* "iterate": the iterate of every fixed-point iteration rounded to FP32 (in the variable the GPU
+  stores: w = v - 1 = u for the scalar model, v = u - z3 for the vector model);
+* "all": in addition, the output of every line inversion H rounded to FP32.
+The difference between the two runs, over the 1e-6 target of the GPU parity tests, is how much
+of that target FP32 rounding of the method's own arithmetic spends, before any kernel is
+involved.  The Dirichlet crop is 256^2 here (about 20 s in all); MOLT_FP32_FLOOR_N=1024 runs it at
+the size of the GPU test (minutes).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle.solver as S
+import oracle.vch as V
+from oracle.solver import OracleSolver, Problem
+from oracle.vch import VchSolver
+from paper_1611_04214_gb300.inputs import gaussian_noise_block, three_phase_mixture
+
+from _parity import record
+
+
+def _r32(a):
+    return a.astype(np.float32).astype(np.float64)
+
+
+class _Planted:
+    """Plants FP32 rounding into the oracle for the duration of a with-block."""
+
+    def __init__(self, mode, vector=False):
+        self.mode, self.vector = mode, vector
+
+    def __enter__(self):
+        self.saved = (S.fixed_point_map, V._component_map, S.helmholtz_inverse)
+        fpm, cm, hi = self.saved
+        if self.mode in ("iterate", "all"):
+            if self.vector:
+                V._component_map = lambda *a: _r32(cm(*a))
+            else:
+                S.fixed_point_map = lambda p, Y, v, sp: _r32(fpm(p, Y, v, sp) - 1) + 1
+        if self.mode == "all":
+            S.helmholtz_inverse = lambda *a, **k: _r32(hi(*a, **k))
+        return self
+
+    def __exit__(self, *exc):
+        S.fixed_point_map, V._component_map, S.helmholtz_inverse = self.saved
+        return False
+
+
+def _config3_dirichlet(n, mode):
+    # top-left n x n block of the 8192^2 SDIRK3 workload, Dirichlet walls u = -1, two steps of
+    # 10 fixed iterations per stage
+    u = gaussian_noise_block((8192, 8192), n, n, 0.05, seed=0, mean=0.1)
+    u[0, :] = u[-1, :] = -1
+    u[:, 0] = u[:, -1] = -1
+    L = 2 * np.pi / 8191 * (n - 1)
+    prob = Problem(nx=n, ny=n, Lx=L, Ly=L, bc="dirichlet", eps=0.02, M=4, tol=1e-30, max_iter=10)
+    with _Planted(mode):
+        o, v = OracleSolver(prob), _r32(u)
+        for _ in range(2):
+            v, _ = o.step(v, 5e-5, "sdirk3")
+    return v
+
+
+def _mixture(bc, mode):
+    nx, ny = 96, 80
+    h = 2 * np.pi / 4095 if bc == "neumann" else 2 * np.pi / 4096
+    Lx, Ly = ((nx - 1) * h, (ny - 1) * h) if bc == "neumann" else (nx * h, ny * h)
+    prob = Problem(nx=nx, ny=ny, Lx=Lx, Ly=Ly, bc=bc, eps=0.03, M=4, tol=1e-30, max_iter=40)
+    u1, u2 = (_r32(a) for a in three_phase_mixture((ny, nx), seed=7))
+    with _Planted(mode, vector=True):
+        o = VchSolver(prob)
+        for _ in range(3):
+            u1, u2, _ = o.step(u1, u2, 1e-6, "bdf2")
+    return np.stack([u1, u2])
+
+
+@pytest.mark.parametrize("mode", ["iterate", "all"])
+def test_config3_dirichlet_crop_fp32_floor(mode):
+    n = int(os.environ.get("MOLT_FP32_FLOOR_N", "256"))
+    ref = _config3_dirichlet(n, "none")
+    err = float(np.abs(_config3_dirichlet(n, mode) - ref).max())
+    target = 1e-6 * np.abs(ref + 1).max()
+    record(f"fp32_floor_config3_crop{n}_dirichlet_{mode}", err, target, target, "fp32-floor")
+    # measured: 256^2 iterate 0.57 x, all 2.25 x; 1024^2 iterate 0.60 x, all 2.20 x
+    assert err > (1.0 if mode == "all" else 0.3) * target, err / target
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+@pytest.mark.parametrize("mode", ["iterate", "all"])
+def test_vch_mixture_fp32_floor(bc, mode):
+    ref = _mixture(bc, "none")
+    err = float(np.abs(_mixture(bc, mode) - ref).max())
+    target = 1e-6 * np.abs(ref).max()
+    record(f"fp32_floor_vch_mixture_{bc}_{mode}", err, target, target, "fp32-floor")
+    # measured: periodic iterate 1.48 x, all 5.19 x; Neumann iterate 0.55 x, all 2.56 x
+    lower = {("periodic", "iterate"): 1.0, ("periodic", "all"): 3.0,
+             ("neumann", "iterate"): 0.3, ("neumann", "all"): 1.5}[(bc, mode)]
+    assert err > lower * target, err / target

@@ -32,6 +32,12 @@ from _parity import check_fp32, check_fp64, record  # noqa: E402
 
 N3, EPS3, DT3, M3, ITERS3 = 8192, 0.02, 5e-5, 4, 10
 
+# Known miss (tests/_parity.py): the Dirichlet variant's FP32 error after 30 to 60 fixed
+# iterations is about 2.5e-6 of max|u|, as on the periodic variant, but its walls at u = -1 make
+# max|u| four times the periodic one while the scale max|u + 1| stays the same; the oracle's own
+# arithmetic with every sweep output rounded to FP32 lands at 2.2 x on the 1024^2 crop.
+CONFIG3_DIRICHLET_MISS = (3.0, "FP32 rounding of the iteration at |u| = 1 walls, 60 fixed iterations")
+
 
 @pytest.fixture(scope="module", autouse=True)
 def _library():
@@ -84,7 +90,8 @@ def test_config3_full_rows_fixed_iterations(bc):
     got, ig = _gpu_fixed(rows, cols, bc, 1, "fp32")
     ref, io = _oracle_fixed(rows, cols, bc, 1)
     assert ig == io == [[ITERS3] * 3], (ig, io)
-    check_fp32(f"config3_rows8192x288_sdirk3_{bc}_1step_10it", got, ref, np.abs(ref + 1).max())
+    check_fp32(f"config3_rows8192x288_sdirk3_{bc}_1step_10it", got, ref, np.abs(ref + 1).max(),
+               known_miss=CONFIG3_DIRICHLET_MISS if bc == "dirichlet" else None)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
@@ -99,7 +106,7 @@ def test_config3_crop_1024(bc, precision):
     if precision == "fp64":
         check_fp64(case + "_fp64", got, ref, 1e-11 * scale)
     else:
-        check_fp32(case, got, ref, scale)
+        check_fp32(case, got, ref, scale, known_miss=CONFIG3_DIRICHLET_MISS if bc == "dirichlet" else None)
 
 
 # ---- the Neumann BDF2 workload, iterated to its tolerance on a 128^2 crop ----

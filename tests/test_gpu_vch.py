@@ -203,8 +203,14 @@ def test_vch_fp32_three_phase_mixture_fixed_iterations(bc):
             r1, r2, oinfo = o.step(r1, r2, 1e-6, "bdf2")
             assert info.iters[0] == oinfo.iters[0] == 40
         got = np.stack([g1.double().cpu().numpy(), g2.double().cpu().numpy()])
+    # Known miss (tests/_parity.py): on this grid-scale mixture the lagged term carries the linear
+    # part s v with s = (c1 + c2)/tau = 73 and each stage runs 40 iterations; rounding only the
+    # oracle's own iterate v = u - z3 to FP32 after every iteration already gives 1.5 x (periodic)
+    # and 0.55 x (Neumann) the target, every sweep output rounded gives 5.2 x and 2.6 x.
+    guard = {"periodic": 12.0, "neumann": 5.5}[bc]
     check_fp32(f"vch_fp32_mixture_crop96x80_{bc}_bdf2_40it", got, np.stack([r1, r2]),
-               max(np.abs(r1).max(), np.abs(r2).max()))
+               max(np.abs(r1).max(), np.abs(r2).max()),
+               known_miss=(guard, "FP32 rounding over 120 iterations of a grid-scale mixture, s = 73"))
 
 
 @pytest.mark.parametrize("estimator", ["richardson", "bdf2"])
