@@ -315,7 +315,27 @@ def batched_leg(args, sample: int = 16):
                     "instance_steps_per_s": n / (ms * 1e-3),
                     "iters_min_median_max": [int(it.min()), float(np.median(it)), int(it.max())],
                     "instances_converged": int(sum(1 for s_ in infos[-1].instance_status if s_ == 0))})
-        del u
+        # the batched sweep over the same instance mix: one H_c of every instance along x, then
+        # along y (molt_batch_helmholtz_apply), nu = h / sqrt(c) = 0.08 on each instance
+        peak, _ = _peaks()
+        tmp = torch.empty_like(u)
+        cs = [(L / (int(s_) - 1) / 0.08) ** 2 for s_ in sides]
+        sweeps, reps = [], 10
+        for axis in (0, 1):
+            b.helmholtz_apply(axis, cs, u, tmp)                           # uploads the parameters
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                b.helmholtz_apply(axis, cs, u, tmp)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_s = e0.elapsed_time(e1) / reps
+            gbs = 8.0 * out["points"] / (ms_s * 1e-3) / 1e9
+            sweeps.append({"axis": "x" if axis == 0 else "y", "ms": ms_s,
+                           "gpts_per_s": out["points"] / (ms_s * 1e-3) / 1e9, "gbs_algorithmic": gbs,
+                           "frac_of_peak": gbs / peak})
+        out["batched_sweep"] = {"nu": 0.08, "bytes_per_point": 8, "cases": sweeps}
+        del u, tmp
     # the FP64 single-instance GPU path on the first `sample` instances, one at a time
     idx = list(range(sample))
     with Batch([(int(sides[i]), int(sides[i]), L, L, float(eps[i])) for i in idx], bc=BATCH["bc"],
@@ -504,7 +524,42 @@ def sweep_microbench(reps: int = 10):
         del fin, fout
         torch.cuda.empty_cache()
     out.append(tc_sweep_case(peak, reps))
+    out.append(nu_order_table(peak, reps))
     return out
+
+
+def nu_order_table(peak, reps: int = 10, n: int = 8192):
+    """FP32 single sweeps on 8192^2 over the range of nu = h/sqrt(c) the workloads span (0.01 for
+    the factorization regime's small alpha up to 4) and over M = 2, 4, 6, periodic and Dirichlet,
+    x and y: the fraction of the measured copy bandwidth of each (8 B/pt)."""
+    import torch
+
+    from paper_1611_04214_gb300.molt import Solver
+    g = torch.Generator(device="cuda").manual_seed(1)
+    fin = torch.rand((n, n), generator=g, device="cuda", dtype=torch.float32) * 2
+    fout = torch.empty_like(fin)
+    rows = []
+    for bc in ("periodic", "dirichlet"):
+        h = 2 * 3.141592653589793 / (n if bc == "periodic" else n - 1)
+        for M in (2, 4, 6):
+            with Solver(nx=n, ny=n, bc=bc, quad_order=M, precision="fp32", eps=0.02) as s:
+                for axis in (0, 1):
+                    for nu in (0.01, 0.08, 0.27, 1.0, 4.0):
+                        c = (h / nu) ** 2
+                        s.helmholtz_apply(axis, c, fin, fout)
+                        torch.cuda.synchronize()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        for _ in range(reps):
+                            s.helmholtz_apply(axis, c, fin, fout)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        ms = e0.elapsed_time(e1) / reps
+                        rows.append({"bc": bc, "M": M, "axis": "x" if axis == 0 else "y", "nu": nu, "ms": ms,
+                                     "frac_of_peak": 8.0 * n * n / (ms * 1e-3) / 1e9 / peak})
+    del fin, fout
+    torch.cuda.empty_cache()
+    return {"variant": "nu_and_order_table", "n": n, "precision": "fp32", "rows": rows}
 
 
 def tc_sweep_case(peak, reps: int = 10, n: int = 8192):

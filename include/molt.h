@@ -377,6 +377,16 @@ molt_status molt_batch_set_execution(molt_batch* batch, molt_execution mode);
 molt_status molt_batch_step(molt_batch* batch, float* u_dev, const double* dt, molt_scheme scheme, void* stream,
                             int* iters, double* residual, int* status);
 
+/* One line inversion H_c (Sec. 3.2, Eq. IL/IR with the boundary correction of Sec. 3.3) of every
+ * instance of the batch along one axis (0 = x, each row; 1 = y, each column), in one launch
+ * sequence over all instances: out = H_{c_i} in, instance by instance, with the batch's boundary
+ * condition and M.  c: host array of `count` values (> 0; alpha = c^(-1/2)); in, out: packed
+ * device fields (FP32, layout of molt_batch_create), not aliased.  The parameters of c are built
+ * and uploaded only when c changes (the call then synchronizes `stream`); later steps reload their
+ * own.  Asynchronous otherwise.  Errors: MOLT_ERR_ARG, MOLT_ERR_CUDA. */
+molt_status molt_batch_helmholtz_apply(molt_batch* batch, int axis, const double* c, const float* in_dev,
+                                       float* out_dev, void* stream);
+
 /* Schedule autotuner of the batched passes (no counterpart in the paper).  Every batched kernel
  * walks its work list (row items, column tiles, carry items) from its block index in steps of the
  * grid size, so one launch runs either one block per work item or a persistent grid of a few

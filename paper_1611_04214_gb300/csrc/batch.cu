@@ -377,6 +377,7 @@ struct molt_batch {
     LoopState* ls_host = nullptr;
     int* active_host = nullptr;
     std::vector<double> tau_loaded;     // taus whose parameters sit in lps / stages
+    std::vector<double> applied[2];     // c of the batched sweep whose parameters sit in slot LIX / LIY
     bool have_prev = false;
     std::vector<double> dt_prev;
     struct Graph {
@@ -547,6 +548,16 @@ cudaError_t iteration_any(molt_batch* b, cudaStream_t st) {
     }
 }
 
+// One line inversion H_c of every instance along one axis (slot LIX for x, LIY for y holds the
+// parameters of c_i while it runs).
+template <int M>
+cudaError_t apply_pass(molt_batch* b, int axis, const float* in, float* out, cudaStream_t st) {
+    molt::OpCopy<float> c{};
+    c.in = in;
+    c.out = out;
+    return axis == 0 ? rows_pass<M>(b, LIX, c, false, st) : cols_pass<M>(b, LIY, c, false, st);
+}
+
 cudaError_t lin(molt_batch* b, float* out, const float* x0, double c0, const float* x1, double c1, double c4,
                 cudaStream_t st) {
     return molt::lincomb<float>(out, b->total, x0, c0, x1, c1, nullptr, 0.0, nullptr, 0.0, c4, st, &b->launches);
@@ -646,6 +657,8 @@ molt_status load_params(molt_batch* b, const std::vector<double>& tau, cudaStrea
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
         return batch_fail(MOLT_ERR_CUDA, std::string("parameter upload: ") + cudaGetErrorString(e));
     b->tau_loaded = tau;
+    b->applied[0].clear();
+    b->applied[1].clear();
     return MOLT_OK;
 }
 
@@ -920,6 +933,48 @@ molt_status molt_batch_step(molt_batch* b, float* u, const double* dt, molt_sche
     }
     if (worst != MOLT_OK) molt::set_abi_error("an instance reached max_iter before the fixed-point tolerance");
     return worst;
+}
+
+molt_status molt_batch_helmholtz_apply(molt_batch* b, int axis, const double* c, const float* in, float* out,
+                                       void* stream) {
+    if (!b || !c || !in || !out) return batch_fail(MOLT_ERR_ARG, "null batch, c or field");
+    if (axis != 0 && axis != 1) return batch_fail(MOLT_ERR_ARG, "axis must be 0 (x) or 1 (y)");
+    if (in == out) return batch_fail(MOLT_ERR_ARG, "in and out must not alias");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int slot = axis == 0 ? LIX : LIY;
+    std::vector<double> cv(c, c + b->count);
+    cudaError_t e = cudaSuccess;
+    if (cv != b->applied[axis]) {
+        for (int i = 0; i < b->count; ++i) {
+            const molt_instance& d = b->desc[i];
+            if (!(cv[i] > 0.0) || !std::isfinite(cv[i]))
+                return batch_fail(MOLT_ERR_ARG, "instance " + std::to_string(i) + ": c must be finite and > 0");
+            const int n = axis == 0 ? d.nx : d.ny;
+            molt::LineParams<double> lpd;
+            const char* err = nullptr;
+            if (!molt::build_line_params(cv[i], molt::grid_h(n, axis == 0 ? d.Lx : d.Ly, b->bc), n, b->M, b->bc,
+                                         &lpd, &err))
+                return batch_fail(MOLT_ERR_ARG, std::string("instance ") + std::to_string(i) + ": " +
+                                                    (err ? err : "bad line parameters"));
+            b->lps_host[4 * i + slot] = molt::cast_line_params<float>(lpd);
+        }
+        b->tau_loaded.clear();   // the slot no longer holds a stage's parameters
+        // the whole table (the other slots are unchanged); the pinned staging buffer is free again
+        // once the copy has completed
+        e = cudaMemcpyAsync(b->lps, b->lps_host, sizeof(LineParams<float>) * 4 * b->count, cudaMemcpyHostToDevice,
+                            st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        b->applied[axis] = e == cudaSuccess ? cv : std::vector<double>();
+    }
+    if (e == cudaSuccess) {
+        switch (b->M) {
+            case 2: e = apply_pass<2>(b, axis, in, out, st); break;
+            case 4: e = apply_pass<4>(b, axis, in, out, st); break;
+            default: e = apply_pass<6>(b, axis, in, out, st); break;
+        }
+    }
+    if (e != cudaSuccess) return batch_fail(MOLT_ERR_CUDA, std::string("batched sweep: ") + cudaGetErrorString(e));
+    return MOLT_OK;
 }
 
 molt_status molt_batch_set_schedule(molt_batch* b, int grid_rows, int grid_cols) {

@@ -30,7 +30,7 @@ EXPORTS = [
     "molt_batch_offsets", "molt_batch_set_execution", "molt_batch_step", "molt_selftest_bounded_wait",
     "molt_step_adaptive",
     "molt_vch_step", "molt_fma_throughput_probe", "molt_helmholtz_rows_tc", "molt_vch_step_adaptive",
-    "molt_batch_autotune", "molt_batch_set_schedule", "molt_autotune",
+    "molt_batch_autotune", "molt_batch_set_schedule", "molt_autotune", "molt_batch_helmholtz_apply",
 ]
 EXECUTION = {"host_loop": 0, "graph": 1}
 PROFILE_SLOTS = 32
@@ -126,6 +126,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_batch_set_execution": ([VP, I], I),
         "molt_batch_autotune": ([VP, ctypes.POINTER(D), VP, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "molt_batch_set_schedule": ([VP, I, I], I),
+        "molt_batch_helmholtz_apply": ([VP, I, ctypes.POINTER(D), VP, VP, VP], I),
         "molt_autotune": ([P, VP, ctypes.POINTER(_Tuning), I, ctypes.POINTER(I)], I),
         "molt_batch_step": ([VP, VP, ctypes.POINTER(D), I, VP, ctypes.POINTER(I), ctypes.POINTER(D),
                              ctypes.POINTER(I)], I),
@@ -464,6 +465,16 @@ class Batch:
     def set_schedule(self, grid_rows: int, grid_cols: int):
         """Blocks per row / column launch of the batched passes (0 = one block per work item)."""
         _check(self._lib.molt_batch_set_schedule(self._h, int(grid_rows), int(grid_cols)))
+
+    def helmholtz_apply(self, axis: int, c, fin, fout, stream=None):
+        """out = H_{c_i} in for every instance along axis 0 (x) or 1 (y) (molt_batch_helmholtz_apply);
+        fin, fout: packed contiguous CUDA float32 tensors; c: one value per instance."""
+        for t in (fin, fout):
+            if not t.is_cuda or t.dtype.itemsize != 4 or not t.is_contiguous() or t.numel() != self.points:
+                raise ValueError("expected packed contiguous CUDA float32 fields of the batch")
+        cs = (ctypes.c_double * self.count)(*[float(x) for x in c])
+        _check(self._lib.molt_batch_helmholtz_apply(self._h, int(axis), cs, ctypes.c_void_p(fin.data_ptr()),
+                                                    ctypes.c_void_p(fout.data_ptr()), _stream_handle(stream)))
 
     def pack(self, fields):
         """Host arrays (one per instance, shape (ny, nx)) -> one packed float32 numpy array."""

@@ -173,3 +173,56 @@ def test_batch_autotune_keeps_results_bitwise():
             outs.append(u.cpu().numpy())
     for o in outs[1:]:
         assert np.array_equal(outs[0], o)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann", "dirichlet"])
+@pytest.mark.parametrize("M", [2, 4, 6])
+@pytest.mark.parametrize("axis", [0, 1])
+def test_batch_helmholtz_apply_matches_oracle(bc, M, axis):
+    # One batched line inversion per instance (molt_batch_helmholtz_apply) against the oracle's
+    # H_c of each instance, each with its own c (nu = h / sqrt(c) from 0.02 to 3), held to 1e-6 of
+    # the output's scale like the single-grid FP32 sweeps; a second call with other c reuses nothing.
+    from oracle.helmholtz import helmholtz_inverse
+    from paper_1611_04214_gb300.inputs import spacing
+    from paper_1611_04214_gb300.molt import Batch
+    inst = [(nx, ny, Lx, Ly, eps) for (nx, ny, Lx, Ly, eps, _) in INSTANCES]
+    with Batch(inst, bc=bc, quad_order=M, tol=1e-6, max_iter=10) as b:
+        fields = [uniform_noise((ny, nx), 1.0, seed=30 + i, mean=1.0) for i, (nx, ny, *_r) in enumerate(inst)]
+        fin = torch.tensor(b.pack(fields), device="cuda")
+        fout = torch.empty_like(fin)
+        for nus in ([0.02, 0.08, 0.27, 1.0, 3.0], [3.0, 1.0, 0.27, 0.08, 0.02]):
+            cs = []
+            for (nx, ny, Lx, Ly, _), nu in zip(inst, nus):
+                n, L = (nx, Lx) if axis == 0 else (ny, Ly)
+                cs.append((spacing(n, L, bc == "periodic") / nu) ** 2)
+            b.helmholtz_apply(axis, cs, fin, fout)
+            torch.cuda.synchronize()
+            got = b.unpack(fout.cpu().numpy())
+            for i, (nx, ny, Lx, Ly, _) in enumerate(inst):
+                h = spacing(nx if axis == 0 else ny, Lx if axis == 0 else Ly, bc == "periodic")
+                f = b.unpack(b.pack(fields))[i].astype(np.float64)
+                ref = helmholtz_inverse(f, cs[i], h, bc, M, axis=1 if axis == 0 else 0)
+                err = np.abs(got[i] - ref).max() / np.abs(ref).max()
+                assert err < 1e-6, (i, nus[i], err)
+
+
+def test_batch_helmholtz_apply_then_step_reloads_stage_parameters():
+    # A batched sweep overwrites a slot of the stage parameters; the next step must reload them and
+    # give the same result as a batch that never swept.
+    from paper_1611_04214_gb300.molt import Batch
+    inst = [(nx, ny, Lx, Ly, eps) for (nx, ny, Lx, Ly, eps, _) in INSTANCES]
+    dts = [dt for (*_, dt) in INSTANCES]
+    outs = []
+    for sweep_first in (False, True):
+        with Batch(inst, bc="neumann", quad_order=4, tol=1e-6, max_iter=20) as b:
+            u = torch.tensor(b.pack([_initial("neumann", i, nx, ny) for i, (nx, ny, *_r) in enumerate(inst)]),
+                             device="cuda")
+            b.step(u, dts, "be", raise_on_nonconvergence=False)
+            if sweep_first:
+                tmp = torch.empty_like(u)
+                b.helmholtz_apply(0, [0.5] * len(inst), u, tmp)
+                b.helmholtz_apply(1, [0.5] * len(inst), u, tmp)
+            b.step(u, dts, "be", raise_on_nonconvergence=False)
+            torch.cuda.synchronize()
+            outs.append(u.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
