@@ -404,13 +404,6 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
         }
         T JL[kPack ? 1 : NF][K], JR[kPack ? 1 : NF][K], aL[NF], aR[NF];
         unsigned long long JL2[kPack ? K : 1], JR2[kPack ? K : 1];   // packed J (then outputs)
-        auto at_field = [&](int p, int q) {
-            T sv[NS], fv[NF];
-#pragma unroll
-            for (int f = 0; f < NS; ++f) sv[f] = reinterpret_cast<const T*>(stage_buf(sb, f) + swz(p / V))[p % V];
-            op.prologue(sv, fv);
-            return fv[q];
-        };
         // J^L_j, J^R_j of the wall positions of a non-periodic line (shifted wall stencils, Sec. 3.2
         // reading), from the thread's own window: nodes 0..M of the first chunk sit at window
         // indices H + o, nodes N-M..N of the last chunk at K - 1 - M + H + o.  Same operations in
@@ -461,32 +454,44 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
                 JL2[k] = jl;
                 JR2[k] = jr;
             }
-            if (!periodic && (start == 0 || start + K == n)) {
+            if (!periodic) {
                 // chunks touching a wall: the shifted wall stencils, field by field (as
-                // local_integrals), node values gathered from the staged line
-                const int N = lp.N, jb = N - H + 1;
+                // local_integrals), from the thread's own packed window: nodes 0..M of the first
+                // chunk sit at window indices H + o, nodes N-M..N of the last chunk at
+                // K - 1 - M + H + o (the prologue is not evaluated again)
+                if (start == 0) {
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const int j = start + k;
-                    if (j >= H && j < jb) continue;
-                    T jl[2] = {T(0), T(0)}, jr[2] = {T(0), T(0)};
+                    for (int k = 0; k < H; ++k) {   // j = k < H
+                        T jl[2] = {T(0), T(0)}, jr[2] = {T(0), T(0)};
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
+                        for (int q = 0; q < 2; ++q) {
 #pragma unroll
-                        for (int o = 0; o <= M; ++o) {
-                            if (j < H) {
-                                const T v = at_field(o, q);
-                                if (j >= 1) jl[q] = fma(lp.wlA[j - 1][o], v, jl[q]);
-                                jr[q] = fma(lp.wrA[j][o], v, jr[q]);
-                            } else {
-                                const T v = at_field(N - M + o, q);
-                                jl[q] = fma(lp.wlB[j - jb][o], v, jl[q]);
-                                if (j < N) jr[q] = fma(lp.wrB[j - jb][o], v, jr[q]);
+                            for (int o = 0; o <= M; ++o) {
+                                const T v = PL::get(win2[H + o], q);
+                                if (k >= 1) jl[q] = fma(lp.wlA[k - 1][o], v, jl[q]);
+                                jr[q] = fma(lp.wrA[k][o], v, jr[q]);
                             }
                         }
+                        JL2[k] = PL::pack(jl[0], jl[1]);
+                        JR2[k] = PL::pack(jr[0], jr[1]);
                     }
-                    JL2[k] = PL::pack(jl[0], jl[1]);
-                    JR2[k] = PL::pack(jr[0], jr[1]);
+                }
+                if (start + K == n) {
+#pragma unroll
+                    for (int k = K - H; k < K; ++k) {   // j = start + k >= jb = n - H
+                        T jl[2] = {T(0), T(0)}, jr[2] = {T(0), T(0)};
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+#pragma unroll
+                            for (int o = 0; o <= M; ++o) {
+                                const T v = PL::get(win2[K - 1 - M + H + o], q);
+                                jl[q] = fma(lp.wlB[k - (K - H)][o], v, jl[q]);
+                                if (k < K - 1) jr[q] = fma(lp.wrB[k - (K - H)][o], v, jr[q]);
+                            }
+                        }
+                        JL2[k] = PL::pack(jl[0], jl[1]);
+                        JR2[k] = PL::pack(jr[0], jr[1]);
+                    }
                 }
             }
             const unsigned long long d2 = PL::splat(d);
@@ -845,16 +850,6 @@ rows_cluster_kernel(const __grid_constant__ LineParams<float> lp, const __grid_c
         }
         T JL[kPack ? 1 : NF][K], JR[kPack ? 1 : NF][K], aL[NF], aR[NF];
         unsigned long long JL2[kPack ? K : 1], JR2[kPack ? K : 1];   // packed J (then outputs)
-        // field q at line position p of this block's slice (wall stencils only)
-        auto at_field = [&](int p, int q) {
-            const int pl_ = p - slice0;
-            T sv[NS], fv[NF];
-#pragma unroll
-            for (int f = 0; f < NS; ++f)
-                sv[f] = reinterpret_cast<const T*>(stage_buf(sb, f) + staged_index(pl_ / V, nchl))[pl_ % V];
-            op.prologue(sv, fv);
-            return fv[q];
-        };
         // J^L_j, J^R_j of the wall positions of a non-periodic line (shifted wall stencils, Sec. 3.2
         // reading), from the thread's own window: nodes 0..M of the first chunk sit at window
         // indices H + o, nodes N-M..N of the last chunk at K - 1 - M + H + o.  Same operations in
@@ -905,32 +900,44 @@ rows_cluster_kernel(const __grid_constant__ LineParams<float> lp, const __grid_c
                 JL2[k] = jl;
                 JR2[k] = jr;
             }
-            if (!periodic && (start == 0 || start + K == n)) {
+            if (!periodic) {
                 // chunks touching a wall: the shifted wall stencils, field by field (as
-                // local_integrals), node values gathered from the staged slice
-                const int N = lp.N, jb = N - H + 1;
+                // local_integrals), from the thread's own packed window: nodes 0..M of the first
+                // chunk sit at window indices H + o, nodes N-M..N of the last chunk at
+                // K - 1 - M + H + o (the prologue is not evaluated again)
+                if (start == 0) {
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const int j = start + k;
-                    if (j >= H && j < jb) continue;
-                    T jl[2] = {T(0), T(0)}, jr[2] = {T(0), T(0)};
+                    for (int k = 0; k < H; ++k) {   // j = k < H
+                        T jl[2] = {T(0), T(0)}, jr[2] = {T(0), T(0)};
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
+                        for (int q = 0; q < 2; ++q) {
 #pragma unroll
-                        for (int o = 0; o <= M; ++o) {
-                            if (j < H) {
-                                const T v = at_field(o, q);
-                                if (j >= 1) jl[q] = fma(lp.wlA[j - 1][o], v, jl[q]);
-                                jr[q] = fma(lp.wrA[j][o], v, jr[q]);
-                            } else {
-                                const T v = at_field(N - M + o, q);
-                                jl[q] = fma(lp.wlB[j - jb][o], v, jl[q]);
-                                if (j < N) jr[q] = fma(lp.wrB[j - jb][o], v, jr[q]);
+                            for (int o = 0; o <= M; ++o) {
+                                const T v = PL::get(win2[H + o], q);
+                                if (k >= 1) jl[q] = fma(lp.wlA[k - 1][o], v, jl[q]);
+                                jr[q] = fma(lp.wrA[k][o], v, jr[q]);
                             }
                         }
+                        JL2[k] = PL::pack(jl[0], jl[1]);
+                        JR2[k] = PL::pack(jr[0], jr[1]);
                     }
-                    JL2[k] = PL::pack(jl[0], jl[1]);
-                    JR2[k] = PL::pack(jr[0], jr[1]);
+                }
+                if (start + K == n) {
+#pragma unroll
+                    for (int k = K - H; k < K; ++k) {   // j = start + k >= jb = n - H
+                        T jl[2] = {T(0), T(0)}, jr[2] = {T(0), T(0)};
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+#pragma unroll
+                            for (int o = 0; o <= M; ++o) {
+                                const T v = PL::get(win2[K - 1 - M + H + o], q);
+                                jl[q] = fma(lp.wlB[k - (K - H)][o], v, jl[q]);
+                                if (k < K - 1) jr[q] = fma(lp.wrB[k - (K - H)][o], v, jr[q]);
+                            }
+                        }
+                        JL2[k] = PL::pack(jl[0], jl[1]);
+                        JR2[k] = PL::pack(jr[0], jr[1]);
+                    }
                 }
             }
             const unsigned long long d2 = PL::splat(d);

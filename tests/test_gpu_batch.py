@@ -180,8 +180,11 @@ def test_batch_autotune_keeps_results_bitwise():
 @pytest.mark.parametrize("axis", [0, 1])
 def test_batch_helmholtz_apply_matches_oracle(bc, M, axis):
     # One batched line inversion per instance (molt_batch_helmholtz_apply) against the oracle's
-    # H_c of each instance, each with its own c (nu = h / sqrt(c) from 0.02 to 3), held to 1e-6 of
-    # the output's scale like the single-grid FP32 sweeps; a second call with other c reuses nothing.
+    # H_c of each instance, each with its own c (nu = h / sqrt(c) from 0.02 to 3); a second call
+    # with other c reuses nothing.  Held to 1e-6 of the input's scale: the recurrences sum values of
+    # the input's size, and on a Dirichlet line much shorter than the decay length 1/alpha (24
+    # nodes at nu = 0.02: alpha L = 0.46) the output is the remainder of those sums after the
+    # boundary correction, 60 times smaller than the input.
     from oracle.helmholtz import helmholtz_inverse
     from paper_1611_04214_gb300.inputs import spacing
     from paper_1611_04214_gb300.molt import Batch
@@ -202,7 +205,7 @@ def test_batch_helmholtz_apply_matches_oracle(bc, M, axis):
                 h = spacing(nx if axis == 0 else ny, Lx if axis == 0 else Ly, bc == "periodic")
                 f = b.unpack(b.pack(fields))[i].astype(np.float64)
                 ref = helmholtz_inverse(f, cs[i], h, bc, M, axis=1 if axis == 0 else 0)
-                err = np.abs(got[i] - ref).max() / np.abs(ref).max()
+                err = np.abs(got[i] - ref).max() / np.abs(f).max()
                 assert err < 1e-6, (i, nus[i], err)
 
 
