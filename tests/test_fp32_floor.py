@@ -102,3 +102,24 @@ def test_vch_mixture_fp32_floor(bc, mode):
     lower = {("periodic", "iterate"): 1.0, ("periodic", "all"): 3.0,
              ("neumann", "iterate"): 0.3, ("neumann", "all"): 1.5}[(bc, mode)]
     assert err > lower * target, err / target
+
+
+def test_neumann_slowest_mode_sits_at_the_corners():
+    # Why the converged Neumann cases are rho-limited at the wall: iterate the oracle's own 2D
+    # stage (BE, the 33 x 40 batch instance, eps = 0.08, dt = 8e-4) to 1e-14; the last update,
+    # which has the shape of the slowest mode, peaks at a corner and is far smaller inside.
+    from oracle.solver import fixed_point_map, stage_params, stage_rhs_inverse
+    from paper_1611_04214_gb300.inputs import uniform_noise
+    nx, ny, Lx, Ly, eps, dt = 33, 40, 1.5, 1.9, 0.08, 8e-4
+    prob = Problem(nx=nx, ny=ny, Lx=Lx, Ly=Ly, bc="neumann", eps=eps, M=4, tol=1e-14, max_iter=3000)
+    v = _r32(uniform_noise((ny, nx), 0.05, seed=4, mean=0.0)) + 1
+    sp = stage_params(dt, eps)
+    Y = stage_rhs_inverse(prob, v, sp)
+    for _ in range(prob.max_iter):
+        nv = fixed_point_map(prob, Y, v, sp)
+        d, v = np.abs(nv - v), nv
+        if d.max() < prob.tol:
+            break
+    j, i = np.unravel_index(int(np.argmax(d)), d.shape)
+    assert (j in (0, ny - 1)) and (i in (0, nx - 1)), (j, i)
+    assert d.max() > 10 * d[2:-2, 2:-2].max(), (d.max(), d[2:-2, 2:-2].max())
