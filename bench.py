@@ -47,9 +47,23 @@ KERNEL_FIELDS = {
     "cols_agg_H": (1, 0), "cols_agg_pass1": (1, 0), "cols_agg_pass3": (2, 0),
     "cols_final_H": (1, 1), "cols_final_pass1": (1, 2), "cols_final_pass3": (2, 2),
 }
-# DRAM bytes per launch measured by ncu for the kernels of this workload, keyed by kernel name;
-# filled only for kernels unchanged since their capture.
-NCU_TRAFFIC = {"rows_pass2": 1297.9e6}   # dram__bytes_read.sum + dram__bytes_write.sum, one 8192^2 launch
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured by ncu for the
+# kernels of the workloads, keyed by kernel slot, with the pass and kernel family captured; filled
+# only for kernels unchanged since their capture, and reported only when the autotuner kept the
+# same family for that pass.
+NCU_TRAFFIC = {"rows_pass2": (1296.96e6, 2, "rows_one_block")}        # one 8192^2 launch of rows P2
+VCH_NCU_TRAFFIC = {"rows_pass2": (365.67e6, 8, "rows_one_block")}     # one 4096^2 launch of rows vector P2
+
+
+def _traffic(table, slot, tuning):
+    """The captured DRAM bytes of a kernel slot, or None when the tuned family differs."""
+    if slot not in table:
+        return None
+    value, pass_, family = table[slot]
+    for t in tuning or []:
+        if t["pass"] == pass_ and t["chosen"] not in ("default", family):
+            return None
+    return value
 
 
 def _peaks():
@@ -452,6 +466,8 @@ def vch_leg(args, steps: int = 3):
     for prec in ("fp32", "fp64"):
         with Solver(nx=n, ny=n, Lx=L, Ly=L, bc=VCH["bc"], eps=VCH["eps"], quad_order=VCH["M"], precision=prec,
                     tol=1e-6, max_iter=args.iters) as s:
+            if prec == "fp32" and not args.no_autotune:
+                out["autotune"] = s.autotune()   # kernel families of every sweep, vector passes included
             # device-driven stage loops (the default) for the step time; host-driven loops with
             # per-kernel events for the kernel table
             u1, u2, infos, ms, launches, _ = run(s, False)
@@ -476,6 +492,7 @@ def vch_leg(args, steps: int = 3):
                 out["fp32"]["kernels"] = kern
                 out["fp32"]["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
                                            "unit": "GB/s", "frac": kern[dom]["gbs"] / peak,
+                                           "traffic": _traffic(VCH_NCU_TRAFFIC, dom, out.get("autotune")),
                                            "share_of_kernel_time": prof[dom][0] / total if total else None}
     d = max((fields["fp32"][c] - fields["fp64"][c]).abs().max().item() for c in range(2))
     out["max_abs_diff_fp32_vs_fp64"] = d
@@ -780,7 +797,7 @@ def run_ours(args, rank, world, dist):
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     total_prof_ms = sum(v[0] for v in prof.values())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get(dom), "kernel": dom, "algorithmic_bytes_per_launch": bytes_per_launch,
+                "traffic": _traffic(NCU_TRAFFIC, dom, tuning), "kernel": dom, "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_ms": avg_ms, "peak_source": f"{peak_kind} copy bandwidth",
                 "share_of_kernel_time": prof[dom][0] / total_prof_ms if total_prof_ms else None}
     kernels = {k: {"ms_total": v[0], "launches": v[1], "gbs": (

@@ -194,7 +194,8 @@ enum {
 };
 
 typedef struct {
-    int pass;          /* 0 = single H_c sweeps (rhs inverses), 1..4 = 2D iteration passes, 5, 6 = 1D passes */
+    int pass;          /* 0 = single H_c sweeps (rhs inverses), 1..4 = 2D iteration passes, 5, 6 = 1D passes,
+                          7, 8 = vector-model 2D passes 1 and 2, 9 = vector-model 1D pass a */
     int axis;          /* 0 = rows (x), 1 = columns (y) */
     int chosen;        /* MOLT_LAUNCH_* kept for this sweep (0: none available; the default stays) */
     int candidates;    /* entries of launch[] and ms[] filled */

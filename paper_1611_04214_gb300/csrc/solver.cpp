@@ -1331,14 +1331,19 @@ struct Solver final : molt_solver {
         molt::LineParams<T> lx, ly;
         if (!line_params(cx, 0, &lx) || (g.dim == 2 && !line_params(cy, 1, &ly))) return MOLT_ERR_ARG;
         const StageParams sp = stage_params(1e-3, p.eps);
-        Passes ps;
-        if (!make_passes(sp, &ps)) return MOLT_ERR_ARG;
+        Passes ps, pv;
+        double vc_in = 0.0, vc_out = 0.0;
+        if (!make_passes(sp, &ps) || !make_vch_passes(1e-3, &pv, &vc_in, &vc_out)) return MOLT_ERR_ARG;
+        // the vector passes are timed on the scalar work fields (f6 stands in for the second
+        // component), so tuning needs no vector workspace
         struct Entry { int pass, kind, axis; };
         static const Entry k2d[] = {{0, molt::OP_COPY, 0}, {0, molt::OP_COPY, 1}, {1, molt::OP_P1, 1},
-                                    {2, molt::OP_P2, 0},   {3, molt::OP_P3, 1},   {4, molt::OP_P4, 0}};
-        static const Entry k1d[] = {{0, molt::OP_COPY, 0}, {5, molt::OP_1A, 0}, {6, molt::OP_1B, 0}};
+                                    {2, molt::OP_P2, 0},   {3, molt::OP_P3, 1},   {4, molt::OP_P4, 0},
+                                    {7, molt::OP_V1, 1},   {8, molt::OP_V2, 0}};
+        static const Entry k1d[] = {{0, molt::OP_COPY, 0}, {5, molt::OP_1A, 0}, {6, molt::OP_1B, 0},
+                                    {9, molt::OP_V1A, 0}};
         const Entry* ebeg = g.dim == 2 ? k2d : k1d;
-        const Entry* eend = g.dim == 2 ? k2d + 6 : k1d + 3;
+        const Entry* eend = g.dim == 2 ? k2d + 8 : k1d + 4;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
             if (e0) cudaEventDestroy(e0);
@@ -1359,7 +1364,15 @@ struct Solver final : molt_solver {
                 case molt::OP_P3: a.in0 = f3; a.in1 = f4; a.out0 = f5; a.out1 = f6; break;
                 case molt::OP_P4: a.in0 = f5; a.in1 = f6; a.in2 = f4; a.in3 = Y; a.out0 = f1; break;
                 case molt::OP_1A: a.in0 = w; a.out0 = f1; break;
+                case molt::OP_V1: a.in0 = w; a.in1 = f6; a.out0 = f1; a.out1 = f2; break;
+                case molt::OP_V2: a.in0 = w; a.in1 = f6; a.in2 = f1; a.in3 = f2; a.out0 = f3; a.out1 = f4; break;
+                case molt::OP_V1A: a.in0 = w; a.in1 = f6; a.out0 = f1; break;
                 default: a.in0 = f1; a.in1 = Y; a.out0 = f2; break;   // OP_1B
+            }
+            if (en.kind == molt::OP_V1 || en.kind == molt::OP_V2 || en.kind == molt::OP_V1A) {
+                a.vs = pv.vs;
+                a.beta = pv.beta;
+                a.comp = 0;
             }
             const molt::LineParams<T>& lp = en.axis == 0 ? lx : ly;
             std::vector<int> cand = en.axis == 0
