@@ -382,9 +382,10 @@ molt_status molt_batch_step(molt_batch* batch, float* u_dev, const double* dt, m
  * instance of the batch along one axis (0 = x, each row; 1 = y, each column), in one launch
  * sequence over all instances: out = H_{c_i} in, instance by instance, with the batch's boundary
  * condition and M.  c: host array of `count` values (> 0; alpha = c^(-1/2)); in, out: packed
- * device fields (FP32, layout of molt_batch_create), not aliased.  The parameters of c are built
- * and uploaded only when c changes (the call then synchronizes `stream`); later steps reload their
- * own.  Asynchronous otherwise.  Errors: MOLT_ERR_ARG, MOLT_ERR_CUDA. */
+ * device fields (FP32, layout of molt_batch_create), not aliased.  Per axis the batch keeps the
+ * line parameters of the last two arrays c it swept with; another c is built on the host and
+ * uploaded (the call then synchronizes `stream`).  Later steps reload their own parameters.
+ * Asynchronous otherwise.  Errors: MOLT_ERR_ARG, MOLT_ERR_CUDA. */
 molt_status molt_batch_helmholtz_apply(molt_batch* batch, int axis, const double* c, const float* in_dev,
                                        float* out_dev, void* stream);
 
@@ -404,6 +405,44 @@ molt_status molt_batch_autotune(molt_batch* batch, const double* dt, void* strea
 /* Set the schedule of the batched passes directly: grid_rows / grid_cols blocks per row / column
  * launch (0 = one block per work item).  Results do not depend on it.  Errors: MOLT_ERR_ARG. */
 molt_status molt_batch_set_schedule(molt_batch* batch, int grid_rows, int grid_cols);
+
+/* ---- Three-dimensional split stage (the extension of Sec. 5's splitting to 3D) ------------
+ * The paper only remarks that its dimensional splitting extends to three dimensions.  The
+ * reading implemented here: with L_a = I - c d_aa per axis, I - c Lap = L_x L_y L_z - P, and with
+ * H_a = L_a^{-1}, D_a = I - H_a, M^{-1} = H_x H_y H_z, the splitting remainder is
+ * M^{-1} P = X = D_x D_y + D_x D_z + D_y D_z - 2 D_x D_y D_z (X = D_x D_y in 2D, Eq.
+ * CH_2D_Doperator1); the 2D fixed-point iteration of Sec. 5.1 then holds with X in place of
+ * D_x D_y.  FP32 fields of nz * ny * nx floats, row-major with x fastest, periodic or Neumann
+ * lines (the grid conventions of molt_grid_create per axis).  Each iteration is a sequence of
+ * single line sweeps over the whole field (not fused).  Errors of these calls are reported by
+ * molt_last_error(NULL). */
+typedef struct molt_solver3d molt_solver3d;
+
+/* nx, ny in [M + 2, 1024] (the y lines run as a batch of nz slabs, molt_batch_create), nz >= M + 2;
+ * params: precision must be MOLT_FP32; eps, M, tol and max_iter as molt_solver_create.  The
+ * solver owns 17 fields of workspace, the column scan scratch of the z lines and an internal
+ * batch of nz slabs.  Errors: MOLT_ERR_ARG, MOLT_ERR_UNSUPPORTED (Dirichlet, FP64),
+ * MOLT_ERR_OOM, MOLT_ERR_CUDA. */
+molt_status molt_solver3d_create(molt_solver3d** solver, int nx, int ny, int nz, double Lx, double Ly,
+                                 double Lz, molt_bc bc, const molt_params* params);
+molt_status molt_solver3d_destroy(molt_solver3d* solver);
+
+/* One time step in place on the device field u_dev (u of the paper): MOLT_BE, or MOLT_BDF2 with a
+ * BE start repeated whenever dt changes.  The stage's stopping rule is molt_step's (FP32 floor
+ * and stall rule); info (may be NULL) receives iterations, residual and tolerance used.
+ * Synchronizes `stream` once per iteration (host-driven loop).  Errors: MOLT_ERR_ARG,
+ * MOLT_ERR_UNSUPPORTED (other schemes), MOLT_ERR_NOT_CONVERGED (the field holds the last
+ * iterate), MOLT_ERR_CUDA. */
+molt_status molt_solver3d_step(molt_solver3d* solver, float* u_dev, double dt, molt_scheme scheme, void* stream,
+                               molt_step_info* info);
+
+/* One line inversion H_c (Sec. 3) of every line along axis 0 (x), 1 (y) or 2 (z); in_dev and
+ * out_dev distinct.  Errors: MOLT_ERR_ARG, MOLT_ERR_CUDA. */
+molt_status molt_solver3d_apply(molt_solver3d* solver, int axis, double c, const float* in_dev, float* out_dev,
+                                void* stream);
+
+/* Kernels this 3D solver has launched (its internal batch's sweeps counted as 3 each). */
+long long molt_solver3d_launches(const molt_solver3d* solver);
 
 /* Last error message of `solver` (or of the last failed create/ABI call when NULL). */
 const char* molt_last_error(const molt_solver* solver);

@@ -377,7 +377,8 @@ struct molt_batch {
     LoopState* ls_host = nullptr;
     int* active_host = nullptr;
     std::vector<double> tau_loaded;     // taus whose parameters sit in lps / stages
-    std::vector<double> applied[2];     // c of the batched sweep whose parameters sit in slot LIX / LIY
+    std::vector<double> applied[4];     // c of the batched sweeps whose parameters sit in each slot
+    int applied_last[2] = {0, 2};       // slot (LIX, LIY) of each axis written last by a batched sweep
     bool have_prev = false;
     std::vector<double> dt_prev;
     struct Graph {
@@ -548,14 +549,14 @@ cudaError_t iteration_any(molt_batch* b, cudaStream_t st) {
     }
 }
 
-// One line inversion H_c of every instance along one axis (slot LIX for x, LIY for y holds the
-// parameters of c_i while it runs).
+// One line inversion H_c of every instance along one axis, with the parameters of c_i held in
+// `slot` (LIX or LOX for x, LIY or LOY for y) while it runs.
 template <int M>
-cudaError_t apply_pass(molt_batch* b, int axis, const float* in, float* out, cudaStream_t st) {
+cudaError_t apply_pass(molt_batch* b, int axis, int slot, const float* in, float* out, cudaStream_t st) {
     molt::OpCopy<float> c{};
     c.in = in;
     c.out = out;
-    return axis == 0 ? rows_pass<M>(b, LIX, c, false, st) : cols_pass<M>(b, LIY, c, false, st);
+    return axis == 0 ? rows_pass<M>(b, slot, c, false, st) : cols_pass<M>(b, slot, c, false, st);
 }
 
 cudaError_t lin(molt_batch* b, float* out, const float* x0, double c0, const float* x1, double c1, double c4,
@@ -657,8 +658,7 @@ molt_status load_params(molt_batch* b, const std::vector<double>& tau, cudaStrea
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
         return batch_fail(MOLT_ERR_CUDA, std::string("parameter upload: ") + cudaGetErrorString(e));
     b->tau_loaded = tau;
-    b->applied[0].clear();
-    b->applied[1].clear();
+    for (std::vector<double>& a : b->applied) a.clear();
     return MOLT_OK;
 }
 
@@ -941,10 +941,16 @@ molt_status molt_batch_helmholtz_apply(molt_batch* b, int axis, const double* c,
     if (axis != 0 && axis != 1) return batch_fail(MOLT_ERR_ARG, "axis must be 0 (x) or 1 (y)");
     if (in == out) return batch_fail(MOLT_ERR_ARG, "in and out must not alias");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int slot = axis == 0 ? LIX : LIY;
+    // two parameter slots per axis: a caller alternating between two values of c (the inner and
+    // outer inversions of a stage) uploads each once
+    const int pair[2] = {axis == 0 ? LIX : LIY, axis == 0 ? LOX : LOY};
     std::vector<double> cv(c, c + b->count);
+    int slot = -1;
+    for (int s : pair)
+        if (cv == b->applied[s]) slot = s;
     cudaError_t e = cudaSuccess;
-    if (cv != b->applied[axis]) {
+    if (slot < 0) {
+        slot = b->applied_last[axis] == pair[0] ? pair[1] : pair[0];
         for (int i = 0; i < b->count; ++i) {
             const molt_instance& d = b->desc[i];
             if (!(cv[i] > 0.0) || !std::isfinite(cv[i]))
@@ -964,13 +970,14 @@ molt_status molt_batch_helmholtz_apply(molt_batch* b, int axis, const double* c,
         e = cudaMemcpyAsync(b->lps, b->lps_host, sizeof(LineParams<float>) * 4 * b->count, cudaMemcpyHostToDevice,
                             st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        b->applied[axis] = e == cudaSuccess ? cv : std::vector<double>();
+        b->applied[slot] = e == cudaSuccess ? cv : std::vector<double>();
+        b->applied_last[axis] = slot;
     }
     if (e == cudaSuccess) {
         switch (b->M) {
-            case 2: e = apply_pass<2>(b, axis, in, out, st); break;
-            case 4: e = apply_pass<4>(b, axis, in, out, st); break;
-            default: e = apply_pass<6>(b, axis, in, out, st); break;
+            case 2: e = apply_pass<2>(b, axis, slot, in, out, st); break;
+            case 4: e = apply_pass<4>(b, axis, slot, in, out, st); break;
+            default: e = apply_pass<6>(b, axis, slot, in, out, st); break;
         }
     }
     if (e != cudaSuccess) return batch_fail(MOLT_ERR_CUDA, std::string("batched sweep: ") + cudaGetErrorString(e));

@@ -31,6 +31,8 @@ EXPORTS = [
     "molt_step_adaptive",
     "molt_vch_step", "molt_fma_throughput_probe", "molt_helmholtz_rows_tc", "molt_vch_step_adaptive",
     "molt_batch_autotune", "molt_batch_set_schedule", "molt_autotune", "molt_batch_helmholtz_apply",
+    "molt_solver3d_create", "molt_solver3d_destroy", "molt_solver3d_step", "molt_solver3d_apply",
+    "molt_solver3d_launches",
 ]
 EXECUTION = {"host_loop": 0, "graph": 1}
 PROFILE_SLOTS = 32
@@ -127,6 +129,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_batch_autotune": ([VP, ctypes.POINTER(D), VP, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "molt_batch_set_schedule": ([VP, I, I], I),
         "molt_batch_helmholtz_apply": ([VP, I, ctypes.POINTER(D), VP, VP, VP], I),
+        "molt_solver3d_create": ([ctypes.POINTER(VP), I, I, I, D, D, D, I, ctypes.POINTER(_Params)], I),
+        "molt_solver3d_destroy": ([VP], I),
+        "molt_solver3d_step": ([VP, VP, D, I, VP, ctypes.POINTER(_StepInfo)], I),
+        "molt_solver3d_apply": ([VP, I, D, VP, VP, VP], I),
+        "molt_solver3d_launches": ([VP], ctypes.c_longlong),
         "molt_autotune": ([P, VP, ctypes.POINTER(_Tuning), I, ctypes.POINTER(I)], I),
         "molt_batch_step": ([VP, VP, ctypes.POINTER(D), I, VP, ctypes.POINTER(I), ctypes.POINTER(D),
                              ctypes.POINTER(I)], I),
@@ -506,6 +513,62 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.molt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Solver3D:
+    """The 3D split stage solver of the C ABI (molt_solver3d_*): FP32 fields [nz][ny][nx]."""
+
+    def __init__(self, nx: int, ny: int, nz: int, Lx: float = 6.283185307179586, Ly: float = 6.283185307179586,
+                 Lz: float = 6.283185307179586, bc: str = "periodic", eps: float = 0.1, quad_order: int = 4,
+                 tol: float = 1e-10, max_iter: int = 500):
+        lib = load_library()
+        self._lib = lib
+        self.shape = (nz, ny, nx)
+        self._params = _Params(eps, quad_order, PRECISION["fp32"], tol, max_iter)
+        h = ctypes.c_void_p()
+        _check(lib.molt_solver3d_create(ctypes.byref(h), nx, ny, nz, Lx, Ly, Lz, BC[bc], ctypes.byref(self._params)))
+        self._h = h
+
+    def _field(self, t):
+        if not t.is_cuda or t.dtype.itemsize != 4 or not t.is_contiguous() or tuple(t.shape) != self.shape:
+            raise ValueError(f"expected a contiguous CUDA float32 tensor of shape {self.shape}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def step(self, u, dt: float, scheme: str = "be", stream=None, raise_on_nonconvergence: bool = True) -> StepInfo:
+        info = _StepInfo()
+        st = self._lib.molt_solver3d_step(self._h, self._field(u), float(dt), SCHEME[scheme], _stream_handle(stream),
+                                          ctypes.byref(info))
+        out = StepInfo(info.status, info.stages, list(info.iters)[: max(info.stages, 0)], info.total_iters,
+                       info.residual, info.tol_used)
+        if st == MOLT_ERR_NOT_CONVERGED and not raise_on_nonconvergence:
+            return out
+        _check(st, None)
+        return out
+
+    def helmholtz_apply(self, axis: int, c: float, inp, out, stream=None):
+        """out = H_c inp along axis 0 (x), 1 (y) or 2 (z)."""
+        _check(self._lib.molt_solver3d_apply(self._h, int(axis), float(c), self._field(inp), self._field(out),
+                                             _stream_handle(stream)))
+
+    def kernel_launches(self) -> int:
+        return int(self._lib.molt_solver3d_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.molt_solver3d_destroy(self._h)
             self._h = None
 
     def __del__(self):
