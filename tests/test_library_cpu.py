@@ -22,7 +22,7 @@ def lib():
 def _declared_symbols():
     with open(os.path.join(ROOT, "include", "molt.h")) as fh:
         text = fh.read()
-    decl = re.compile(r"^\s*(?:molt_status|void|const char\s*\*|long long)\s+(molt_[a-z_]+)\s*\(", re.M)
+    decl = re.compile(r"^\s*(?:molt_status|void|const char\s*\*|long long)\s+(molt_[a-z0-9_]+)\s*\(", re.M)
     return sorted(set(decl.findall(text)))
 
 
