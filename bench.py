@@ -620,6 +620,51 @@ CONFIG2 = dict(name="ch2d_1024_neumann_bdf2_converged", n=1024, eps=0.05, dt=1e-
                max_iter=20000, M=4, bc="neumann", amp=0.05, seed=0)
 
 
+SPLIT3D = dict(name="ch3d_256_be_periodic", n=256, eps=0.05, dt=1e-4, M=4, amp=0.05, seed=0, iters=10, steps=3)
+# per 3D iteration: 21 single-field line sweeps (8 B/pt each), 4 linear combinations of 4 fields
+# (20 B/pt), the cubic (8 B/pt) and two max reductions (8 B/pt); per stage the rhs inverse's 6 sweeps
+SPLIT3D_BYTES_ITER, SPLIT3D_BYTES_RHS = 21 * 8 + 4 * 20 + 8 + 2 * 8, 6 * 8
+SPLIT3D_SWEEPS_ITER, SPLIT3D_SWEEPS_RHS = 21, 6
+
+
+def split3d_leg():
+    """The 3D split stage (molt_solver3d_*; the extension of the splitting that Sec. 5 remarks on)
+    on a 256^3 periodic grid over [0, 2pi]^3: eps = 0.05, BE dt = 1e-4, u0 = 0.05 U[-1, 1]
+    (SplitMix64, seed 0), a fixed 10 fixed-point iterations per stage.  Line-sweep points per second
+    and the step's algorithmic HBM fraction; the passes are not fused."""
+    import torch
+
+    from paper_1611_04214_gb300.inputs import uniform_noise
+    from paper_1611_04214_gb300.molt import Solver3D
+    c = SPLIT3D
+    n = c["n"]
+    peak, _ = _peaks()
+    u0 = uniform_noise((n * n, n), c["amp"], seed=c["seed"]).reshape(n, n, n).astype("float32")
+    with Solver3D(n, n, n, bc="periodic", eps=c["eps"], quad_order=c["M"], tol=1e-30, max_iter=c["iters"]) as s:
+        u = torch.tensor(u0, device="cuda")
+        s.step(u, c["dt"], "be", raise_on_nonconvergence=False)     # warm-up
+        torch.cuda.synchronize()
+        k0 = s.kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        infos = [s.step(u, c["dt"], "be", raise_on_nonconvergence=False) for _ in range(c["steps"])]
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / c["steps"]
+        launches = (s.kernel_launches() - k0) / c["steps"]
+    its = sum(i.iters[0] for i in infos) / c["steps"]
+    pts = n ** 3
+    sweeps = (SPLIT3D_SWEEPS_RHS + SPLIT3D_SWEEPS_ITER * its) * pts
+    step_bytes = (SPLIT3D_BYTES_RHS + SPLIT3D_BYTES_ITER * its) * pts
+    torch.cuda.empty_cache()
+    return {"workload": c["name"], "grid": [n, n, n], "eps": c["eps"], "dt": c["dt"], "scheme": "be",
+            "fixed_point_iters_per_stage": c["iters"], "initial_state": "0.05 U[-1,1], SplitMix64 seed 0",
+            "ms_per_step": ms, "line_sweep_gpts": sweeps / (ms * 1e-3) / 1e9,
+            "hbm_frac_step_algorithmic": step_bytes / (ms * 1e-3) / 1e9 / peak,
+            "algorithmic_bytes_per_point_iteration": SPLIT3D_BYTES_ITER, "kernel_launches_per_step": launches,
+            "final_residual": infos[-1].residual}
+
+
 def converged_leg():
     """The 1024^2 Neumann BDF2 workload in full (eps = 0.05, dt = 1e-4, 200 steps, u0 = 0.05 U[-1,1]
     seed 0, BE start), every stage iterated to the tolerance 1e-6 (the tolerance of the paper's 2D
@@ -870,6 +915,12 @@ def run_ours(args, rank, world, dist):
                 vch = vch_leg(args)
             except Exception as exc:   # a side leg records its failure instead of costing the main line
                 vch = {"error": f"{type(exc).__name__}: {exc}"}
+        split3d = None
+        if not args.skip_3d:
+            try:
+                split3d = split3d_leg()
+            except Exception as exc:
+                split3d = {"error": f"{type(exc).__name__}: {exc}"}
         last = infos[-1]
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                   "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -885,7 +936,7 @@ def run_ours(args, rank, world, dist):
                   "ms_per_step_graph_mode": graph_ms, "fp32_vs_fp64": fp64, "batched": batched,
                   "sweep_microbench": sweeps_mb, "vector_ch": vch, "kernels": kernels,
                   "converged_l2_resident": converged, "oracle_parity": parity, "fma_probe": fp64_probe,
-                  "autotune": tuning}
+                  "autotune": tuning, "split3d": split3d}
         if parity and "config3_crop1024_fp32" in parity:
             result["config3_crop_err_vs_oracle"] = {p_: parity[f"config3_crop1024_{p_}"]["max_rel_err_v"]
                                                     for p_ in ("fp32", "fp64")}
@@ -905,6 +956,7 @@ def main():
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched-instances leg")
     ap.add_argument("--skip-sweeps", action="store_true", help="skip the single-sweep microbenchmark")
     ap.add_argument("--skip-vch", action="store_true", help="skip the vector Cahn-Hilliard leg")
+    ap.add_argument("--skip-3d", action="store_true", help="skip the 3D split-stage leg")
     ap.add_argument("--skip-converged", action="store_true", help="skip the converged 1024^2 Neumann BDF2 leg")
     ap.add_argument("--skip-oracle", action="store_true", help="skip the host-core oracle (cpu_baseline, parity)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel families (no molt_autotune)")
