@@ -957,6 +957,8 @@ def main():
     ap.add_argument("--skip-sweeps", action="store_true", help="skip the single-sweep microbenchmark")
     ap.add_argument("--skip-vch", action="store_true", help="skip the vector Cahn-Hilliard leg")
     ap.add_argument("--skip-3d", action="store_true", help="skip the 3D split-stage leg")
+    ap.add_argument("--split3d-only", action="store_true",
+                    help="run only the 3D split-stage leg and print its JSON (for profiling)")
     ap.add_argument("--skip-converged", action="store_true", help="skip the converged 1024^2 Neumann BDF2 leg")
     ap.add_argument("--skip-oracle", action="store_true", help="skip the host-core oracle (cpu_baseline, parity)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel families (no molt_autotune)")
@@ -989,6 +991,10 @@ def main():
     if args.vch_only:
         if rank == 0:
             print(json.dumps({"vector_ch": vch_leg(args)}), flush=True)
+        return
+    if args.split3d_only:
+        if rank == 0:
+            print(json.dumps({"split3d": split3d_leg()}), flush=True)
         return
     if dist:
         dist.barrier()

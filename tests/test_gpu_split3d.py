@@ -4,8 +4,8 @@
   the input's scale (the FP32 single-sweep bar); the z lines of 136 nodes span two column tiles
   with a ragged tail, the y lines run through the internal batch of z slabs.
 * Steps with the same fixed iteration count on both sides (BE and BDF2), held to the FP32 bar
-  1e-6 of max|u + 1| (tests/_parity.py); a converged periodic run keeps the mass and is held to
-  the rho-limited bound against the converged oracle.
+  1e-6 of max|u + 1| (tests/_parity.py); a converged periodic run keeps the mass and meets the
+  same bar against the converged oracle.
 """
 import numpy as np
 import pytest
@@ -88,11 +88,12 @@ def test_3d_steps_fixed_iterations(bc, scheme):
 
 def test_3d_converged_periodic_mass():
     # Converged steps: the GPU's FP32 stopping rule (tolerance floored at its rounding level)
-    # against the oracle converged to 1e-12; held to the rho-limited bound of tests/_parity.py
-    # with rho observed by the oracle, and periodic mass kept to rounding.
+    # against the oracle converged to 1e-12, held to the FP32 bar (the iteration contracts with
+    # rho = 0.81 here, so the FP32 fixed point sits well inside it), and periodic mass kept to
+    # rounding.
     shape = (20, 24, 28)
     got, ref, ig, io, prob, u0, rho = _run_both(shape, "periodic", "bdf2", 3, 2e-3, 0.15, 1e-10, 3000, seed=9,
                                                 oracle_tol=1e-12)
     assert abs(mass(prob, got) - mass(prob, u0.astype(np.float64))) < 1e-5 * prob.Lx * prob.Ly * prob.Lz
     check_fp32("split3d_28x24x20_periodic_bdf2_3steps_converged", got, ref, np.abs(ref + 1).max(), rho,
-               rho_limited_w=np.abs(ref).max(), iters_gpu=ig, iters_oracle=io)
+               iters_gpu=ig, iters_oracle=io)
