@@ -418,7 +418,8 @@ molt_status molt_batch_set_schedule(molt_batch* batch, int grid_rows, int grid_c
  * molt_last_error(NULL). */
 typedef struct molt_solver3d molt_solver3d;
 
-/* nx, ny in [M + 2, 1024] (the y lines run as a batch of nz slabs, molt_batch_create), nz >= M + 2;
+/* nx, ny in [M + 2, 1024] (the y lines run as a batch of nz slabs, molt_batch_create), nz in
+ * [M + 2, 2^20];
  * params: precision must be MOLT_FP32; eps, M, tol and max_iter as molt_solver_create.  The
  * solver owns 17 fields of workspace, the column scan scratch of the z lines and an internal
  * batch of nz slabs.  Errors: MOLT_ERR_ARG, MOLT_ERR_UNSUPPORTED (Dirichlet, FP64),
@@ -437,7 +438,8 @@ molt_status molt_solver3d_step(molt_solver3d* solver, float* u_dev, double dt, m
                                molt_step_info* info);
 
 /* One line inversion H_c (Sec. 3) of every line along axis 0 (x), 1 (y) or 2 (z); in_dev and
- * out_dev distinct.  Errors: MOLT_ERR_ARG, MOLT_ERR_CUDA. */
+ * out_dev distinct.  Synchronizes `stream` to read the column kernels' wait status.  Errors:
+ * MOLT_ERR_ARG, MOLT_ERR_CUDA (also when a bounded wait for a tile copy ran out). */
 molt_status molt_solver3d_apply(molt_solver3d* solver, int axis, double c, const float* in_dev, float* out_dev,
                                 void* stream);
 

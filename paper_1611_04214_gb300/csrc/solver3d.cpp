@@ -238,8 +238,8 @@ molt_status molt_solver3d_create(molt_solver3d** out, int nx, int ny, int nz, do
     if (!(p->eps > 0.0) || !std::isfinite(p->eps) || !(p->tol > 0.0) || p->max_iter < 1)
         return fail3(MOLT_ERR_ARG, "eps and tol must be positive, max_iter >= 1");
     const int lo = p->quad_order + 2;
-    if (nx < lo || ny < lo || nz < lo || nx > 1024 || ny > 1024)
-        return fail3(MOLT_ERR_ARG, "nx, ny must lie in [M + 2, 1024] and nz >= M + 2");
+    if (nx < lo || ny < lo || nz < lo || nx > 1024 || ny > 1024 || nz > (1 << 20))
+        return fail3(MOLT_ERR_ARG, "nx, ny must lie in [M + 2, 1024] and nz in [M + 2, 2^20]");
     if (!(Lx > 0.0) || !(Ly > 0.0) || !(Lz > 0.0) || !std::isfinite(Lx) || !std::isfinite(Ly) || !std::isfinite(Lz))
         return fail3(MOLT_ERR_ARG, "Lx, Ly, Lz must be finite and > 0");
     molt_solver3d* s = new (std::nothrow) molt_solver3d();
@@ -315,7 +315,11 @@ molt_status molt_solver3d_apply(molt_solver3d* s, int axis, double c, const floa
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(s->status, 0, sizeof(unsigned), st);
     if (e == cudaSuccess) e = sweep3(s, axis, c, in, out, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->status_host, s->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail3(MOLT_ERR_CUDA, std::string("3D sweep: ") + cudaGetErrorString(e));
+    if (*s->status_host)
+        return fail3(MOLT_ERR_CUDA, "a column kernel's bounded wait for a tile copy ran out; the output is incomplete");
     return MOLT_OK;
 }
 
