@@ -844,15 +844,20 @@ cudaError_t energy_mass(const T* u, int nx, int ny, int bc, double hx, double hy
 namespace molt {
 namespace detail {
 
-// max |a - b| over n values, widened to FP64; the non-negative FP64 bit patterns order like the
-// values, so blocks combine by an integer atomicMax on *out (zeroed by the caller).
+// max |a - b| over n values.  Each |a_i - b_i| and the running max are formed in the field
+// precision: rounding is monotone, so the FP32 result is the FP32 rounding of the exact maximum
+// (for the nearby iterates a residual compares, the difference is exact), and the loop stays a
+// memory stream instead of an FP64 one.  The thread's max is widened to FP64 for the combine; the
+// non-negative FP64 bit patterns order like the values, so blocks combine by an integer atomicMax
+// on *out (zeroed by the caller).
 template <typename T>
 __global__ void max_abs_diff_kernel(const T* __restrict__ a, const T* __restrict__ b, long long n,
                                     unsigned long long* out) {
-    double m = 0.0;
+    T mt = T(0);
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<long long>(gridDim.x) * blockDim.x)
-        m = fmax(m, fabs(static_cast<double>(a[i]) - static_cast<double>(b[i])));
+        mt = fmax(mt, fabs(a[i] - b[i]));
+    double m = static_cast<double>(mt);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
     __shared__ double s[32];
