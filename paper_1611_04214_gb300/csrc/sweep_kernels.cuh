@@ -30,9 +30,8 @@ __device__ __forceinline__ void rows_body(const LineParams<T>& lp, const Op& op,
     const int lib = tid >> tl_log2;
     const int t = tid & (TL - 1);
 
-    // ---- stage the block's lines (prologue): batches of U independent loads per thread (16 for
-    // single-field ops, whose short lines otherwise leave too few bytes in flight per SM) ----
-    constexpr int U = NF == 1 ? 16 : 8;
+    // ---- stage the block's lines (prologue): batches of U independent loads per thread ----
+    constexpr int U = 8;
     for (int l = 0; l < lpb; ++l) {
         const int gl = line0 + l;
         if (gl >= nlines) break;
