@@ -17,7 +17,8 @@
 // the rows of the [nz * ny][nx] view, z lines the columns of the [nz][ny * nx] view, and the y
 // lines of each z slab are the columns of one instance of an internal batch of nz slabs
 // (molt_batch_helmholtz_apply), so every sweep is one launch sequence over the whole field.
-// The passes are not fused: 21 single-field sweeps and 4 linear combinations per iteration.
+// By linearity of H_x, Q and A need one x sweep each after combining their y and z products.
+// The passes are not fused: 15 single-field sweeps and 7 linear combinations per iteration.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -101,21 +102,31 @@ cudaError_t sweep3(molt_solver3d* s, int axis, double c, const float* in, float*
     return molt::sweep<float>(1, lp, molt::OP_COPY, a, s->nx * s->ny, s->nz, &s->cs, s->red, st, &s->launches);
 }
 
-// The products of f by the line inverses at one c, into t[0..5]: XY = H_x H_y f, YZ = H_y H_z f,
-// XZ = H_x H_z f, XYZ = H_x H_y H_z f, and the intermediates H_z f, H_y f.
-cudaError_t products(molt_solver3d* s, double c, const float* f, cudaStream_t st) {
-    float* XY = s->t[0];
-    float* YZ = s->t[1];
-    float* XZ = s->t[2];
-    float* XYZ = s->t[3];
-    float* Z = s->t[4];
-    float* Yf = s->t[5];
+// The y and z products of f at one c: t[4] = H_z f, t[5] = H_y f, t[1] = H_y H_z f.  The x
+// sweeps come after a combination: by linearity of H_x,
+//   Q f = H_x H_y f + H_x H_z f + H_y H_z f - 2 H_x H_y H_z f = H_x (H_y f + H_z f - 2 H_y H_z f) + H_y H_z f,
+//   A f = 3 H_x H_y H_z f - H_x H_y f - H_x H_z f - H_y H_z f = H_x (3 H_y H_z f - H_y f - H_z f) - H_y H_z f,
+// so each takes one x sweep instead of three.
+cudaError_t yz_products(molt_solver3d* s, double c, const float* f, cudaStream_t st) {
     cudaError_t e;
-    if ((e = sweep3(s, 2, c, f, Z, st)) != cudaSuccess || (e = sweep3(s, 1, c, f, Yf, st)) != cudaSuccess ||
-        (e = sweep3(s, 1, c, Z, YZ, st)) != cudaSuccess || (e = sweep3(s, 0, c, Yf, XY, st)) != cudaSuccess ||
-        (e = sweep3(s, 0, c, Z, XZ, st)) != cudaSuccess || (e = sweep3(s, 0, c, YZ, XYZ, st)) != cudaSuccess)
+    if ((e = sweep3(s, 2, c, f, s->t[4], st)) != cudaSuccess || (e = sweep3(s, 1, c, f, s->t[5], st)) != cudaSuccess)
         return e;
-    return cudaSuccess;
+    return sweep3(s, 1, c, s->t[4], s->t[1], st);
+}
+
+// out = x_part + sign * H_y H_z f with x_part = H_x (a (H_y f + H_z f) + b H_y H_z f): Q f for
+// (a, b, sign) = (1, -2, +1), A f for (-1, 3, -1).  Uses t[0], t[1], t[2], t[4], t[5].
+cudaError_t q_or_a(molt_solver3d* s, double c, const float* f, double a, double b, double sign, double scale,
+                   float* out, cudaStream_t st) {
+    const long long n = static_cast<long long>(s->n);
+    cudaError_t e;
+    if ((e = yz_products(s, c, f, st)) != cudaSuccess ||
+        (e = molt::lincomb<float>(s->t[0], n, s->t[5], a, s->t[4], a, s->t[1], b, nullptr, 0.0, 0.0, st,
+                                  &s->launches)) != cudaSuccess ||
+        (e = sweep3(s, 0, c, s->t[0], s->t[2], st)) != cudaSuccess)
+        return e;
+    return molt::lincomb<float>(out, n, s->t[2], scale, s->t[1], sign * scale, nullptr, 0.0, nullptr, 0.0, 0.0, st,
+                                &s->launches);
 }
 
 // out = H_x H_y H_z f (tmp: two scratch fields).
@@ -134,29 +145,17 @@ namespace {
 // One fixed-point iteration: wn = Y + w + H_ox H_oy H_oz [beta A_i g] - Q_o [Q_i w].
 cudaError_t iteration3(molt_solver3d* s, const molt::StageParams& sp, cudaStream_t st) {
     const long long n = static_cast<long long>(s->n);
-    float* tb = s->t[6];   // beta A_i g, then H_ox H_oy H_oz of it
+    float* tb = s->t[6];   // beta A_i g
     float* qi = s->t[7];   // Q_i w
     float* qo = s->t[8];   // Q_o Q_i w
-    float* hb = s->t[9];
+    float* hb = s->t[9];   // H_ox H_oy H_oz (beta A_i g)
     cudaError_t e;
     // g = w^3 + (lam - 3) w
-    if ((e = molt::cubic<float>(s->g, n, s->w, 0.0, sp.lam - 3.0, st, &s->launches)) != cudaSuccess) return e;
-    // beta A_i g = beta (3 XYZ - XY - YZ - XZ) g
-    if ((e = products(s, sp.c_in, s->g, st)) != cudaSuccess) return e;
-    if ((e = molt::lincomb<float>(tb, n, s->t[3], 3.0 * sp.beta, s->t[0], -sp.beta, s->t[1], -sp.beta, s->t[2],
-                                  -sp.beta, 0.0, st, &s->launches)) != cudaSuccess)
-        return e;
-    // Q_i w = (XY + YZ + XZ - 2 XYZ) w
-    if ((e = products(s, sp.c_in, s->w, st)) != cudaSuccess) return e;
-    if ((e = molt::lincomb<float>(qi, n, s->t[0], 1.0, s->t[1], 1.0, s->t[2], 1.0, s->t[3], -2.0, 0.0, st,
-                                  &s->launches)) != cudaSuccess)
-        return e;
-    // H_ox H_oy H_oz (beta A_i g)
-    if ((e = triple(s, sp.c_out, tb, hb, s->t[4], s->t[5], st)) != cudaSuccess) return e;
-    // Q_o Q_i w
-    if ((e = products(s, sp.c_out, qi, st)) != cudaSuccess) return e;
-    if ((e = molt::lincomb<float>(qo, n, s->t[0], 1.0, s->t[1], 1.0, s->t[2], 1.0, s->t[3], -2.0, 0.0, st,
-                                  &s->launches)) != cudaSuccess)
+    if ((e = molt::cubic<float>(s->g, n, s->w, 0.0, sp.lam - 3.0, st, &s->launches)) != cudaSuccess ||
+        (e = q_or_a(s, sp.c_in, s->g, -1.0, 3.0, -1.0, sp.beta, tb, st)) != cudaSuccess ||
+        (e = q_or_a(s, sp.c_in, s->w, 1.0, -2.0, 1.0, 1.0, qi, st)) != cudaSuccess ||
+        (e = triple(s, sp.c_out, tb, hb, s->t[4], s->t[5], st)) != cudaSuccess ||
+        (e = q_or_a(s, sp.c_out, qi, 1.0, -2.0, 1.0, 1.0, qo, st)) != cudaSuccess)
         return e;
     return molt::lincomb<float>(s->wn, n, s->Y, 1.0, s->w, 1.0, hb, 1.0, qo, -1.0, 0.0, st, &s->launches);
 }
