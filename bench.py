@@ -621,10 +621,10 @@ CONFIG2 = dict(name="ch2d_1024_neumann_bdf2_converged", n=1024, eps=0.05, dt=1e-
 
 
 SPLIT3D = dict(name="ch3d_256_be_periodic", n=256, eps=0.05, dt=1e-4, M=4, amp=0.05, seed=0, iters=10, steps=3)
-# per 3D iteration: 15 single-field line sweeps (8 B/pt each); linear combinations: three of 3
-# fields (16 B/pt), three of 2 (12 B/pt), one of 4 (20 B/pt); the cubic (8 B/pt) and two max
-# reductions (8 B/pt); per stage the rhs inverse's 6 sweeps
-SPLIT3D_BYTES_ITER, SPLIT3D_BYTES_RHS = 15 * 8 + 3 * 16 + 3 * 12 + 20 + 8 + 2 * 8, 6 * 8
+# per 3D iteration: 15 line sweeps, 12 of them single-field (8 B/pt) and 3 fused x sweeps that
+# read three fields and write one (16 B/pt); one linear combination of 4 fields (20 B/pt), the
+# cubic (8 B/pt) and two max reductions (8 B/pt); per stage the rhs inverse's 6 sweeps
+SPLIT3D_BYTES_ITER, SPLIT3D_BYTES_RHS = 12 * 8 + 3 * 16 + 20 + 8 + 2 * 8, 6 * 8
 SPLIT3D_SWEEPS_ITER, SPLIT3D_SWEEPS_RHS = 15, 6
 
 

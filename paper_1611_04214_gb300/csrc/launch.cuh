@@ -60,6 +60,10 @@ template <typename T> inline OpP2V<T> build(const OpArgs<T>& a, OpP2V<T>*) {
     OpP2V<T> o; o.v1 = a.in0; o.v2 = a.in1; o.t_in = a.in2; o.s_in = a.in3; o.p_out = a.out0; o.u_out = a.out1;
     o.s = a.vs; o.beta = a.beta; o.comp = a.comp; return o;
 }
+template <typename T> inline OpComb3<T> build(const OpArgs<T>& a, OpComb3<T>*) {
+    OpComb3<T> o; o.y = a.in0; o.z = a.in1; o.yz = a.in2; o.out = a.out0; o.ka = a.g2; o.kb = a.g1; o.kc = a.beta;
+    return o;
+}
 template <typename T> inline Op1aV<T> build(const OpArgs<T>& a, Op1aV<T>*) {
     Op1aV<T> o; o.v1 = a.in0; o.v2 = a.in1; o.e_out = a.out0; o.s = a.vs; o.beta = a.beta; o.comp = a.comp;
     return o;
@@ -182,6 +186,7 @@ template <> struct PipeOf<OpCopy<float>> { using type = PipeCopy<float>; };
 template <> struct PipeOf<OpP2<float>> { using type = PipeP2<float>; };
 template <> struct PipeOf<OpP4<float>> { using type = PipeP4<float>; };
 template <> struct PipeOf<Op1a<float>> { using type = Pipe1a<float>; };
+template <> struct PipeOf<OpComb3<float>> { using type = PipeComb3<float>; };
 template <> struct PipeOf<Op1b<float>> { using type = Pipe1b<float>; };
 template <> struct PipeOf<OpP2V<float>> { using type = PipeP2V<float>; };
 template <> struct PipeOf<Op1aV<float>> { using type = Pipe1aV<float>; };
@@ -208,6 +213,7 @@ P pipe_build(int kind, const OpArgs<float>& a) {
             p.s[0] = a.in0; p.s[1] = a.in1; p.s[2] = a.in2; p.s[3] = a.in3; p.o[0] = a.out0; p.o[1] = a.out1;
             break;
         case OP_V1A: p.s[0] = a.in0; p.s[1] = a.in1; p.o[0] = a.out0; break;
+        case OP_C3: p.s[0] = a.in0; p.s[1] = a.in1; p.s[2] = a.in2; p.o[0] = a.out0; break;
     }
     set_vch(p, a);
     return p;
@@ -473,7 +479,8 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
                      unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof, int kind) {
     Op op = build(a, static_cast<Op*>(nullptr));
     // the vector CH passes are timed in the slots of their scalar counterparts
-    const int pk = kind == OP_V1 ? OP_P1 : kind == OP_V2 ? OP_P2 : kind == OP_V1A ? OP_1A : kind;
+    const int pk = kind == OP_V1 ? OP_P1 : kind == OP_V2 ? OP_P2 : kind == OP_V1A ? OP_1A : kind == OP_C3 ? OP_COPY
+                                                                                                        : kind;
     const int nlines = axis == 0 ? ny : nx;
     set_strides<T>(op, axis == 0 ? nx : 1, axis == 0 ? 1 : nx);
     if (launches) *launches += 1;
@@ -676,6 +683,7 @@ MOLT_DECLARE_PASS(sweep_p3)
 MOLT_DECLARE_PASS(sweep_p4)
 MOLT_DECLARE_PASS(sweep_v1)
 MOLT_DECLARE_PASS(sweep_v2)
+MOLT_DECLARE_PASS(sweep_c3)   // the 3D x-line combination (kernels_c3.cu)
 #undef MOLT_DECLARE_PASS
 
 template <typename T>
@@ -693,6 +701,7 @@ cudaError_t sweep(int axis, const LineParams<T>& lp, int kind, const OpArgs<T>& 
         case OP_V1:
         case OP_V2:
         case OP_V1A: return sweep_vch<T>(axis, lp, kind, a, nx, ny, cs, red, st, launches, prof);
+        case OP_C3: return sweep_c3<T>(axis, lp, kind, a, nx, ny, cs, red, st, launches, prof);
     }
     return cudaErrorInvalidValue;
 }

@@ -97,7 +97,7 @@ struct ColScratch {
 namespace molt {
 
 // Which fused prologue/epilogue a sweep runs (see sweep_common.cuh for the formulas).
-enum OpKind { OP_COPY = 0, OP_P1, OP_P2, OP_P3, OP_P4, OP_1A, OP_1B, OP_V1, OP_V2, OP_V1A };
+enum OpKind { OP_COPY = 0, OP_P1, OP_P2, OP_P3, OP_P4, OP_1A, OP_1B, OP_V1, OP_V2, OP_V1A, OP_C3 };
 
 template <typename T>
 struct OpArgs {

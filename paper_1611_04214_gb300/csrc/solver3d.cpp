@@ -17,8 +17,9 @@
 // the rows of the [nz * ny][nx] view, z lines the columns of the [nz][ny * nx] view, and the y
 // lines of each z slab are the columns of one instance of an internal batch of nz slabs
 // (molt_batch_helmholtz_apply), so every sweep is one launch sequence over the whole field.
-// By linearity of H_x, Q and A need one x sweep each after combining their y and z products.
-// The passes are not fused: 15 single-field sweeps and 7 linear combinations per iteration.
+// By linearity of H_x, Q and A need one x sweep each after combining their y and z products, and
+// that combination is fused into the x sweep's prologue and epilogue: 15 line sweeps and one
+// linear combination per iteration, the other passes not fused.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -114,19 +115,26 @@ cudaError_t yz_products(molt_solver3d* s, double c, const float* f, cudaStream_t
     return sweep3(s, 1, c, s->t[4], s->t[1], st);
 }
 
-// out = x_part + sign * H_y H_z f with x_part = H_x (a (H_y f + H_z f) + b H_y H_z f): Q f for
-// (a, b, sign) = (1, -2, +1), A f for (-1, 3, -1).  Uses t[0], t[1], t[2], t[4], t[5].
+// out = scale (H_x (a (H_y f + H_z f) + b H_y H_z f) + sign H_y H_z f): Q f for (a, b, sign) =
+// (1, -2, +1), A f for (-1, 3, -1).  The combination and the x sweep are one fused row pass
+// (OpComb3).  Uses t[1], t[4], t[5].
 cudaError_t q_or_a(molt_solver3d* s, double c, const float* f, double a, double b, double sign, double scale,
                    float* out, cudaStream_t st) {
-    const long long n = static_cast<long long>(s->n);
     cudaError_t e;
-    if ((e = yz_products(s, c, f, st)) != cudaSuccess ||
-        (e = molt::lincomb<float>(s->t[0], n, s->t[5], a, s->t[4], a, s->t[1], b, nullptr, 0.0, 0.0, st,
-                                  &s->launches)) != cudaSuccess ||
-        (e = sweep3(s, 0, c, s->t[0], s->t[2], st)) != cudaSuccess)
-        return e;
-    return molt::lincomb<float>(out, n, s->t[2], scale, s->t[1], sign * scale, nullptr, 0.0, nullptr, 0.0, 0.0, st,
-                                &s->launches);
+    if ((e = yz_products(s, c, f, st)) != cudaSuccess) return e;
+    molt::LineParams<double> lpd;
+    const char* err = nullptr;
+    if (!molt::build_line_params(c, s->h(0), s->nx, s->p.quad_order, s->bc, &lpd, &err)) return cudaErrorInvalidValue;
+    const molt::LineParams<float> lp = molt::cast_line_params<float>(lpd);
+    molt::OpArgs<float> oa;
+    oa.in0 = s->t[5];   // H_y f
+    oa.in1 = s->t[4];   // H_z f
+    oa.in2 = s->t[1];   // H_y H_z f
+    oa.out0 = out;
+    oa.g2 = static_cast<float>(scale * a);
+    oa.g1 = static_cast<float>(scale * b);
+    oa.beta = static_cast<float>(scale * sign);
+    return molt::sweep<float>(0, lp, molt::OP_C3, oa, s->nx, s->ny * s->nz, &s->cs, s->red, st, &s->launches);
 }
 
 // out = H_x H_y H_z f (tmp: two scratch fields).

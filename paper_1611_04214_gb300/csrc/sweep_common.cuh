@@ -334,6 +334,31 @@ struct OpP4 : OpBase<T> {
     }
 };
 
+// 3D split stage, x lines (rows only): out = H_x[ka (y + z) + kb yz] + kc yz, with y = H_y f,
+// z = H_z f and yz = H_y H_z f of one field f.  The pair and triple products of the 3D remainder
+// X regroup by linearity of H_x into this one sweep: (ka, kb, kc) = s (1, -2, 1) gives s Q f and
+// s (-1, 3, -1) gives s A f.
+template <typename T>
+struct OpComb3 : OpBase<T> {
+    static constexpr int NF = 1;
+    static constexpr int NA = 1;
+    static constexpr int kAxes = 1;
+    static constexpr bool kReduce = false;
+    const T* y;
+    const T* z;
+    const T* yz;
+    T* out;
+    T ka, kb, kc;
+    __device__ __forceinline__ void load(int line, int pos, T (&f)[1]) const {
+        const size_t i = this->at(line, pos);
+        f[0] = fma(kb, yz[i], ka * (y[i] + z[i]));
+    }
+    __device__ __forceinline__ void fetch(int line, int pos, T (&a)[NA]) const { a[0] = yz[this->at(line, pos)]; }
+    __device__ __forceinline__ void put(int line, int pos, const T (&h)[1], const T (&a)[NA], RedAcc<T>&) const {
+        out[this->at(line, pos)] = fma(kc, a[0], h[0]);
+    }
+};
+
 // 1D pass a (inner c): E = H_i[beta G(w)] - beta G(w).
 template <typename T>
 struct Op1a : OpBase<T> {
@@ -554,6 +579,25 @@ struct PipeP2 {
         const T u = sv[2] + h[1];
         ov[0] = fma(beta, h[0] - sv[1], u);
         ov[1] = u;
+    }
+};
+
+// 3D x lines: staged y, z, yz; output H[ka (y + z) + kb yz] + kc yz (see OpComb3; ka = g2,
+// kb = g1, kc = beta)
+template <typename T>
+struct PipeComb3 {
+    static constexpr int NS = 3, NA = 0, NF = 1, NO = 1;
+    static constexpr bool kReduce = false;
+    const T* s[NS];
+    const T* a[1];
+    T* o[NO];
+    T g2, g1, beta;
+    __device__ __forceinline__ void prologue(const T (&sv)[NS], T (&f)[NF]) const {
+        f[0] = fma(g1, sv[2], g2 * (sv[0] + sv[1]));
+    }
+    __device__ __forceinline__ void epilogue(const T (&h)[NF], const T (&sv)[NS], const T (&)[1], T (&ov)[NO],
+                                             RedAcc<T>&) const {
+        ov[0] = fma(beta, sv[2], h[0]);
     }
 };
 
