@@ -304,8 +304,9 @@ rows_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, i
 }
 
 // =========================================================================================
-// Rows, FP32, persistent and pipelined.  A block owns one line per iteration with K = 16
-// positions per thread (TL = n / 16 threads) and loops over lines blockIdx.x, +gridDim.x, ...
+// Rows, FP32, persistent and pipelined.  A block owns one line per iteration with K = KT
+// positions per thread (TL = n / K threads; K = 16, or 8 for lines of at most 4096 nodes so that
+// their blocks keep 16 warps) and loops over lines blockIdx.x, +gridDim.x, ...
 // The staged input fields of the next line arrive by cp.async (16-byte chunks, swizzled) into
 // the other half of a double buffer while the current line is swept; the epilogue's auxiliary
 // fields of the current line are fetched the same way during the sweep.  Window reads and the
@@ -323,12 +324,13 @@ __device__ __forceinline__ void set4(float4& v, int e, float x) {
     else v.w = x;
 }
 
-template <int M, class Op>
+template <int M, class Op, int KT = 16>
 __global__ void __launch_bounds__(512, 1)
 rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_constant__ PackedStencil pw, const Op op,
                  int nlines, long long ld, unsigned long long* red_slots) {
     using T = float;
-    constexpr int K = 16, V = 4, KC = K / V, H = M / 2, WC = KC + 2;
+    constexpr int K = KT, V = 4, KC = K / V, H = M / 2, WC = KC + 2;
+    static_assert(K % V == 0 && K >= 8, "whole 16-byte chunks per thread, at least one wall stencil");
     constexpr int NS = Op::NS, NA = Op::NA, NF = Op::NF, NO = Op::NO;
     // two swept fields (pass 2): their stencil and recurrence steps run as fma.rn.f32x2 pairs
     constexpr bool kPack = NF == 2;
