@@ -285,8 +285,8 @@ cudaError_t rows_pipe(const LineParams<float>& lp, const P& op, int nlines, unsi
     const PackedStencil pw = packed_stencil(lp);
     const long long ld = n;
     if constexpr (C == 1) {
-        // lines of at most 4096 nodes take 8 positions per thread: twice the warps per block
-        if (n <= 4096) return rows_pipe_one<M, P, 8>(lp, pw, op, nlines, ld, smem, red, st, prof, kind);
+        // 16 positions per thread at every length (8 for lines of at most 4096 nodes, with twice
+        // the warps per block, measured slower)
         return rows_pipe_one<M, P, 16>(lp, pw, op, nlines, ld, smem, red, st, prof, kind);
     } else {
         auto kern = rows_cluster_kernel<M, P, C>;

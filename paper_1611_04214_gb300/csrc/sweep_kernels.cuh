@@ -305,8 +305,8 @@ rows_kernel(const __grid_constant__ LineParams<T> lp, const Op op, int nlines, i
 
 // =========================================================================================
 // Rows, FP32, persistent and pipelined.  A block owns one line per iteration with K = KT
-// positions per thread (TL = n / K threads; K = 16, or 8 for lines of at most 4096 nodes so that
-// their blocks keep 16 warps) and loops over lines blockIdx.x, +gridDim.x, ...
+// positions per thread (TL = n / K threads; the launch uses K = 16) and loops over lines
+// blockIdx.x, +gridDim.x, ...
 // The staged input fields of the next line arrive by cp.async (16-byte chunks, swizzled) into
 // the other half of a double buffer while the current line is swept; the epilogue's auxiliary
 // fields of the current line are fetched the same way during the sweep.  Window reads and the
