@@ -71,6 +71,25 @@ def test_grid_validation_host_only(lib):
     assert lib.molt_grid_create(ctypes.byref(g), 3, 64, 48, 1.0, 1.0, 0) == -1      # bad dim
 
 
+def test_solver3d_validation_host_only(lib):
+    # molt_solver3d_create checks its arguments before any device work.
+    from paper_1611_04214_gb300 import molt
+    h = ctypes.c_void_p()
+    p32 = molt._Params(0.1, 4, molt.PRECISION["fp32"], 1e-8, 50)
+    p64 = molt._Params(0.1, 4, molt.PRECISION["fp64"], 1e-8, 50)
+    create = lib.molt_solver3d_create
+    assert create(ctypes.byref(h), 32, 32, 32, 1.0, 1.0, 1.0, 2, ctypes.byref(p32)) == molt.MOLT_ERR_UNSUPPORTED
+    assert b"periodic and Neumann" in lib.molt_last_error(None)
+    assert create(ctypes.byref(h), 32, 32, 32, 1.0, 1.0, 1.0, 0, ctypes.byref(p64)) == molt.MOLT_ERR_UNSUPPORTED
+    assert create(ctypes.byref(h), 2048, 32, 32, 1.0, 1.0, 1.0, 0, ctypes.byref(p32)) == -1    # nx > 1024
+    assert create(ctypes.byref(h), 32, 32, 4, 1.0, 1.0, 1.0, 0, ctypes.byref(p32)) == -1       # nz < M + 2
+    assert create(ctypes.byref(h), 32, 32, 32, 1.0, -1.0, 1.0, 0, ctypes.byref(p32)) == -1     # bad length
+    assert create(ctypes.byref(h), 32, 32, 32, 1.0, 1.0, 1.0, 0, None) == -1                   # no params
+    assert lib.molt_solver3d_step(None, None, 1e-3, 0, None, None) == -1
+    assert lib.molt_solver3d_apply(None, 0, 1.0, None, None, None) == -1
+    assert lib.molt_batch_helmholtz_apply(None, 0, None, None, None, None) == -1
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_1611_04214_gb300 import molt
     saved = molt._lib
