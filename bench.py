@@ -175,17 +175,17 @@ def oracle_crop_task(task):
     return sweeps * n * n, el, w0, time.time(), (out if keep else None)
 
 
-CONFIG1 = dict(n=256, eps=0.1, dt=1e-3, steps=1000, tol=1e-10, max_iter=500, M=4, bc="neumann", amp=0.05, seed=0)
+CH1D256 = dict(n=256, eps=0.1, dt=1e-3, steps=1000, tol=1e-10, max_iter=500, M=4, bc="neumann", amp=0.05, seed=0)
 
 
-def oracle_config1_task(_=None):
+def oracle_ch1d256_task(_=None):
     """The 1D Neumann BE workload in full on the oracle: N = 256, eps = 0.1, dt = 1e-3, 1000 steps,
     tolerance 1e-10.  Returns (seconds, field, total iterations)."""
     import numpy as np
 
     from oracle.solver import OracleSolver, Problem
     from paper_1611_04214_gb300.inputs import uniform_noise
-    c = CONFIG1
+    c = CH1D256
     prob = Problem(nx=c["n"], ny=1, bc=c["bc"], eps=c["eps"], M=c["M"], tol=c["tol"], max_iter=c["max_iter"])
     o = OracleSolver(prob)
     u = uniform_noise((1, c["n"]), c["amp"], seed=c["seed"]).astype(np.float32).astype(np.float64)
@@ -616,7 +616,7 @@ def tc_sweep_case(peak, reps: int = 10, n: int = 8192):
             "gbs_algorithmic": gbs, "frac_of_peak": gbs / peak, "max_rel_diff_vs_fp32_sweep": diff}
 
 
-CONFIG2 = dict(name="ch2d_1024_neumann_bdf2_converged", n=1024, eps=0.05, dt=1e-4, steps=200, tol=1e-6,
+CONVERGED_WL = dict(name="ch2d_1024_neumann_bdf2_converged", n=1024, eps=0.05, dt=1e-4, steps=200, tol=1e-6,
                max_iter=20000, M=4, bc="neumann", amp=0.05, seed=0)
 
 
@@ -679,7 +679,7 @@ def converged_leg():
 
     from paper_1611_04214_gb300.inputs import uniform_noise
     from paper_1611_04214_gb300.molt import Solver
-    c = CONFIG2
+    c = CONVERGED_WL
     n = c["n"]
     u0 = uniform_noise((n, n), c["amp"], seed=c["seed"]).astype(np.float32)
     out = {"workload": c["name"], "grid": [n, n], "eps": c["eps"], "dt": c["dt"], "scheme": "bdf2", "steps": c["steps"],
@@ -719,7 +719,7 @@ def converged_leg():
     return out
 
 
-def oracle_parity(args, crop_field, config1):
+def oracle_parity(args, crop_field, ch1d256):
     """The FP32 and FP64 GPU paths against the oracle results of the cpu_baseline pool: the top-left
     1024^2 periodic block of the 8192^2 workload after one SDIRK3 step (the bench's fixed iterations
     per stage on both sides), and the 1D Neumann BE workload after its 1000 steps."""
@@ -739,9 +739,9 @@ def oracle_parity(args, crop_field, config1):
             u = torch.tensor(start, device="cuda").to(s.dtype)
             s.step(u, WORKLOAD["dt"], WORKLOAD["scheme"], raise_on_nonconvergence=False)
             err = float(np.abs(u.double().cpu().numpy() - crop_field).max())
-        out[f"config3_crop1024_{prec}"] = {"max_abs_err": err, "max_rel_err_v": err / scale}
-    secs, ref1, its1 = config1
-    c = CONFIG1
+        out[f"ch2d8192_crop1024_{prec}"] = {"max_abs_err": err, "max_rel_err_v": err / scale}
+    secs, ref1, its1 = ch1d256
+    c = CH1D256
     u1 = uniform_noise((1, c["n"]), c["amp"], seed=c["seed"]).astype(np.float32)
     for prec in ("fp32", "fp64"):
         with Solver(nx=c["n"], ny=1, bc=c["bc"], eps=c["eps"], quad_order=c["M"], precision=prec, tol=c["tol"],
@@ -752,10 +752,10 @@ def oracle_parity(args, crop_field, config1):
             its = sum(s.step(u, c["dt"], "be", raise_on_nonconvergence=False).iters[0] for _ in range(c["steps"]))
             el = time.perf_counter() - t0
             err = float(np.abs(u.double().cpu().numpy() - ref1).max())
-        out[f"config1_1d256_be_1000steps_{prec}"] = {"max_abs_err": err,
+        out[f"ch1d256_neumann_be_1000steps_{prec}"] = {"max_abs_err": err,
                                                      "max_rel_err_v": err / float(np.abs(ref1 + 1).max()),
                                                      "iters_total": int(its), "seconds": el}
-    out["config1_oracle"] = {"seconds": secs, "iters_total": int(its1), "cores": 1}
+    out["ch1d256_oracle"] = {"seconds": secs, "iters_total": int(its1), "cores": 1}
     return out
 
 
@@ -787,7 +787,7 @@ def run_ours(args, rank, world, dist):
         pool = oracle_pool(procs)
         tasks = [(1024, r, c, args.iters, i == 0) for i, (r, c) in enumerate((CROP_TILES * 4)[:procs])]
         crop_jobs = pool.map_async(oracle_crop_task, tasks)
-        c1_job = pool.apply_async(oracle_config1_task)
+        c1_job = pool.apply_async(oracle_ch1d256_task)
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     n = WORKLOAD["n"]
@@ -938,8 +938,8 @@ def run_ours(args, rank, world, dist):
                   "sweep_microbench": sweeps_mb, "vector_ch": vch, "kernels": kernels,
                   "converged_l2_resident": converged, "oracle_parity": parity, "fma_probe": fp64_probe,
                   "autotune": tuning, "split3d": split3d}
-        if parity and "config3_crop1024_fp32" in parity:
-            result["config3_crop_err_vs_oracle"] = {p_: parity[f"config3_crop1024_{p_}"]["max_rel_err_v"]
+        if parity and "ch2d8192_crop1024_fp32" in parity:
+            result["ch2d8192_crop1024_err_vs_oracle"] = {p_: parity[f"ch2d8192_crop1024_{p_}"]["max_rel_err_v"]
                                                     for p_ in ("fp32", "fp64")}
     solver.close()
     return result

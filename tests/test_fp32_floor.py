@@ -52,7 +52,7 @@ class _Planted:
         return False
 
 
-def _config3_dirichlet(n, mode):
+def _ch2d8192_dirichlet(n, mode):
     # top-left n x n block of the 8192^2 SDIRK3 workload, Dirichlet walls u = -1, two steps of
     # 10 fixed iterations per stage
     u = gaussian_noise_block((8192, 8192), n, n, 0.05, seed=0, mean=0.1)
@@ -81,12 +81,12 @@ def _mixture(bc, mode):
 
 
 @pytest.mark.parametrize("mode", ["iterate", "all"])
-def test_config3_dirichlet_crop_fp32_floor(mode):
+def test_ch2d8192_dirichlet_crop_fp32_floor(mode):
     n = int(os.environ.get("MOLT_FP32_FLOOR_N", "256"))
-    ref = _config3_dirichlet(n, "none")
-    err = float(np.abs(_config3_dirichlet(n, mode) - ref).max())
+    ref = _ch2d8192_dirichlet(n, "none")
+    err = float(np.abs(_ch2d8192_dirichlet(n, mode) - ref).max())
     target = 1e-6 * np.abs(ref + 1).max()
-    record(f"fp32_floor_config3_crop{n}_dirichlet_{mode}", err, target, target, "fp32-floor")
+    record(f"fp32_floor_ch2d8192_crop{n}_dirichlet_{mode}", err, target, target, "fp32-floor")
     # measured: 256^2 iterate 0.57 x, all 2.25 x; 1024^2 iterate 0.60 x, all 2.20 x
     assert err > (1.0 if mode == "all" else 0.3) * target, err / target
 

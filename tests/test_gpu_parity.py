@@ -297,12 +297,12 @@ def test_steps_2d_fp32_within_bar(scheme, bc):
     _check32(f"steps2d_72x96_noise_{scheme}_{bc}", got, ref, bc, rho[0])
 
 
-# Config 1 FP32 horizon: the steps over which the FP32 field stays within 1e-6 of max|u + 1|.
+# FP32 horizon of the 1D Neumann workload (N = 256, BE, 1000 steps): the steps over which the FP32 field stays within 1e-6 of max|u + 1|.
 # Spinodal decomposition and the coarsening events that follow amplify any perturbation: in the
 # FP64 oracle a one-ulp (6e-8) perturbation of this initial state grows to 8e-7 by step 200 and to
 # 8.5e-6 at step 550, then falls back to 4e-7 by step 1000.  The FP32 run injects rounding at
 # every step, so beyond the horizon its error is bounded by that amplification, not by 1e-6.
-CONFIG1_HORIZON = 150
+CH1D256_HORIZON = 150
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -326,17 +326,17 @@ def test_1d_neumann_be_matches_oracle(precision):
                 errs[k] = (got, u_ref.copy())
     if precision == "fp64":
         got, ref = errs[steps]
-        check_fp64("config1_1d256_neumann_be_1000steps_fp64", got, ref, 1e-10 * np.abs(ref + 1).max())
+        check_fp64("ch1d256_neumann_be_1000steps_fp64", got, ref, 1e-10 * np.abs(ref + 1).max())
         assert all(abs(a - b) <= 1 for a, b in zip(ig, ir))
         return
     curve = {k: float(np.abs(g - r).max()) for k, (g, r) in errs.items()}
-    got, ref = errs[CONFIG1_HORIZON]
-    check_fp32(f"config1_1d256_neumann_be_{CONFIG1_HORIZON}steps", got, ref, np.abs(ref + 1).max(),
+    got, ref = errs[CH1D256_HORIZON]
+    check_fp32(f"ch1d256_neumann_be_{CH1D256_HORIZON}steps", got, ref, np.abs(ref + 1).max(),
                error_every_50_steps=curve)
     # past the horizon: within the FP64 oracle's own amplification of one-ulp perturbations (8.5e-6
     # at its peak), with a margin for the rounding that every step adds
     got, ref = errs[steps]
-    record("config1_1d256_neumann_be_1000steps", curve[steps], 1e-6 * np.abs(ref + 1).max(), 5e-5,
+    record("ch1d256_neumann_be_1000steps", curve[steps], 1e-6 * np.abs(ref + 1).max(), 5e-5,
            "growth-limited", None)
     assert max(curve.values()) <= 5e-5, curve
 

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 from paper_1611_04214_gb300.inputs import paper_ic_1d  # noqa: E402
 
 # (scheme, dt) -> ripening time printed in Table 1DCH_ripeninglargedt
-PAPER = {("be", 10.0): 8250.0, ("bdf2", 10.0): 8290.0, ("be", 1.0): 8296.0, ("bdf2", 1.0): 8303.0}
+PAPER_RIPENING = {("be", 10.0): 8250.0, ("bdf2", 10.0): 8290.0, ("be", 1.0): 8296.0, ("bdf2", 1.0): 8303.0}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -46,7 +46,7 @@ def _ripening(scheme, dt, precision, t_max=12000.0):
     return None
 
 
-@pytest.mark.parametrize("scheme,dt", sorted(PAPER))
+@pytest.mark.parametrize("scheme,dt", sorted(PAPER_RIPENING))
 def test_ripening_time_matches_paper_fp64(scheme, dt):
-    assert _ripening(scheme, dt, "fp64") == PAPER[(scheme, dt)]
+    assert _ripening(scheme, dt, "fp64") == PAPER_RIPENING[(scheme, dt)]
 

@@ -36,7 +36,7 @@ N3, EPS3, DT3, M3, ITERS3 = 8192, 0.02, 5e-5, 4, 10
 # iterations is about 2.5e-6 of max|u|, as on the periodic variant, but its walls at u = -1 make
 # max|u| four times the periodic one while the scale max|u + 1| stays the same; the oracle's own
 # arithmetic with every sweep output rounded to FP32 lands at 2.2 x on the 1024^2 crop.
-CONFIG3_DIRICHLET_MISS = (3.0, "FP32 rounding of the iteration at |u| = 1 walls, 60 fixed iterations")
+CH2D8192_DIRICHLET_MISS = (3.0, "FP32 rounding of the iteration at |u| = 1 walls, 60 fixed iterations")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -47,7 +47,7 @@ def _library():
     build.build_library()
 
 
-def _config3_block(rows, cols, bc):
+def _ch2d8192_block(rows, cols, bc):
     """Top-left rows x cols block of the 8192^2 initial state, with its node spacing and lengths."""
     u = gaussian_noise_block((N3, N3), rows, cols, 0.05, seed=0, mean=0.1)
     h = 2 * np.pi / N3 if bc == "periodic" else 2 * np.pi / (N3 - 1)
@@ -62,7 +62,7 @@ def _config3_block(rows, cols, bc):
 @functools.lru_cache(maxsize=8)
 def _oracle_fixed(rows, cols, bc, steps):
     """The oracle's SDIRK3 steps from the FP32-rounded start, ITERS3 iterations per stage."""
-    u0, Lx, Ly = _config3_block(rows, cols, bc)
+    u0, Lx, Ly = _ch2d8192_block(rows, cols, bc)
     start = u0.astype(np.float32).astype(np.float64)
     prob = Problem(nx=cols, ny=rows, Lx=Lx, Ly=Ly, bc=bc, eps=EPS3, M=M3, tol=1e-30, max_iter=ITERS3)
     o = OracleSolver(prob)
@@ -75,7 +75,7 @@ def _oracle_fixed(rows, cols, bc, steps):
 
 def _gpu_fixed(rows, cols, bc, steps, precision):
     from paper_1611_04214_gb300.molt import Solver
-    u0, Lx, Ly = _config3_block(rows, cols, bc)
+    u0, Lx, Ly = _ch2d8192_block(rows, cols, bc)
     with Solver(nx=cols, ny=rows, Lx=Lx, Ly=Ly, bc=bc, eps=EPS3, quad_order=M3, precision=precision,
                 tol=1e-30, max_iter=ITERS3) as s:
         u = torch.tensor(u0.astype(np.float32), device="cuda").to(s.dtype)
@@ -85,35 +85,35 @@ def _gpu_fixed(rows, cols, bc, steps, precision):
 
 
 @pytest.mark.parametrize("bc", ["periodic", "dirichlet"])
-def test_config3_full_rows_fixed_iterations(bc):
+def test_ch2d8192_full_rows_fixed_iterations(bc):
     rows, cols = 288, N3
     got, ig = _gpu_fixed(rows, cols, bc, 1, "fp32")
     ref, io = _oracle_fixed(rows, cols, bc, 1)
     assert ig == io == [[ITERS3] * 3], (ig, io)
-    check_fp32(f"config3_rows8192x288_sdirk3_{bc}_1step_10it", got, ref, np.abs(ref + 1).max(),
-               known_miss=CONFIG3_DIRICHLET_MISS if bc == "dirichlet" else None)
+    check_fp32(f"ch2d8192_rows8192x288_sdirk3_{bc}_1step_10it", got, ref, np.abs(ref + 1).max(),
+               known_miss=CH2D8192_DIRICHLET_MISS if bc == "dirichlet" else None)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("bc", ["periodic", "dirichlet"])
-def test_config3_crop_1024(bc, precision):
+def test_ch2d8192_crop_1024(bc, precision):
     n = 1024
     got, ig = _gpu_fixed(n, n, bc, 2, precision)
     ref, io = _oracle_fixed(n, n, bc, 2)
     assert ig == io == [[ITERS3] * 3] * 2, (ig, io)
-    case = f"config3_crop1024_sdirk3_{bc}_2steps_10it"
+    case = f"ch2d8192_crop1024_sdirk3_{bc}_2steps_10it"
     scale = np.abs(ref + 1).max()
     if precision == "fp64":
         check_fp64(case + "_fp64", got, ref, 1e-11 * scale)
     else:
-        check_fp32(case, got, ref, scale, known_miss=CONFIG3_DIRICHLET_MISS if bc == "dirichlet" else None)
+        check_fp32(case, got, ref, scale, known_miss=CH2D8192_DIRICHLET_MISS if bc == "dirichlet" else None)
 
 
 # ---- the Neumann BDF2 workload, iterated to its tolerance on a 128^2 crop ----
 N2, EPS2, DT2, TOL2, CROP2, STEPS2 = 1024, 0.05, 1e-4, 1e-6, 128, 3
 
 
-def _config2_problem():
+def _ch2d1024_problem():
     h = 2 * np.pi / (N2 - 1)
     L = h * (CROP2 - 1)
     u0 = uniform_noise((CROP2, CROP2), 0.05, seed=0)
@@ -121,8 +121,8 @@ def _config2_problem():
 
 
 @functools.lru_cache(maxsize=1)
-def _oracle_config2():
-    u0, L = _config2_problem()
+def _oracle_ch2d1024():
+    u0, L = _ch2d1024_problem()
     prob = Problem(nx=CROP2, ny=CROP2, Lx=L, Ly=L, bc="neumann", eps=EPS2, M=4, tol=TOL2, max_iter=20000)
     o = OracleSolver(prob)
     u = u0.astype(np.float32).astype(np.float64)
@@ -136,10 +136,10 @@ def _oracle_config2():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_config2_crop_converged_steps(precision):
+def test_ch2d1024_crop_converged_steps(precision):
     from paper_1611_04214_gb300.molt import Solver
-    u0, L = _config2_problem()
-    ref, io, rho, conv, prob = _oracle_config2()
+    u0, L = _ch2d1024_problem()
+    ref, io, rho, conv, prob = _oracle_ch2d1024()
     assert all(conv), io        # the oracle reaches the tolerance at every step
     with Solver(nx=CROP2, ny=CROP2, Lx=L, Ly=L, bc="neumann", eps=EPS2, quad_order=4, precision=precision,
                 tol=TOL2, max_iter=20000) as s:
@@ -155,7 +155,7 @@ def test_config2_crop_converged_steps(precision):
         drift = abs(s.mass(u) - m0)
         got = u.double().cpu().numpy()
     scale = np.abs(ref + 1).max()
-    case = f"config2_crop128_neumann_bdf2_tol1e-6_{STEPS2}steps"
+    case = f"ch2d1024_crop128_neumann_bdf2_tol1e-6_{STEPS2}steps"
     record(case + f"_{precision}_invariants", drift, 0, 0, "invariants", rho, iters_gpu=ig, iters_oracle=io,
            energy_monotone=bool(monotone))
     assert monotone
@@ -181,7 +181,7 @@ def test_autotuned_solver_keeps_parity():
     # step was tuned.
     from paper_1611_04214_gb300.molt import Solver
     rows, cols = 288, 1024
-    u0, Lx, Ly = _config3_block(rows, cols, "periodic")
+    u0, Lx, Ly = _ch2d8192_block(rows, cols, "periodic")
     with Solver(nx=cols, ny=rows, Lx=Lx, Ly=Ly, bc="periodic", eps=EPS3, quad_order=M3, precision="fp32",
                 tol=1e-30, max_iter=ITERS3) as s:
         table = s.autotune()
@@ -194,4 +194,4 @@ def test_autotuned_solver_keeps_parity():
         got = u.double().cpu().numpy()
     ref, io = _oracle_fixed(rows, cols, "periodic", 1)
     assert [iters] == io
-    check_fp32("config3_rows1024x288_sdirk3_periodic_autotuned", got, ref, np.abs(ref + 1).max())
+    check_fp32("ch2d8192_rows1024x288_sdirk3_periodic_autotuned", got, ref, np.abs(ref + 1).max())
