@@ -421,7 +421,7 @@ typedef struct molt_solver3d molt_solver3d;
 /* nx, ny in [M + 2, 1024] (the y lines run as a batch of nz slabs, molt_batch_create), nz in
  * [M + 2, 2^20];
  * params: precision must be MOLT_FP32; eps, M, tol and max_iter as molt_solver_create.  The
- * solver owns 17 fields of workspace, the column scan scratch of the z lines and an internal
+ * solver owns 14 fields of workspace, the column scan scratch of the z lines and an internal
  * batch of nz slabs.  Errors: MOLT_ERR_ARG, MOLT_ERR_UNSUPPORTED (Dirichlet, FP64),
  * MOLT_ERR_OOM, MOLT_ERR_CUDA. */
 molt_status molt_solver3d_create(molt_solver3d** solver, int nx, int ny, int nz, double Lx, double Ly,

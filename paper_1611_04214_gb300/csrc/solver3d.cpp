@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -40,7 +41,8 @@ struct molt_solver3d {
     std::vector<void*> allocs;
     float *w = nullptr, *wn = nullptr, *r = nullptr, *uprev = nullptr, *Y = nullptr, *g = nullptr,
           *zero = nullptr;
-    float* t[10] = {};
+    float *hz = nullptr, *hy = nullptr, *hyz = nullptr;   // H_z f, H_y f, H_y H_z f of the current product
+    float *tb = nullptr, *qi = nullptr, *qo = nullptr, *hb = nullptr;   // the iteration's terms
     molt::ColScratch<float> cs{};
     unsigned long long* red = nullptr;
     unsigned long long* red_host = nullptr;
@@ -103,21 +105,21 @@ cudaError_t sweep3(molt_solver3d* s, int axis, double c, const float* in, float*
     return molt::sweep<float>(1, lp, molt::OP_COPY, a, s->nx * s->ny, s->nz, &s->cs, s->red, st, &s->launches);
 }
 
-// The y and z products of f at one c: t[4] = H_z f, t[5] = H_y f, t[1] = H_y H_z f.  The x
+// The y and z products of f at one c: hz = H_z f, hy = H_y f, hyz = H_y H_z f.  The x
 // sweeps come after a combination: by linearity of H_x,
 //   Q f = H_x H_y f + H_x H_z f + H_y H_z f - 2 H_x H_y H_z f = H_x (H_y f + H_z f - 2 H_y H_z f) + H_y H_z f,
 //   A f = 3 H_x H_y H_z f - H_x H_y f - H_x H_z f - H_y H_z f = H_x (3 H_y H_z f - H_y f - H_z f) - H_y H_z f,
 // so each takes one x sweep instead of three.
 cudaError_t yz_products(molt_solver3d* s, double c, const float* f, cudaStream_t st) {
     cudaError_t e;
-    if ((e = sweep3(s, 2, c, f, s->t[4], st)) != cudaSuccess || (e = sweep3(s, 1, c, f, s->t[5], st)) != cudaSuccess)
+    if ((e = sweep3(s, 2, c, f, s->hz, st)) != cudaSuccess || (e = sweep3(s, 1, c, f, s->hy, st)) != cudaSuccess)
         return e;
-    return sweep3(s, 1, c, s->t[4], s->t[1], st);
+    return sweep3(s, 1, c, s->hz, s->hyz, st);
 }
 
 // out = scale (H_x (a (H_y f + H_z f) + b H_y H_z f) + sign H_y H_z f): Q f for (a, b, sign) =
 // (1, -2, +1), A f for (-1, 3, -1).  The combination and the x sweep are one fused row pass
-// (OpComb3).  Uses t[1], t[4], t[5].
+// (OpComb3).  Uses hz, hy, hyz.
 cudaError_t q_or_a(molt_solver3d* s, double c, const float* f, double a, double b, double sign, double scale,
                    float* out, cudaStream_t st) {
     cudaError_t e;
@@ -127,9 +129,9 @@ cudaError_t q_or_a(molt_solver3d* s, double c, const float* f, double a, double 
     if (!molt::build_line_params(c, s->h(0), s->nx, s->p.quad_order, s->bc, &lpd, &err)) return cudaErrorInvalidValue;
     const molt::LineParams<float> lp = molt::cast_line_params<float>(lpd);
     molt::OpArgs<float> oa;
-    oa.in0 = s->t[5];   // H_y f
-    oa.in1 = s->t[4];   // H_z f
-    oa.in2 = s->t[1];   // H_y H_z f
+    oa.in0 = s->hy;
+    oa.in1 = s->hz;
+    oa.in2 = s->hyz;
     oa.out0 = out;
     oa.g2 = static_cast<float>(scale * a);
     oa.g1 = static_cast<float>(scale * b);
@@ -153,16 +155,16 @@ namespace {
 // One fixed-point iteration: wn = Y + w + H_ox H_oy H_oz [beta A_i g] - Q_o [Q_i w].
 cudaError_t iteration3(molt_solver3d* s, const molt::StageParams& sp, cudaStream_t st) {
     const long long n = static_cast<long long>(s->n);
-    float* tb = s->t[6];   // beta A_i g
-    float* qi = s->t[7];   // Q_i w
-    float* qo = s->t[8];   // Q_o Q_i w
-    float* hb = s->t[9];   // H_ox H_oy H_oz (beta A_i g)
+    float* tb = s->tb;   // beta A_i g
+    float* qi = s->qi;   // Q_i w
+    float* qo = s->qo;   // Q_o Q_i w
+    float* hb = s->hb;   // H_ox H_oy H_oz (beta A_i g)
     cudaError_t e;
     // g = w^3 + (lam - 3) w
     if ((e = molt::cubic<float>(s->g, n, s->w, 0.0, sp.lam - 3.0, st, &s->launches)) != cudaSuccess ||
         (e = q_or_a(s, sp.c_in, s->g, -1.0, 3.0, -1.0, sp.beta, tb, st)) != cudaSuccess ||
         (e = q_or_a(s, sp.c_in, s->w, 1.0, -2.0, 1.0, 1.0, qi, st)) != cudaSuccess ||
-        (e = triple(s, sp.c_out, tb, hb, s->t[4], s->t[5], st)) != cudaSuccess ||
+        (e = triple(s, sp.c_out, tb, hb, s->hz, s->hy, st)) != cudaSuccess ||
         (e = q_or_a(s, sp.c_out, qi, 1.0, -2.0, 1.0, 1.0, qo, st)) != cudaSuccess)
         return e;
     return molt::lincomb<float>(s->wn, n, s->Y, 1.0, s->w, 1.0, hb, 1.0, qo, -1.0, 0.0, st, &s->launches);
@@ -188,8 +190,8 @@ molt_status stage3(molt_solver3d* s, double tau, cudaStream_t st, int* iters, do
     const molt::StageParams sp = molt::stage_params(tau, s->p.eps);
     cudaError_t e;
     if ((e = cudaMemsetAsync(s->status, 0, sizeof(unsigned), st)) != cudaSuccess ||
-        (e = triple(s, sp.c_in, s->r, s->t[6], s->t[4], s->t[5], st)) != cudaSuccess ||
-        (e = triple(s, sp.c_out, s->t[6], s->Y, s->t[4], s->t[5], st)) != cudaSuccess)
+        (e = triple(s, sp.c_in, s->r, s->tb, s->hz, s->hy, st)) != cudaSuccess ||
+        (e = triple(s, sp.c_out, s->tb, s->Y, s->hz, s->hy, st)) != cudaSuccess)
         return fail3(MOLT_ERR_CUDA, std::string("3D rhs inverse: ") + cudaGetErrorString(e));
     double res = INFINITY, best = INFINITY, tol_used = s->p.tol;
     int k = 0, stall = 0;
@@ -263,7 +265,7 @@ molt_status molt_solver3d_create(molt_solver3d** out, int nx, int ny, int nz, do
     s->cbuf.assign(nz, 0.0);
     bool ok = s->alloc(&s->w, s->n) && s->alloc(&s->wn, s->n) && s->alloc(&s->r, s->n) && s->alloc(&s->uprev, s->n) &&
               s->alloc(&s->Y, s->n) && s->alloc(&s->g, s->n) && s->alloc(&s->zero, s->n);
-    for (int k = 0; ok && k < 10; ++k) ok = s->alloc(&s->t[k], s->n);
+    for (float** q : {&s->hz, &s->hy, &s->hyz, &s->tb, &s->qi, &s->qo, &s->hb}) ok = ok && s->alloc(q, s->n);
     // column scratch of the z sweeps: nx * ny columns of nz nodes
     const int lines = nx * ny, tiles = (nz + molt::kColTileRows - 1) / molt::kColTileRows;
     const size_t sc = static_cast<size_t>(2) * tiles * lines;
