@@ -49,3 +49,17 @@ def test_combine_ranks_single_process():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.combine_ranks(7.0, 5.0, None) == (7.0, 5.0)
+
+
+def test_roofline_traffic_only_for_the_captured_kernel_family():
+    # The bench reports an ncu DRAM figure only while the autotuner kept the kernel family that
+    # was captured for that pass (or ran without the autotuner).
+    sys.path.insert(0, ROOT)
+    import bench
+    table = {"rows_pass2": (1.0e9, 2, "rows_one_block")}
+    assert bench._traffic(table, "rows_pass2", None) == 1.0e9
+    assert bench._traffic(table, "rows_pass2", [{"pass": 2, "chosen": "rows_one_block"}]) == 1.0e9
+    assert bench._traffic(table, "rows_pass2", [{"pass": 2, "chosen": "default"}]) == 1.0e9
+    assert bench._traffic(table, "rows_pass2", [{"pass": 2, "chosen": "rows_cluster2"}]) is None
+    assert bench._traffic(table, "rows_pass2", [{"pass": 4, "chosen": "rows_cluster2"}]) == 1.0e9
+    assert bench._traffic(table, "rows_pass4", None) is None
