@@ -15,13 +15,17 @@ notation, with no blocking, fusion or reordering:
                   IR, homogeneous)
 * ``solver``    - stage parameters, the 1D and 2D fixed-point stage solves
                   (Eq. CH_BE_fixed2_factor, CH_BE_fixed_complete, Sec. 5.1),
-                  time schemes (BE, BDF2, SDIRK2, SDIRK3) and the discrete
+                  time schemes (BE, BDF2, BDF3, SDIRK2, SDIRK3, SDC2) and the discrete
                   energy / mass.
 * ``adaptive``  - adaptive step-size control (Algorithm 1) with the Richardson,
                   BE-SDC2 and BE-BDF2 LTE estimates.
 * ``vch``       - the vector (three-phase) model of Eq. CH_vector: potential,
                   stage parameters of Eq. CH_vector_fixed1/2, stage solve, BE and
                   BDF2 steps and energy (Sec. 5.2).
+* ``split3d``   - the splitting of Sec. 5.1 carried to three dimensions (the
+                  extension the paper remarks on), BE and BDF2.
+* ``fch``       - the sixth-order model of Eq. FCH0 / FCH in 1D, BE by completing
+                  the cube (Eq. FCH_BE, with the PDE's signs).
 
 Readings of passages the paper leaves open are listed in each docstring.
 """
