@@ -446,6 +446,45 @@ molt_status molt_solver3d_apply(molt_solver3d* solver, int axis, double c, const
 /* Kernels this 3D solver has launched (its internal batch's sweeps counted as 3 each). */
 long long molt_solver3d_launches(const molt_solver3d* solver);
 
+/* ---- Sixth-order (functionalized) Cahn-Hilliard model on independent 1D lines ----------------
+ * Eq. FCH0 in v = u + 1 (Eq. FCH): v_t = Lap[(eps^2 Lap - f'(v) + eta eps^2)(eps^2 Lap v - f(v))],
+ * f(v) = v^3 - 3v^2 + 2v, BE steps with the cube completed (the paper's last section).  The
+ * reading implemented: BE keeps the PDE's signs (Eq. FCH_BE prints the last four bracket terms
+ * with the opposite ones); with a = (dt eps^4)^(1/3), H = (I - a Lap)^{-1} (the line inverse of
+ * Sec. 3 with c = a) and D = H - I the lagged iteration is v^{k+1} = H z,
+ *   z = H^2 v^n + (3 + c_eta) D^2 v - 3 H D v - c_f D^2 f + c_p H D p,
+ *   p = -eps^2 f' Lap v + f f' - eta eps^2 f,
+ * c_eta = dt eta eps^4 / a^2, c_f = dt eps^2 / a^2, c_p = dt / a, and Lap v^{k+1} = (v^{k+1} - z)/a
+ * carried with the iterate (across steps; the first step takes (H v^n - v^n)/a).  About the
+ * wells a mode x = a k^2 is multiplied per iteration by m(x) = h[(3 + c_eta - 2c_f) x^2 h^2 + 3x h^2
+ * - c_p x h^2 (2 eps^2 x / a + 4 - 2 eta eps^2)], h = 1/(1 + x): the iteration diverges where
+ * |m| > 1 (eps = 0.18, eta = 1: dt = 0.1 does, dt <= 0.07 does not).  Fields are `lines`
+ * independent lines of nx nodes, [lines][nx] row-major, FP32 or FP64 per params->precision.
+ * Each iteration runs 7 line sweeps, one pointwise kernel and 6 linear combinations, and
+ * synchronizes `stream` to read the residual.  Errors of these calls are reported by
+ * molt_last_error(NULL). */
+typedef struct molt_fch1d molt_fch1d;
+
+/* nx in [M + 2, the one-field row kernel's limit (molt_solver_create's 1D limit)], lines in
+ * [1, 2^24], L > 0 the line length (the grid conventions of molt_grid_create), bc periodic or
+ * Neumann, eta finite; params: precision, eps, M, tol, max_iter as molt_solver_create.  The
+ * solver owns 16 fields of nx * lines values.  Errors: MOLT_ERR_ARG, MOLT_ERR_UNSUPPORTED
+ * (Dirichlet), MOLT_ERR_OOM. */
+molt_status molt_fch1d_create(molt_fch1d** solver, int nx, int lines, double L, molt_bc bc, double eta,
+                              const molt_params* params);
+molt_status molt_fch1d_destroy(molt_fch1d* solver);
+
+/* One BE step in place on the device field u_dev (u of the paper; float* or double* per the
+ * precision).  The stopping rule is molt_step's: ||v^{k+1} - v^k||_inf < tol (Sec. 4.4) over all
+ * lines, in FP32 floored at 2 ulp of max|v| with the stall rule below 64 ulp.  info (may be NULL)
+ * receives the iterations, residual and tolerance used.  Errors: MOLT_ERR_ARG (null, dt <= 0),
+ * MOLT_ERR_NOT_CONVERGED (the field holds the last iterate), MOLT_ERR_CUDA. */
+molt_status molt_fch1d_step(molt_fch1d* solver, void* u_dev, double dt, void* stream, molt_step_info* info);
+
+/* Kernels launched by this solver so far (host counter). */
+long long molt_fch1d_launches(const molt_fch1d* solver);
+
+
 /* Last error message of `solver` (or of the last failed create/ABI call when NULL). */
 const char* molt_last_error(const molt_solver* solver);
 

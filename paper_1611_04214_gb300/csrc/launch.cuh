@@ -793,6 +793,34 @@ __global__ void cubic_kernel(T* out, long long n, const T* x, T a2, T a1) {
 }  // namespace detail
 
 namespace detail {
+// Sixth-order model: f = v^3 - 3v^2 + 2v and p = -eps2 f'(v) lap + f f'(v) - eta_eps2 f, with
+// f'(v) = 3v^2 - 6v + 2 (the pointwise part of the lagged term).
+template <typename T>
+__global__ void fch_pointwise_kernel(long long n, const T* __restrict__ v, const T* __restrict__ lap, T eps2,
+                                     T eta_eps2, T* __restrict__ f_out, T* __restrict__ p_out) {
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+        const T x = v[i];
+        const T f = x * fma(x, x - T(3), T(2));
+        const T fp = fma(x, fma(T(3), x, T(-6)), T(2));
+        f_out[i] = f;
+        p_out[i] = fma(f, fp, -fma(eps2 * fp, lap[i], eta_eps2 * f));
+    }
+}
+}  // namespace detail
+
+template <typename T>
+cudaError_t fch_pointwise(long long n, const T* v, const T* lap, double eps2, double eta_eps2, T* f_out, T* p_out,
+                          cudaStream_t st, long long* launches) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    detail::fch_pointwise_kernel<T><<<static_cast<int>(blocks), 256, 0, st>>>(
+        n, v, lap, static_cast<T>(eps2), static_cast<T>(eta_eps2), f_out, p_out);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+namespace detail {
 template <typename T>
 __global__ void set_walls_kernel(T* w, int nx, int ny, T value) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -916,4 +944,6 @@ cudaError_t max_abs_diff(const T* a, const T* b, long long n, unsigned long long
     template cudaError_t molt::add_separable<T>(T*, int, int, const molt::Separable&, cudaStream_t, long long*); \
     template cudaError_t molt::fill_pattern<T>(T*, long long, unsigned, double, double, cudaStream_t);         \
     template cudaError_t molt::set_walls<T>(T*, int, int, double, cudaStream_t, long long*);                   \
-    template cudaError_t molt::max_abs_diff<T>(const T*, const T*, long long, unsigned long long*, cudaStream_t);
+    template cudaError_t molt::max_abs_diff<T>(const T*, const T*, long long, unsigned long long*, cudaStream_t); \
+    template cudaError_t molt::fch_pointwise<T>(long long, const T*, const T*, double, double, T*, T*, cudaStream_t, \
+                                                long long*);

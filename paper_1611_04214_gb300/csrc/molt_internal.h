@@ -220,4 +220,10 @@ int reduce_blocks();
 template <typename T>
 cudaError_t max_abs_diff(const T* a, const T* b, long long n, unsigned long long* out, cudaStream_t st);
 
+// Sixth-order model, pointwise: f_out = f(v) = v^3 - 3v^2 + 2v and
+// p_out = -eps2 f'(v) lap + f f'(v) - eta_eps2 f(v), n elements.
+template <typename T>
+cudaError_t fch_pointwise(long long n, const T* v, const T* lap, double eps2, double eta_eps2, T* f_out, T* p_out,
+                          cudaStream_t st, long long* launches);
+
 }  // namespace molt

@@ -32,7 +32,7 @@ EXPORTS = [
     "molt_vch_step", "molt_fma_throughput_probe", "molt_helmholtz_rows_tc", "molt_vch_step_adaptive",
     "molt_batch_autotune", "molt_batch_set_schedule", "molt_autotune", "molt_batch_helmholtz_apply",
     "molt_solver3d_create", "molt_solver3d_destroy", "molt_solver3d_step", "molt_solver3d_apply",
-    "molt_solver3d_launches",
+    "molt_solver3d_launches", "molt_fch1d_create", "molt_fch1d_destroy", "molt_fch1d_step", "molt_fch1d_launches",
 ]
 EXECUTION = {"host_loop": 0, "graph": 1}
 PROFILE_SLOTS = 32
@@ -134,6 +134,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_solver3d_step": ([VP, VP, D, I, VP, ctypes.POINTER(_StepInfo)], I),
         "molt_solver3d_apply": ([VP, I, D, VP, VP, VP], I),
         "molt_solver3d_launches": ([VP], ctypes.c_longlong),
+        "molt_fch1d_create": ([ctypes.POINTER(VP), I, I, D, I, D, ctypes.POINTER(_Params)], I),
+        "molt_fch1d_destroy": ([VP], I),
+        "molt_fch1d_step": ([VP, VP, D, VP, ctypes.POINTER(_StepInfo)], I),
+        "molt_fch1d_launches": ([VP], ctypes.c_longlong),
         "molt_autotune": ([P, VP, ctypes.POINTER(_Tuning), I, ctypes.POINTER(I)], I),
         "molt_batch_step": ([VP, VP, ctypes.POINTER(D), I, VP, ctypes.POINTER(I), ctypes.POINTER(D),
                              ctypes.POINTER(I)], I),
@@ -569,6 +573,59 @@ class Solver3D:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.molt_solver3d_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Fch1D:
+    """BE steps of the sixth-order model on independent 1D lines (molt_fch1d_*): fields [lines][nx]
+    of u (the paper's variable) in FP32 or FP64."""
+
+    def __init__(self, nx: int, lines: int = 1, L: float = 6.283185307179586, bc: str = "periodic",
+                 eps: float = 0.18, eta: float = 1.0, quad_order: int = 6, tol: float = 1e-10, max_iter: int = 500,
+                 precision: str = "fp64"):
+        lib = load_library()
+        self._lib = lib
+        self.shape = (lines, nx)
+        self._itemsize = 4 if precision == "fp32" else 8
+        self._params = _Params(eps, quad_order, PRECISION[precision], tol, max_iter)
+        h = ctypes.c_void_p()
+        _check(lib.molt_fch1d_create(ctypes.byref(h), nx, lines, L, BC[bc], float(eta), ctypes.byref(self._params)))
+        self._h = h
+
+    def _field(self, t):
+        if (not t.is_cuda or t.dtype.itemsize != self._itemsize or not t.is_floating_point() or not t.is_contiguous()
+                or tuple(t.shape) != self.shape):
+            raise ValueError(f"expected a contiguous CUDA tensor of shape {self.shape} with {self._itemsize}-byte floats")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def step(self, u, dt: float, stream=None, raise_on_nonconvergence: bool = True) -> StepInfo:
+        info = _StepInfo()
+        st = self._lib.molt_fch1d_step(self._h, self._field(u), float(dt), _stream_handle(stream), ctypes.byref(info))
+        out = StepInfo(info.status, info.stages, list(info.iters)[: max(info.stages, 0)], info.total_iters,
+                       info.residual, info.tol_used)
+        if st == MOLT_ERR_NOT_CONVERGED and not raise_on_nonconvergence:
+            return out
+        _check(st, None)
+        return out
+
+    def kernel_launches(self) -> int:
+        return int(self._lib.molt_fch1d_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.molt_fch1d_destroy(self._h)
             self._h = None
 
     def __del__(self):

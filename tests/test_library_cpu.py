@@ -90,6 +90,23 @@ def test_solver3d_validation_host_only(lib):
     assert lib.molt_batch_helmholtz_apply(None, 0, None, None, None, None) == -1
 
 
+def test_fch1d_validation_host_only(lib):
+    # molt_fch1d_create checks its arguments before any device work.
+    from paper_1611_04214_gb300 import molt
+    h = ctypes.c_void_p()
+    p = molt._Params(0.18, 6, molt.PRECISION["fp64"], 1e-10, 50)
+    create = lib.molt_fch1d_create
+    assert create(ctypes.byref(h), 128, 4, 6.28, 2, 1.0, ctypes.byref(p)) == molt.MOLT_ERR_UNSUPPORTED   # Dirichlet
+    assert b"periodic and Neumann" in lib.molt_last_error(None)
+    assert create(ctypes.byref(h), 7, 4, 6.28, 0, 1.0, ctypes.byref(p)) == -1               # nx < M + 2
+    assert create(ctypes.byref(h), 1 << 20, 4, 6.28, 0, 1.0, ctypes.byref(p)) == -1         # beyond the row kernel
+    assert create(ctypes.byref(h), 128, 0, 6.28, 0, 1.0, ctypes.byref(p)) == -1             # no lines
+    assert create(ctypes.byref(h), 128, 4, 0.0, 0, 1.0, ctypes.byref(p)) == -1              # bad length
+    assert create(ctypes.byref(h), 128, 4, 6.28, 0, float("nan"), ctypes.byref(p)) == -1    # eta
+    assert create(ctypes.byref(h), 128, 4, 6.28, 0, 1.0, None) == -1
+    assert lib.molt_fch1d_step(None, None, 0.05, None, None) == -1
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_1611_04214_gb300 import molt
     saved = molt._lib
