@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256, 2)
 cols_tma_kernel(const __grid_constant__ LineParams<float> lp, const __grid_constant__ ColMaps maps,
                 const __grid_constant__ PackedStencil pw, const Op op, int nlines, long long ld, int tiles,
                 float* __restrict__ aggL, float* __restrict__ aggR, const float* __restrict__ carL,
-                const float* __restrict__ carR, unsigned* status, unsigned long long* red_slots) {
+                const float* __restrict__ carR, unsigned* status, unsigned long long* red_slots, int rev) {
     using T = float;
     constexpr int KY = 16, WY = 8, R = KY * WY, H = M / 2, ROWS = R + M;
     constexpr int NS = Op::NS, NF = Op::NF, NO = Op::NO, STAGES = tma_col_stages(Op::NS);
@@ -131,8 +131,11 @@ cols_tma_kernel(const __grid_constant__ LineParams<float> lp, const __grid_const
     };
 
     auto stage = [&](int s, int f) { return sm + (static_cast<size_t>(s) * NS + f) * ROWS * 32; };
+    // rev = 1 takes the items from the last tile row up (the block order of the kernel that ran
+    // before decides which end of the field is still in L2); results do not depend on it
+    auto phys = [&](int itm) { return rev ? items - 1 - itm : itm; };
     auto issue = [&](int itm, int s) {
-        const int strip = itm % nstrips, tile = itm / nstrips;
+        const int strip = phys(itm) % nstrips, tile = phys(itm) / nstrips;
         mbar_expect_tx(&full[s], kStageBytes);
 #pragma unroll
         for (int f = 0; f < NS; ++f) tma_load_2d(stage(s, f), &maps.m[f], strip * 32, tile * R - H, &full[s]);
@@ -158,7 +161,7 @@ cols_tma_kernel(const __grid_constant__ LineParams<float> lp, const __grid_const
         const int pb = it & 1;
         const bool arrived = mbar_wait(&full[s], static_cast<unsigned>((it / STAGES) & 1));
 
-        const int strip = item % nstrips, tile = item / nstrips;
+        const int strip = phys(item) % nstrips, tile = phys(item) / nstrips;
         const int line = strip * 32 + lane;
         const int r0 = tile * R - H;
         const int start = tile * R + wy * KY;

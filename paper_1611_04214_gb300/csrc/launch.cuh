@@ -258,7 +258,7 @@ int pipe_cluster(const P& p, int n) {
 // One-block-per-line pipelined row kernel with K positions per thread (n / K threads).
 template <int M, class P, int K>
 cudaError_t rows_pipe_one(const LineParams<float>& lp, const PackedStencil& pw, const P& op, int nlines, long long ld,
-                          size_t smem, unsigned long long* red, cudaStream_t st, Prof* prof, int kind) {
+                          size_t smem, unsigned long long* red, cudaStream_t st, Prof* prof, int kind, int rev) {
     const int TL = lp.n / K;
     auto kern = rows_pipe_kernel<M, P, K>;
     static int limit = smem_optin(kern);
@@ -271,14 +271,14 @@ cudaError_t rows_pipe_one(const LineParams<float>& lp, const PackedStencil& pw, 
     int grid = sms * per_sm;
     if (grid > nlines) grid = nlines;
     prof_begin(prof, kind, st);
-    kern<<<grid, TL, smem, st>>>(lp, pw, op, nlines, ld, red);
+    kern<<<grid, TL, smem, st>>>(lp, pw, op, nlines, ld, red, rev);
     prof_end(prof, st);
     return cudaGetLastError();
 }
 
 template <int M, class P, int C>
 cudaError_t rows_pipe(const LineParams<float>& lp, const P& op, int nlines, unsigned long long* red, cudaStream_t st,
-                      Prof* prof, int kind) {
+                      Prof* prof, int kind, int order) {
     const int n = lp.n;
     const int TL = n / (16 * C);
     const size_t smem = static_cast<size_t>(pipe_smem<P>(n, C));
@@ -287,7 +287,7 @@ cudaError_t rows_pipe(const LineParams<float>& lp, const P& op, int nlines, unsi
     if constexpr (C == 1) {
         // 16 positions per thread at every length (8 for lines of at most 4096 nodes, with twice
         // the warps per block, measured slower)
-        return rows_pipe_one<M, P, 16>(lp, pw, op, nlines, ld, smem, red, st, prof, kind);
+        return rows_pipe_one<M, P, 16>(lp, pw, op, nlines, ld, smem, red, st, prof, kind, order & 1);
     } else {
         auto kern = rows_cluster_kernel<M, P, C>;
         static int limit = smem_optin(kern);
@@ -438,7 +438,8 @@ bool col_tma_maps(const P& op, int nlines, int n, int rows, ColMaps* maps) {
 
 template <int M, class P, bool kFinal>
 cudaError_t cols_tma_launch(const LineParams<float>& lp, const ColMaps& maps, const PackedStencil& pw, const P& op,
-                            int nlines, int tiles, ColScratch<float>* cs, unsigned long long* red, cudaStream_t st) {
+                            int nlines, int tiles, ColScratch<float>* cs, unsigned long long* red, cudaStream_t st,
+                            int rev) {
     constexpr int ROWS = kColR + M;
     const size_t smem = static_cast<size_t>(tma_col_stages(P::NS)) * P::NS * ROWS * 32 * sizeof(float) + 128;
     auto kern = cols_tma_kernel<M, P, kFinal>;
@@ -453,21 +454,21 @@ cudaError_t cols_tma_launch(const LineParams<float>& lp, const ColMaps& maps, co
     int grid = sms * per_sm;
     if (grid > items) grid = items;
     kern<<<grid, 32 * kColWY, smem, st>>>(lp, maps, pw, op, nlines, static_cast<long long>(nlines), tiles, cs->aggL,
-                                          cs->aggR, cs->carL, cs->carR, cs->status, red);
+                                          cs->aggR, cs->carL, cs->carR, cs->status, red, rev);
     count_tma_launch();
     return cudaGetLastError();
 }
 
 template <int M, class P>
 cudaError_t cols_tma(const LineParams<float>& lp, const ColMaps& maps, const P& op, int nlines, ColScratch<float>* cs,
-                     unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof, int kind) {
+                     unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof, int kind, int order) {
     const int n = lp.n;
     const int tiles = (n + kColR - 1) / kColR;
     if (cs == nullptr || cs->capacity_lines < nlines || cs->capacity_fields < P::NF || cs->tiles < tiles)
         return cudaErrorInvalidValue;
     const PackedStencil pw = packed_stencil(lp);
     prof_begin(prof, 8 + kind, st);
-    cudaError_t e = cols_tma_launch<M, P, false>(lp, maps, pw, op, nlines, tiles, cs, red, st);
+    cudaError_t e = cols_tma_launch<M, P, false>(lp, maps, pw, op, nlines, tiles, cs, red, st, order & 1);
     prof_end(prof, st);
     if (e != cudaSuccess) return e;
     const int strips = (nlines + 31) / 32;
@@ -478,15 +479,25 @@ cudaError_t cols_tma(const LineParams<float>& lp, const ColMaps& maps, const P& 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     prof_begin(prof, 17 + kind, st);
-    e = cols_tma_launch<M, P, true>(lp, maps, pw, op, nlines, tiles, cs, red, st);
+    e = cols_tma_launch<M, P, true>(lp, maps, pw, op, nlines, tiles, cs, red, st, (order >> 1) & 1);
     prof_end(prof, st);
     if (launches) *launches += 2;
     return e;
 }
 
+// The alternating block orders of the 2D iteration (OpArgs::order) are on by default;
+// MOLT_BLOCK_ORDER=0 in the environment at launch (or graph capture) time runs every pass from the
+// first line / tile row down.  Results do not depend on it.
+inline bool block_order_enabled() {
+    const char* v = std::getenv("MOLT_BLOCK_ORDER");
+    return !(v && v[0] == '0');
+}
+
 template <typename T, class Op>
-cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int nx, int ny, ColScratch<T>* cs,
+cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a_in, int nx, int ny, ColScratch<T>* cs,
                      unsigned long long* red, cudaStream_t st, long long* launches, Prof* prof, int kind) {
+    OpArgs<T> a = a_in;
+    if (!block_order_enabled()) a.order = 0;
     Op op = build(a, static_cast<Op*>(nullptr));
     // the vector CH passes are timed in the slots of their scalar counterparts
     const int pk = kind == OP_V1 ? OP_P1 : kind == OP_V2 ? OP_P2 : kind == OP_V1A ? OP_1A : kind == OP_C3 ? OP_COPY
@@ -506,12 +517,12 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
             }
             if (C > 0) {
                 switch (lp.M * 8 + C) {
-                    case 2 * 8 + 1: return rows_pipe<2, P, 1>(lp, pop, nlines, red, st, prof, pk);
-                    case 2 * 8 + 2: return rows_pipe<2, P, 2>(lp, pop, nlines, red, st, prof, pk);
-                    case 4 * 8 + 1: return rows_pipe<4, P, 1>(lp, pop, nlines, red, st, prof, pk);
-                    case 4 * 8 + 2: return rows_pipe<4, P, 2>(lp, pop, nlines, red, st, prof, pk);
-                    case 6 * 8 + 1: return rows_pipe<6, P, 1>(lp, pop, nlines, red, st, prof, pk);
-                    case 6 * 8 + 2: return rows_pipe<6, P, 2>(lp, pop, nlines, red, st, prof, pk);
+                    case 2 * 8 + 1: return rows_pipe<2, P, 1>(lp, pop, nlines, red, st, prof, pk, a.order);
+                    case 2 * 8 + 2: return rows_pipe<2, P, 2>(lp, pop, nlines, red, st, prof, pk, a.order);
+                    case 4 * 8 + 1: return rows_pipe<4, P, 1>(lp, pop, nlines, red, st, prof, pk, a.order);
+                    case 4 * 8 + 2: return rows_pipe<4, P, 2>(lp, pop, nlines, red, st, prof, pk, a.order);
+                    case 6 * 8 + 1: return rows_pipe<6, P, 1>(lp, pop, nlines, red, st, prof, pk, a.order);
+                    case 6 * 8 + 2: return rows_pipe<6, P, 2>(lp, pop, nlines, red, st, prof, pk, a.order);
                 }
             }
         }
@@ -539,9 +550,9 @@ cudaError_t dispatch(int axis, const LineParams<T>& lp, const OpArgs<T>& a, int 
                 if (a.variant == LAUNCH_COLS_TMA && !have_maps) return cudaErrorInvalidValue;
                 if (have_maps) {
                     switch (lp.M) {
-                        case 2: return cols_tma<2>(lp, maps, pop, nlines, cs, red, st, launches, prof, pk);
-                        case 4: return cols_tma<4>(lp, maps, pop, nlines, cs, red, st, launches, prof, pk);
-                        case 6: return cols_tma<6>(lp, maps, pop, nlines, cs, red, st, launches, prof, pk);
+                        case 2: return cols_tma<2>(lp, maps, pop, nlines, cs, red, st, launches, prof, pk, a.order);
+                        case 4: return cols_tma<4>(lp, maps, pop, nlines, cs, red, st, launches, prof, pk, a.order);
+                        case 6: return cols_tma<6>(lp, maps, pop, nlines, cs, red, st, launches, prof, pk, a.order);
                     }
                 }
                 switch (lp.M) {

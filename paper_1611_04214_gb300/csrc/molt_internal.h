@@ -111,6 +111,10 @@ struct OpArgs {
     T vs = 0;       // vector CH: s = (c1 + c2)/tau
     int comp = 0;   // vector CH: component of the pass
     int variant = 0;   // launch choice (Launch); 0 = the default for the line length and field count
+    // Block order over the field, for L2 reuse between consecutive passes (results do not depend
+    // on it): rows, bit 0 = lines from the last one up; TMA columns, bit 0 = the aggregate phase
+    // from the last tile row up, bit 1 = the same for the final phase.  Other kernels ignore it.
+    int order = 0;
 };
 
 // Kernel choices of one sweep, picked by the solver's autotuner (the values of molt_launch in

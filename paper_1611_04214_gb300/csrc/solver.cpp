@@ -619,15 +619,20 @@ struct Solver final : molt_solver {
         if (ps.vch) return launch_vch_iteration(ps, st);
         cudaError_t e;
         if (ps.two_d) {
+            // Block orders alternate so that each pass starts at the end of the field the pass
+            // before it finished on (still in L2): pass 4 ends at the last row, pass 1 aggregates
+            // from the last tile row up and finishes from the first down, pass 2 runs from the
+            // last line up, pass 3 aggregates from the first tile row down and finishes from the
+            // last up, and pass 4 starts again at the first line.
             molt::OpArgs<T> a1;
-            a1.in0 = w; a1.out0 = f1; a1.out1 = f2; a1.g2 = ps.g2; a1.g1 = ps.g1;
+            a1.in0 = w; a1.out0 = f1; a1.out1 = f2; a1.g2 = ps.g2; a1.g1 = ps.g1; a1.order = 1;
             if ((e = sweep(1, ps.liy, molt::OP_P1, a1, st)) != cudaSuccess) return e;
             molt::OpArgs<T> a2;
             a2.in0 = w; a2.in1 = f1; a2.in2 = f2; a2.out0 = f3; a2.out1 = f4;
-            a2.g2 = ps.g2; a2.g1 = ps.g1; a2.beta = ps.beta;
+            a2.g2 = ps.g2; a2.g1 = ps.g1; a2.beta = ps.beta; a2.order = 1;
             if ((e = sweep(0, ps.lix, molt::OP_P2, a2, st)) != cudaSuccess) return e;
             molt::OpArgs<T> a3;
-            a3.in0 = f3; a3.in1 = f4; a3.out0 = f5; a3.out1 = f6;
+            a3.in0 = f3; a3.in1 = f4; a3.out0 = f5; a3.out1 = f6; a3.order = 2;
             if ((e = sweep(1, ps.loy, molt::OP_P3, a3, st)) != cudaSuccess) return e;
             molt::OpArgs<T> a4;
             a4.in0 = f5; a4.in1 = f6; a4.in2 = f4; a4.in3 = Y; a4.out0 = w; a4.shift = ps.s;

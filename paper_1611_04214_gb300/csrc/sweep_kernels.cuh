@@ -327,7 +327,7 @@ __device__ __forceinline__ void set4(float4& v, int e, float x) {
 template <int M, class Op, int KT = 16>
 __global__ void __launch_bounds__(512, 1)
 rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_constant__ PackedStencil pw, const Op op,
-                 int nlines, long long ld, unsigned long long* red_slots) {
+                 int nlines, long long ld, unsigned long long* red_slots, int rev) {
     using T = float;
     constexpr int K = KT, V = 4, KC = K / V, H = M / 2, WC = KC + 2;
     static_assert(K % V == 0 && K >= 8, "whole 16-byte chunks per thread, at least one wall stencil");
@@ -364,11 +364,15 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
         }
     };
 
+    // rev = 1 takes the lines from the last one up (the block order of the pass that ran before
+    // decides which end of the field is still in L2)
+    auto phys = [&](int l) { return rev ? nlines - 1 - l : l; };
     RedAcc<T> red{T(0), T(0)};
-    int line = blockIdx.x;
-    if (line < nlines) issue_staged(line, 0);
+    int li = blockIdx.x;
+    if (li < nlines) issue_staged(phys(li), 0);
     cp_async_commit();
-    for (int it = 0; line < nlines; ++it, line += gridDim.x) {
+    for (int it = 0; li < nlines; ++it, li += gridDim.x) {
+        const int line = phys(li);
         const int sb = it & 1;
         cp_async_wait<0>();          // this line's staged fields (the only group in flight)
         __syncthreads();             // ... visible to all; every warp is done with the last line
@@ -380,8 +384,8 @@ rows_pipe_kernel(const __grid_constant__ LineParams<float> lp, const __grid_cons
             for (int c = tid; c < nch; c += TL) cp_async16(dst + swz(c), src + c);
         }
         cp_async_commit();
-        const int next = line + gridDim.x;
-        if (next < nlines) issue_staged(next, sb ^ 1);
+        const int next = li + gridDim.x;
+        if (next < nlines) issue_staged(phys(next), sb ^ 1);
         cp_async_commit();
 
         // ---- window (prologue applied) from chunks start/V - 1 .. start/V + KC ----
