@@ -285,8 +285,16 @@ cudaError_t rows_pipe(const LineParams<float>& lp, const P& op, int nlines, unsi
     const PackedStencil pw = packed_stencil(lp);
     const long long ld = n;
     if constexpr (C == 1) {
-        // 16 positions per thread at every length (8 for lines of at most 4096 nodes, with twice
-        // the warps per block, measured slower)
+        // single-field copy sweeps of lines of at least 4096 nodes: 32 positions per thread (half
+        // the warps, about 115 registers), so two blocks share an SM and two lines are in flight
+        // (8192 nodes: 146 -> 124 us per 8192^2 sweep); MOLT_ROWS_K32=0 keeps 16
+        if constexpr (std::is_same<P, PipeCopy<float>>::value) {
+            const char* v = std::getenv("MOLT_ROWS_K32");
+            if (!(v && v[0] == '0') && n >= 4096 && n % 1024 == 0)
+                return rows_pipe_one<M, P, 32>(lp, pw, op, nlines, ld, smem, red, st, prof, kind, order & 1);
+        }
+        // otherwise 16 positions per thread (8 for lines of at most 4096 nodes, with twice the
+        // warps per block, measured slower)
         return rows_pipe_one<M, P, 16>(lp, pw, op, nlines, ld, smem, red, st, prof, kind, order & 1);
     } else {
         auto kern = rows_cluster_kernel<M, P, C>;
