@@ -180,7 +180,9 @@ struct Fch1d final : molt_fch1d {
             info->residual = res;
             info->tol_used = tol_used;
         }
-        if (!converged) molt::set_abi_error("the sixth-order stage reached max_iter before the fixed-point tolerance");
+        if (!converged)
+            molt::set_abi_error(std::isfinite(res) ? "the sixth-order stage reached max_iter before the fixed-point tolerance"
+                                                   : "the sixth-order iteration diverged (non-finite residual)");
         return converged ? MOLT_OK : MOLT_ERR_NOT_CONVERGED;
     }
 };

@@ -227,7 +227,9 @@ molt_status stage3(molt_solver3d* s, double tau, cudaStream_t st, int* iters, do
     *iters = converged ? k : std::min(k, s->p.max_iter);
     *res_out = res;
     *tol_out = tol_used;
-    if (!converged) molt::set_abi_error("the 3D stage reached max_iter before the fixed-point tolerance");
+    if (!converged)
+        molt::set_abi_error(std::isfinite(res) ? "the 3D stage reached max_iter before the fixed-point tolerance"
+                                               : "the 3D iteration diverged (non-finite residual)");
     return converged ? MOLT_OK : MOLT_ERR_NOT_CONVERGED;
 }
 
