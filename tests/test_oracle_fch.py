@@ -1,7 +1,8 @@
 """Pins of the 1D FCH oracle (``oracle/fch.py``) against things other than itself.
 
 * A small mode about u = -1 decays in one BE step by the linearised rate of Eq. FCH0:
-  1 / (1 + dt k^2 (eps^2 k^2 + 2)(eps^2 k^2 + 2 - eta eps^2)).
+  1 / (1 + dt k^2 (eps^2 k^2 + 2)(eps^2 k^2 + 2 - eta eps^2)), periodic and, for cosine modes
+  with nodes on the walls, Neumann.
 * The converged step solves the BE equation of the PDE with the discrete Laplacian the line
   inverse implies (symbol (1/h(k) - 1)/a, measured by FFT of H's impulse response), evaluated
   pointwise and by FFT, independently of the iteration's rearrangement; the printed signs of
@@ -34,6 +35,20 @@ def test_small_mode_decays_at_the_linear_rate(k, dt):
     k2 = float(k * k)
     rate = 1.0 / (1.0 + dt * k2 * (eps ** 2 * k2 + 2) * (eps ** 2 * k2 + 2 - eta * eps ** 2))
     np.testing.assert_allclose(u1 + 1.0, rate * (u0 + 1.0), rtol=0, atol=1e-4 * amp)
+
+
+@pytest.mark.parametrize("m", [2, 4, 6])
+def test_neumann_cosine_mode_decays_at_the_linear_rate(m):
+    # cos(m x / 2) on [0, 2pi] with nodes on both walls is a Neumann mode (wavenumber m / 2): the
+    # walls' boundary correction and shifted stencils must reproduce the same linear rate.
+    from paper_1611_04214_gb300.inputs import nodes
+    n, eps, eta, amp, dt = 129, 0.18, 1.0, 1e-7, 0.05
+    prob = Problem(nx=n, eps=eps, M=6, tol=1e-16, max_iter=400, bc="neumann")
+    kap2 = (m / 2.0) ** 2
+    u0 = (-1.0 + amp * np.cos(0.5 * m * nodes(n, 2 * np.pi, False)))[None, :]
+    u1, res = FchSolver(prob, eta).step(u0, dt)
+    rate = 1.0 / (1.0 + dt * kap2 * (eps ** 2 * kap2 + 2) * (eps ** 2 * kap2 + 2 - eta * eps ** 2))
+    np.testing.assert_allclose(u1 + 1.0, rate * (u0 + 1.0), rtol=0, atol=1e-6 * amp)
 
 
 def _discrete_lap(prob, a):
