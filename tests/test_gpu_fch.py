@@ -4,6 +4,7 @@ FCH oracle (``oracle/fch.py``).
 * Fixed iteration counts (tol below reach) on both sides, FP64, periodic and Neumann, four
   different lines per field (a ragged line of 200 nodes spans 13 chunks of 16 with a tail of 8):
   held to 1e-11 of max|v|.
+* Fixed iteration counts with M = 2, 4 and eta = 1, 3 (FP64, 1e-11 of max|v|).
 * Converged steps, FP64, to the same tolerance on both sides: iteration counts within 2 and the
   fields within 1e-10 (the iteration contracts with rho = 0.95 at dt = 0.05, eps = 0.18, so each
   side's distance to the fixed point is below tol rho / (1 - rho) = 2e-12).
@@ -46,14 +47,14 @@ def _lines(n, periodic):
                      uniform_noise((1, n), 0.05, seed=4, mean=0.2)[0]])
 
 
-def _run_both(u0, bc, steps, tol, max_iter, precision="fp64", oracle_tol=None, dt=DT):
+def _run_both(u0, bc, steps, tol, max_iter, precision="fp64", oracle_tol=None, dt=DT, M=6, eta=ETA):
     from paper_1611_04214_gb300.molt import Fch1D
     lines, n = u0.shape
-    prob = Problem(nx=n, eps=EPS, M=6, tol=oracle_tol or tol, max_iter=max_iter, bc=bc)
-    o = OracleFch(prob, ETA)
+    prob = Problem(nx=n, eps=EPS, M=M, tol=oracle_tol or tol, max_iter=max_iter, bc=bc)
+    o = OracleFch(prob, eta)
     dtype = torch.float32 if precision == "fp32" else torch.float64
     ref, its_o, its_g, rho = u0.astype(np.float64), [], [], 0.0
-    with Fch1D(n, lines, bc=bc, eps=EPS, eta=ETA, quad_order=6, tol=tol, max_iter=max_iter,
+    with Fch1D(n, lines, bc=bc, eps=EPS, eta=eta, quad_order=M, tol=tol, max_iter=max_iter,
                precision=precision) as s:
         u = torch.tensor(u0, dtype=dtype, device="cuda")
         for _ in range(steps):
@@ -76,6 +77,17 @@ def test_fch_fixed_iterations_fp64(bc, n):
     assert ig == io == [25, 25], (ig, io)
     assert launches > 2 * 25 * 14
     check_fp64(f"fch1d_{n}x4_{bc}_2steps_25it_fp64", got, ref, 1e-11 * np.abs(ref + 1).max())
+
+
+@pytest.mark.parametrize("eta", [1.0, 3.0])
+@pytest.mark.parametrize("M", [2, 4])
+@pytest.mark.parametrize("bc,n", [("periodic", 200), ("neumann", 136)])
+def test_fch_orders_and_eta_fp64(bc, n, M, eta):
+    # the quadrature orders M = 2, 4 and a stronger eta (both contract at dt = 0.05, rho <= 0.95)
+    u0 = _lines(n, bc == "periodic")
+    got, ref, ig, io, _, _ = _run_both(u0, bc, 1, 1e-30, 15, M=M, eta=eta)
+    assert ig == io == [15], (ig, io)
+    check_fp64(f"fch1d_{n}x4_{bc}_M{M}_eta{eta:g}_1step_15it_fp64", got, ref, 1e-11 * np.abs(ref + 1).max())
 
 
 @pytest.mark.parametrize("bc,n", [("periodic", 200), ("neumann", 136)])
