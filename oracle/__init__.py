@@ -24,8 +24,9 @@ notation, with no blocking, fusion or reordering:
                   BDF2 steps and energy (Sec. 5.2).
 * ``split3d``   - the splitting of Sec. 5.1 carried to three dimensions (the
                   extension the paper remarks on), BE and BDF2.
-* ``fch``       - the sixth-order model of Eq. FCH0 / FCH in 1D, BE by completing
-                  the cube (Eq. FCH_BE, with the PDE's signs).
+* ``fch``       - the sixth-order model of Eq. FCH0 / FCH in 1D and 2D, BE by
+                  completing the cube (Eq. FCH_BE, with the PDE's signs); in 2D with
+                  the splitting of Sec. 5.1 for the three equal factors.
 
 Readings of passages the paper leaves open are listed in each docstring.
 """

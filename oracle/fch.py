@@ -1,4 +1,4 @@
-"""The sixth-order (functionalized) Cahn-Hilliard model of the paper's last section, 1D, FP64.
+"""The sixth-order (functionalized) Cahn-Hilliard model of the paper's last section, 1D and 2D, FP64.
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
@@ -104,4 +104,110 @@ class FchSolver:
         return res.v - 1.0, res
 
 
-__all__ = ["f_v", "fp_v", "fch_be_step", "FchSolver", "FchResult"]
+# ---- 2D (the paper's section is the 2D model, solved "by the procedure of Sec. 5.1") ----------
+#
+# Reading (the paper gives the cube and refers to the 2D splitting for the rest).  Sec. 5.1 replaces
+# I - a Lap by the split product M = L_x L_y, L = I - a d_aa, and absorbs the remainder in the
+# iteration: I - a Lap = M (I - X) with X = D_x D_y, D_a = H_a - I, H_a = L_a^{-1} (its sign does
+# not matter in the product).  All of these commute, so (I - a Lap)^3 = M^3 (I - X)^3 and the BE
+# equation (I - a Lap)^3 v = R(v) = v^n + dt Lap g(v) - (3a Lap - 3a^2 Lap^2) v becomes the lagged
+#     v^{k+1} = M^{-3} R(v^k) + (1 - (1 - X)^3) v^k,
+# the 2D iteration of Sec. 5.1 with three equal factors (it reduces to the 1D one above for X = 0).
+# Every Lap comes with an M^{-1}: K = M^{-1} a Lap = D_x H_y + H_x D_y = 2 M^{-1} - H_x - H_y, so
+#     v^{k+1} = M^{-1} W^{k+1},
+#     W^{k+1} = M^{-2} v^n - 3 M^{-1} K v + (3 + c_eta) K^2 v - c_f K^2 f + c_p M^{-1} K p
+#               + (3X - 3X^2 + X^3) W^k,
+# with c_eta, c_f, c_p and p as in 1D.  Keeping the iterate as v = M^{-1} W (the lagged term commutes
+# with M^{-1}, so (1 - (1-X)^3) v^k = M^{-1} (1 - (1-X)^3) W^k) gives Lap v = K W / a exactly for the
+# discrete operators, which the product f' Lap v needs (in 1D, W is z and K W = v - z).  The first
+# step starts from W^0 = v^n (v^0 = M^{-1} v^n, Lap v^0 = K v^n / a); later steps carry W.  The
+# fixed point does not depend on the start.  One iteration is 26 line sweeps.
+
+
+@dataclass
+class Fch2DResult:
+    v: np.ndarray
+    w: np.ndarray          # W of the last iterate (v = M^{-1} W)
+    lap_v: np.ndarray
+    iters: int
+    residual: float
+    converged: bool
+    history: list
+
+
+def fch2d_be_step(prob: Problem, vn: np.ndarray, dt: float, eta: float, w0=None) -> Fch2DResult:
+    """One BE step of Eq. FCH on a 2D grid (ny, nx) by the iteration above; w0 is W from the
+    previous step (None for initial data)."""
+    eps = prob.eps
+    a = (dt * eps ** 4) ** (1.0 / 3.0)
+    c_eta, c_f, c_p = dt * eta * eps ** 4 / a ** 2, dt * eps ** 2 / a ** 2, dt / a
+
+    def Hx(g):
+        return helmholtz_inverse(g, a, prob.hx, prob.bc, prob.M, axis=1)
+
+    def Hy(g):
+        return helmholtz_inverse(g, a, prob.hy, prob.bc, prob.M, axis=0)
+
+    def parts(g):
+        """(H_x g, H_y g, M^{-1} g = H_x H_y g)"""
+        hy = Hy(g)
+        return Hx(g), hy, Hx(hy)
+
+    def K(g):
+        """K g = M^{-1} a Lap g = 2 M^{-1} g - H_x g - H_y g, and M^{-1} g"""
+        hx, hy, m = parts(g)
+        return 2 * m - hx - hy, m
+
+    def X(g):
+        """X g = D_x D_y g = M^{-1} g - H_x g - H_y g + g"""
+        hx, hy, m = parts(g)
+        return m - hx - hy + g
+
+    vn = np.asarray(vn, dtype=np.float64)
+    m2_vn = Hx(Hy(Hx(Hy(vn))))
+    W = np.array(vn if w0 is None else w0, dtype=np.float64)
+    hxw, hyw, v = parts(W)
+    lap = (2 * v - hxw - hyw) / a
+    xw = v - hxw - hyw + W
+    res, hist = np.inf, []
+    for k in range(1, prob.max_iter + 1):
+        f, fp = f_v(v), fp_v(v)
+        p = -eps ** 2 * fp * lap + f * fp - eta * eps ** 2 * f
+        kv, _ = K(v)
+        kkv, mkv = K(kv)
+        kf, _ = K(f)
+        kkf, _ = K(kf)
+        kp, _ = K(p)
+        mkp = Hx(Hy(kp))
+        x2w = X(xw)
+        x3w = X(x2w)
+        W_new = (m2_vn - 3 * mkv + (3 + c_eta) * kkv - c_f * kkf + c_p * mkp
+                 + 3 * xw - 3 * x2w + x3w)
+        hxw, hyw, v_new = parts(W_new)
+        lap = (2 * v_new - hxw - hyw) / a
+        xw = v_new - hxw - hyw + W_new
+        res = float(np.max(np.abs(v_new - v)))
+        hist.append(res)
+        v, W = v_new, W_new
+        if res < prob.tol:
+            return Fch2DResult(v, W, lap, k, res, True, hist)
+    return Fch2DResult(v, W, lap, prob.max_iter, res, False, hist)
+
+
+class Fch2DSolver:
+    """BE steps of Eq. FCH in the physical variable u (internally v = u + 1), 2D (ny, nx)."""
+
+    def __init__(self, prob: Problem, eta: float):
+        if prob.dim != 2:
+            raise ValueError("the 2D FCH oracle needs ny > 1")
+        self.prob, self.eta = prob, eta
+        self.w = None
+
+    def step(self, u: np.ndarray, dt: float):
+        res = fch2d_be_step(self.prob, np.asarray(u, dtype=np.float64) + 1.0, dt, self.eta, self.w)
+        self.w = res.w
+        return res.v - 1.0, res
+
+
+__all__ = ["f_v", "fp_v", "fch_be_step", "FchSolver", "FchResult", "fch2d_be_step", "Fch2DSolver",
+           "Fch2DResult"]
