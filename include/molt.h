@@ -484,6 +484,37 @@ molt_status molt_fch1d_step(molt_fch1d* solver, void* u_dev, double dt, void* st
 /* Kernels launched by this solver so far (host counter). */
 long long molt_fch1d_launches(const molt_fch1d* solver);
 
+/* ---- Sixth-order model on a 2D grid (the paper's case) -----------------------------------------
+ * Eq. FCH0 / FCH with BE and the cube completed as for molt_fch1d_*, split as in Sec. 5.1: with
+ * M^{-1} = H_x H_y (line inverses of I - a d_xx, I - a d_yy, a = (dt eps^4)^(1/3)) and
+ * X = D_x D_y, I - a Lap = M (I - X), and the lagged iteration is v <- M^{-3} R(v) + (1 - (1-X)^3) v
+ * (R as in 1D).  With K = M^{-1} a Lap = 2 M^{-1} - H_x - H_y the iterate is kept as v = M^{-1} W,
+ *   W <- M^{-2} v^n - 3 M^{-1} K v + (3 + c_eta) K^2 v - c_f K^2 f + c_p M^{-1} K p
+ *        + (3X - 3X^2 + X^3) W,
+ * so that Lap v = K W / a exactly (the first step starts from W = v^n; later steps carry W).
+ * Fields [ny][nx] row-major, x fastest, FP32 or FP64 per params->precision, periodic or Neumann
+ * (the grid conventions of molt_grid_create).  Each iteration runs 26 one-field line sweeps, one
+ * pointwise kernel and 12 linear combinations, and synchronizes `stream` to read the residual.
+ * Errors are reported by molt_last_error(NULL). */
+typedef struct molt_fch2d molt_fch2d;
+
+/* nx in [M + 2, the one-field row kernel's limit], ny >= M + 2, nx * ny < 2^31, Lx, Ly > 0, bc
+ * periodic or Neumann, eta finite; params as molt_solver_create.  The solver owns 24 fields of
+ * nx * ny values and the column scan scratch.  Errors: MOLT_ERR_ARG, MOLT_ERR_UNSUPPORTED
+ * (Dirichlet), MOLT_ERR_OOM. */
+molt_status molt_fch2d_create(molt_fch2d** solver, int nx, int ny, double Lx, double Ly, molt_bc bc, double eta,
+                              const molt_params* params);
+molt_status molt_fch2d_destroy(molt_fch2d* solver);
+
+/* One BE step in place on the device field u_dev (float* or double* per the precision), with
+ * molt_fch1d_step's stopping rule and info.  Errors: MOLT_ERR_ARG, MOLT_ERR_NOT_CONVERGED (the
+ * field holds the last iterate), MOLT_ERR_CUDA (also when a column kernel's bounded wait for a
+ * tile copy ran out). */
+molt_status molt_fch2d_step(molt_fch2d* solver, void* u_dev, double dt, void* stream, molt_step_info* info);
+
+/* Kernels launched by this solver so far (host counter). */
+long long molt_fch2d_launches(const molt_fch2d* solver);
+
 
 /* Last error message of `solver` (or of the last failed create/ABI call when NULL). */
 const char* molt_last_error(const molt_solver* solver);

@@ -19,7 +19,7 @@ BUILD_DIR = os.path.join(ROOT, "_build")
 SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "kernels_p1.cu", "kernels_p2.cu", "kernels_p3.cu", "kernels_p4.cu",
            "kernels_v1.cu", "kernels_v2.cu", "kernels_c3.cu", "kernels_vch_f32.cu", "kernels_vch_f64.cu", "line_params.cpp", "solver.cpp",
            "noalloc.cu", "batch.cu", "selftest.cu", "probe.cu", "rows_tc.cu", "solver3d.cpp",
-           "fch1d.cpp"]
+           "fch1d.cpp", "fch2d.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]
 

@@ -33,6 +33,7 @@ EXPORTS = [
     "molt_batch_autotune", "molt_batch_set_schedule", "molt_autotune", "molt_batch_helmholtz_apply",
     "molt_solver3d_create", "molt_solver3d_destroy", "molt_solver3d_step", "molt_solver3d_apply",
     "molt_solver3d_launches", "molt_fch1d_create", "molt_fch1d_destroy", "molt_fch1d_step", "molt_fch1d_launches",
+    "molt_fch2d_create", "molt_fch2d_destroy", "molt_fch2d_step", "molt_fch2d_launches",
 ]
 EXECUTION = {"host_loop": 0, "graph": 1}
 PROFILE_SLOTS = 32
@@ -138,6 +139,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_fch1d_destroy": ([VP], I),
         "molt_fch1d_step": ([VP, VP, D, VP, ctypes.POINTER(_StepInfo)], I),
         "molt_fch1d_launches": ([VP], ctypes.c_longlong),
+        "molt_fch2d_create": ([ctypes.POINTER(VP), I, I, D, D, I, D, ctypes.POINTER(_Params)], I),
+        "molt_fch2d_destroy": ([VP], I),
+        "molt_fch2d_step": ([VP, VP, D, VP, ctypes.POINTER(_StepInfo)], I),
+        "molt_fch2d_launches": ([VP], ctypes.c_longlong),
         "molt_autotune": ([P, VP, ctypes.POINTER(_Tuning), I, ctypes.POINTER(I)], I),
         "molt_batch_step": ([VP, VP, ctypes.POINTER(D), I, VP, ctypes.POINTER(I), ctypes.POINTER(D),
                              ctypes.POINTER(I)], I),
@@ -639,3 +644,38 @@ class Fch1D:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Fch2D(Fch1D):
+    """BE steps of the sixth-order model on a 2D grid (molt_fch2d_*): fields [ny][nx] of u in FP32
+    or FP64."""
+
+    def __init__(self, nx: int, ny: int, Lx: float = 6.283185307179586, Ly: float = 6.283185307179586,
+                 bc: str = "periodic", eps: float = 0.18, eta: float = 1.0, quad_order: int = 6, tol: float = 1e-10,
+                 max_iter: int = 500, precision: str = "fp64"):
+        lib = load_library()
+        self._lib = lib
+        self.shape = (ny, nx)
+        self._itemsize = 4 if precision == "fp32" else 8
+        self._params = _Params(eps, quad_order, PRECISION[precision], tol, max_iter)
+        h = ctypes.c_void_p()
+        _check(lib.molt_fch2d_create(ctypes.byref(h), nx, ny, Lx, Ly, BC[bc], float(eta), ctypes.byref(self._params)))
+        self._h = h
+
+    def step(self, u, dt: float, stream=None, raise_on_nonconvergence: bool = True) -> StepInfo:
+        info = _StepInfo()
+        st = self._lib.molt_fch2d_step(self._h, self._field(u), float(dt), _stream_handle(stream), ctypes.byref(info))
+        out = StepInfo(info.status, info.stages, list(info.iters)[: max(info.stages, 0)], info.total_iters,
+                       info.residual, info.tol_used)
+        if st == MOLT_ERR_NOT_CONVERGED and not raise_on_nonconvergence:
+            return out
+        _check(st, None)
+        return out
+
+    def kernel_launches(self) -> int:
+        return int(self._lib.molt_fch2d_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.molt_fch2d_destroy(self._h)
+            self._h = None

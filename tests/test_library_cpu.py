@@ -107,6 +107,23 @@ def test_fch1d_validation_host_only(lib):
     assert lib.molt_fch1d_step(None, None, 0.05, None, None) == -1
 
 
+def test_fch2d_validation_host_only(lib):
+    # molt_fch2d_create checks its arguments before any device work.
+    from paper_1611_04214_gb300 import molt
+    h = ctypes.c_void_p()
+    p = molt._Params(0.18, 6, molt.PRECISION["fp64"], 1e-10, 50)
+    create = lib.molt_fch2d_create
+    assert create(ctypes.byref(h), 128, 128, 6.28, 6.28, 2, 1.0, ctypes.byref(p)) == molt.MOLT_ERR_UNSUPPORTED
+    assert b"periodic and Neumann" in lib.molt_last_error(None)
+    assert create(ctypes.byref(h), 7, 128, 6.28, 6.28, 0, 1.0, ctypes.byref(p)) == -1          # nx < M + 2
+    assert create(ctypes.byref(h), 128, 7, 6.28, 6.28, 0, 1.0, ctypes.byref(p)) == -1          # ny < M + 2
+    assert create(ctypes.byref(h), 1 << 20, 128, 6.28, 6.28, 0, 1.0, ctypes.byref(p)) == -1    # beyond the rows
+    assert create(ctypes.byref(h), 128, 128, 6.28, -1.0, 0, 1.0, ctypes.byref(p)) == -1        # bad length
+    assert create(ctypes.byref(h), 128, 128, 6.28, 6.28, 0, float("inf"), ctypes.byref(p)) == -1
+    assert create(ctypes.byref(h), 128, 128, 6.28, 6.28, 0, 1.0, None) == -1
+    assert lib.molt_fch2d_step(None, None, 0.05, None, None) == -1
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_1611_04214_gb300 import molt
     saved = molt._lib
