@@ -593,20 +593,20 @@ class Solver3D:
         self.close()
 
 
-class Fch1D:
-    """BE steps of the sixth-order model on independent 1D lines (molt_fch1d_*): fields [lines][nx]
-    of u (the paper's variable) in FP32 or FP64."""
+class _FchSteps:
+    """Argument marshalling shared by the sixth-order solvers (``<prefix>_create / _step /
+    _launches / _destroy`` of molt_fch1d_* and molt_fch2d_*)."""
 
-    def __init__(self, nx: int, lines: int = 1, L: float = 6.283185307179586, bc: str = "periodic",
-                 eps: float = 0.18, eta: float = 1.0, quad_order: int = 6, tol: float = 1e-10, max_iter: int = 500,
-                 precision: str = "fp64"):
+    _prefix = ""
+
+    def _open(self, shape, precision: str, eps: float, quad_order: int, tol: float, max_iter: int, create_args):
         lib = load_library()
         self._lib = lib
-        self.shape = (lines, nx)
+        self.shape = tuple(shape)
         self._itemsize = 4 if precision == "fp32" else 8
         self._params = _Params(eps, quad_order, PRECISION[precision], tol, max_iter)
         h = ctypes.c_void_p()
-        _check(lib.molt_fch1d_create(ctypes.byref(h), nx, lines, L, BC[bc], float(eta), ctypes.byref(self._params)))
+        _check(getattr(lib, self._prefix + "_create")(ctypes.byref(h), *create_args, ctypes.byref(self._params)))
         self._h = h
 
     def _field(self, t):
@@ -616,8 +616,10 @@ class Fch1D:
         return ctypes.c_void_p(t.data_ptr())
 
     def step(self, u, dt: float, stream=None, raise_on_nonconvergence: bool = True) -> StepInfo:
+        """One BE step in place on u; StepInfo with the iterations, residual and tolerance used."""
         info = _StepInfo()
-        st = self._lib.molt_fch1d_step(self._h, self._field(u), float(dt), _stream_handle(stream), ctypes.byref(info))
+        st = getattr(self._lib, self._prefix + "_step")(self._h, self._field(u), float(dt), _stream_handle(stream),
+                                                        ctypes.byref(info))
         out = StepInfo(info.status, info.stages, list(info.iters)[: max(info.stages, 0)], info.total_iters,
                        info.residual, info.tol_used)
         if st == MOLT_ERR_NOT_CONVERGED and not raise_on_nonconvergence:
@@ -626,11 +628,11 @@ class Fch1D:
         return out
 
     def kernel_launches(self) -> int:
-        return int(self._lib.molt_fch1d_launches(self._h))
+        return int(getattr(self._lib, self._prefix + "_launches")(self._h))
 
     def close(self):
         if getattr(self, "_h", None):
-            self._lib.molt_fch1d_destroy(self._h)
+            getattr(self._lib, self._prefix + "_destroy")(self._h)
             self._h = None
 
     def __del__(self):
@@ -646,36 +648,25 @@ class Fch1D:
         self.close()
 
 
-class Fch2D(Fch1D):
+class Fch1D(_FchSteps):
+    """BE steps of the sixth-order model on independent 1D lines (molt_fch1d_*): fields [lines][nx]
+    of u (the paper's variable) in FP32 or FP64."""
+
+    _prefix = "molt_fch1d"
+
+    def __init__(self, nx: int, lines: int = 1, L: float = 6.283185307179586, bc: str = "periodic",
+                 eps: float = 0.18, eta: float = 1.0, quad_order: int = 6, tol: float = 1e-10, max_iter: int = 500,
+                 precision: str = "fp64"):
+        self._open((lines, nx), precision, eps, quad_order, tol, max_iter, (nx, lines, L, BC[bc], float(eta)))
+
+
+class Fch2D(_FchSteps):
     """BE steps of the sixth-order model on a 2D grid (molt_fch2d_*): fields [ny][nx] of u in FP32
     or FP64."""
+
+    _prefix = "molt_fch2d"
 
     def __init__(self, nx: int, ny: int, Lx: float = 6.283185307179586, Ly: float = 6.283185307179586,
                  bc: str = "periodic", eps: float = 0.18, eta: float = 1.0, quad_order: int = 6, tol: float = 1e-10,
                  max_iter: int = 500, precision: str = "fp64"):
-        lib = load_library()
-        self._lib = lib
-        self.shape = (ny, nx)
-        self._itemsize = 4 if precision == "fp32" else 8
-        self._params = _Params(eps, quad_order, PRECISION[precision], tol, max_iter)
-        h = ctypes.c_void_p()
-        _check(lib.molt_fch2d_create(ctypes.byref(h), nx, ny, Lx, Ly, BC[bc], float(eta), ctypes.byref(self._params)))
-        self._h = h
-
-    def step(self, u, dt: float, stream=None, raise_on_nonconvergence: bool = True) -> StepInfo:
-        info = _StepInfo()
-        st = self._lib.molt_fch2d_step(self._h, self._field(u), float(dt), _stream_handle(stream), ctypes.byref(info))
-        out = StepInfo(info.status, info.stages, list(info.iters)[: max(info.stages, 0)], info.total_iters,
-                       info.residual, info.tol_used)
-        if st == MOLT_ERR_NOT_CONVERGED and not raise_on_nonconvergence:
-            return out
-        _check(st, None)
-        return out
-
-    def kernel_launches(self) -> int:
-        return int(self._lib.molt_fch2d_launches(self._h))
-
-    def close(self):
-        if getattr(self, "_h", None):
-            self._lib.molt_fch2d_destroy(self._h)
-            self._h = None
+        self._open((ny, nx), precision, eps, quad_order, tol, max_iter, (nx, ny, Lx, Ly, BC[bc], float(eta)))
