@@ -92,8 +92,18 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         raise ImportError(f"{path} is missing: build it with `python -m paper_1611_04214_gb300.build` "
                           "(the library has no CPU fallback)")
     lib = ctypes.CDLL(path)
+    for name, (args, res) in signatures().items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def signatures() -> dict:
+    """ctypes argument and result types of every entry point of include/molt.h."""
     P, I, D, VP = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
-    sig = {
+    return {
         "molt_grid_create": ([ctypes.POINTER(P), I, I, I, D, D, I], I),
         "molt_grid_destroy": ([P], None),
         "molt_solver_create": ([ctypes.POINTER(P), P, ctypes.POINTER(_Params)], I),
@@ -147,12 +157,6 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "molt_batch_step": ([VP, VP, ctypes.POINTER(D), I, VP, ctypes.POINTER(I), ctypes.POINTER(D),
                              ctypes.POINTER(I)], I),
     }
-    for name, (args, res) in sig.items():
-        fn = getattr(lib, name)
-        fn.argtypes = args
-        fn.restype = res
-    _lib = lib
-    return lib
 
 
 def _check(status: int, handle=None):

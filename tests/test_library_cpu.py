@@ -133,3 +133,56 @@ def test_missing_library_fails_loudly(tmp_path):
             molt.load_library(str(tmp_path / "libmolt.so"))
     finally:
         molt._lib = saved
+
+
+def _c_kind(decl: str):
+    t = " ".join(decl.split())
+    if t == "void":
+        return None
+    if "*" in t:
+        return "p"
+    if "double" in t:
+        return "d"
+    if "long long" in t:
+        return "q"
+    return "i"   # int, unsigned, enums
+
+
+def _ctypes_kind(t):
+    if t is None:
+        return None
+    if t in (ctypes.c_int, ctypes.c_uint):
+        return "i"
+    if t is ctypes.c_double:
+        return "d"
+    if t is ctypes.c_longlong:
+        return "q"
+    return "p"   # c_void_p, c_char_p, POINTER(...)
+
+
+def test_binding_signatures_match_the_header():
+    # Every entry point declared in include/molt.h has a ctypes signature in the binding with the same
+    # number of arguments and the same kind (integer / double / 64-bit integer / pointer) per
+    # argument and for the result.
+    import re
+
+    from paper_1611_04214_gb300 import molt
+    text = open(os.path.join(ROOT, "include", "molt.h")).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    decls = {}
+    for m in re.finditer(r"([A-Za-z_][\w\s\*]*?)\b(molt_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text):
+        ret, name, params = m.group(1), m.group(2), m.group(3).strip()
+        ret = ret.replace("extern", "").strip()
+        kinds = []
+        if params not in ("", "void"):
+            for prm in params.split(","):
+                prm = prm.strip()
+                prm = re.sub(r"\b[A-Za-z_]\w*$", "", prm) if not prm.endswith("*") else prm
+                kinds.append(_c_kind(prm))
+        decls[name] = (kinds, _c_kind(ret))
+    sig = molt.signatures()
+    assert set(decls) == set(sig), (sorted(set(decls) ^ set(sig)))
+    for name, (args, res) in sig.items():
+        assert [_ctypes_kind(a) for a in args] == decls[name][0], name
+        assert _ctypes_kind(res) == decls[name][1], name
