@@ -111,7 +111,9 @@ molt_status molt_set_bc(molt_solver* solver, int bc);
  * MOLT_EXEC_HOST_LOOP: the host launches each iteration and reads the residual back after it
  *   (also used while profiling is enabled). */
 typedef enum { MOLT_EXEC_HOST_LOOP = 0, MOLT_EXEC_GRAPH = 1 } molt_execution;
+/* mode: a molt_execution value.  Errors: MOLT_ERR_ARG (null solver or unknown mode). */
 molt_status molt_set_execution(molt_solver* solver, int mode);
+/* Stages that ran the host-driven loop because their graph could not be built (0 for NULL). */
 long long molt_graph_fallbacks(const molt_solver* solver);
 
 /* Forget the time history (BDF2 previous level, SDC2 level-[0] state). */
