@@ -495,13 +495,14 @@ long long molt_fch1d_launches(const molt_fch1d* solver);
  *        + (3X - 3X^2 + X^3) W,
  * so that Lap v = K W / a exactly (the first step starts from W = v^n; later steps carry W).
  * Fields [ny][nx] row-major, x fastest, FP32 or FP64 per params->precision, periodic or Neumann
- * (the grid conventions of molt_grid_create).  Each iteration runs 26 one-field line sweeps, one
- * pointwise kernel and 12 linear combinations, and synchronizes `stream` to read the residual.
+ * (the grid conventions of molt_grid_create).  Regrouped by linearity, each iteration runs 14
+ * one-field line sweeps, one pointwise kernel and 11 linear combinations, and synchronizes
+ * `stream` to read the residual.
  * Errors are reported by molt_last_error(NULL). */
 typedef struct molt_fch2d molt_fch2d;
 
 /* nx in [M + 2, the one-field row kernel's limit], ny >= M + 2, nx * ny < 2^31, Lx, Ly > 0, bc
- * periodic or Neumann, eta finite; params as molt_solver_create.  The solver owns 24 fields of
+ * periodic or Neumann, eta finite; params as molt_solver_create.  The solver owns 23 fields of
  * nx * ny values and the column scan scratch.  Errors: MOLT_ERR_ARG, MOLT_ERR_UNSUPPORTED
  * (Dirichlet), MOLT_ERR_OOM. */
 molt_status molt_fch2d_create(molt_fch2d** solver, int nx, int ny, double Lx, double Ly, molt_bc bc, double eta,

@@ -10,10 +10,15 @@
 //        + (3X - 3X^2 + X^3) W,
 //   c_eta = dt eta eps^4 / a^2, c_f = dt eps^2 / a^2, c_p = dt / a,
 //   p = -eps^2 f' Lap v + f f' - eta eps^2 f,  Lap v = K W / a (exact for the discrete operators).
-// The first step starts from W = v^n; later steps carry W.  One iteration is 26 one-field line
-// sweeps (rows through the row kernels, columns through the column kernels), one pointwise kernel
-// and 12 linear combinations over the [ny][nx] field, then the residual read (one stream
-// synchronization per iteration).  The stopping rule is the single-grid solver's (FP32: the
+// The first step starts from W = v^n; later steps carry W.  By linearity the terms regroup into
+// products of H_x, H_y on a few combinations (with A = (3 + c_eta) v - c_f f, B = -3v + c_p p):
+//   C = K A + M^{-1} B = M^{-1} (2A + B) - H_x A - H_y A,
+//   D = 3W - 3XW + X^2 W = M^{-1} E - H_x E - H_y E + X W,  E = X W - 3W,
+//   W_new = M^{-2} v^n + K C + X D = M^{-2} v^n + M^{-1} (2C + D) - H_x (C + D) - H_y (C + D) + D,
+// 14 one-field line sweeps per iteration (11 here, 3 for v, Lap v and X W of the new W; rows
+// through the row kernels, columns through the column kernels), one pointwise kernel and 11 linear
+// combinations over the [ny][nx] field, then the residual read (one stream synchronization per
+// iteration).  The stopping rule is the single-grid solver's (FP32: the
 // tolerance floored at 2 ulp of max|v| and the stall rule below 64 ulp).
 #include <cuda_runtime.h>
 
@@ -49,12 +54,12 @@ struct Fch2d final : molt_fch2d {
     std::vector<void*> allocs;
     // iterate (v = M^{-1} W), start of step, carried Lap v and the lagged remainder X W
     T *v = nullptr, *vnew = nullptr, *W = nullptr, *Wn = nullptr, *vn = nullptr, *m2vn = nullptr, *lap = nullptr;
-    T *xw = nullptr, *x2w = nullptr, *x3w = nullptr;
-    // pointwise parts and the K products
-    T *f = nullptr, *pp = nullptr, *kv = nullptr, *kkv = nullptr, *mkv = nullptr, *kf = nullptr, *kkf = nullptr;
-    T *kp = nullptr, *mkp = nullptr;
+    T *xw = nullptr;
+    // pointwise parts and the regrouped combinations 2A + B, A, C, E, D, 2C + D, C + D
+    T *f = nullptr, *pp = nullptr, *s1 = nullptr, *aa = nullptr, *cc = nullptr, *ee = nullptr, *dd = nullptr;
+    T *s2 = nullptr, *s3 = nullptr;
     // sweep outputs and combination scratch
-    T *hx = nullptr, *hy = nullptr, *hm = nullptr, *tt = nullptr, *zero = nullptr;
+    T *hx = nullptr, *hy = nullptr, *hm = nullptr, *t1 = nullptr, *tt = nullptr, *zero = nullptr;
     molt::ColScratch<T> cs{};
     unsigned* status = nullptr;
     unsigned* status_host = nullptr;
@@ -78,8 +83,8 @@ struct Fch2d final : molt_fch2d {
     }
 
     bool init() {
-        for (T** q : {&v, &vnew, &W, &Wn, &vn, &m2vn, &lap, &xw, &x2w, &x3w, &f, &pp, &kv, &kkv, &mkv, &kf, &kkf,
-                      &kp, &mkp, &hx, &hy, &hm, &tt, &zero})
+        for (T** q : {&v, &vnew, &W, &Wn, &vn, &m2vn, &lap, &xw, &f, &pp, &s1, &aa, &cc, &ee, &dd, &s2, &s3, &hx,
+                      &hy, &hm, &t1, &tt, &zero})
             if (!alloc(q, n)) return false;
         // column scan scratch of the y sweeps: nx columns of ny nodes in tiles of kColTileRows rows
         const int tiles = (ny + molt::kColTileRows - 1) / molt::kColTileRows;
@@ -121,18 +126,6 @@ struct Fch2d final : molt_fch2d {
         cudaError_t e;
         if ((e = H(0, lp, g, hx, st)) != cudaSuccess || (e = H(1, lp, g, hy, st)) != cudaSuccess) return e;
         return H(0, lp, hy, m, st);
-    }
-
-    // out = K g = 2 M^{-1} g - H_x g - H_y g, with M^{-1} g left in m
-    cudaError_t K(const Lines& lp, const T* g, T* out, T* m, cudaStream_t st) {
-        cudaError_t e = parts(lp, g, m, st);
-        return e != cudaSuccess ? e : lin(out, m, 2.0, hx, -1.0, hy, -1.0, nullptr, 0.0, st);
-    }
-
-    // out = X g = D_x D_y g = M^{-1} g - H_x g - H_y g + g
-    cudaError_t X(const Lines& lp, const T* g, T* out, cudaStream_t st) {
-        cudaError_t e = parts(lp, g, hm, st);
-        return e != cudaSuccess ? e : lin(out, hm, 1.0, hx, -1.0, hy, -1.0, g, 1.0, st);
     }
 
     // v = M^{-1} W, Lap v = K W / a and X W, from the current W
@@ -204,20 +197,25 @@ molt_status Fch2d<T>::step(void* uv, double dt, cudaStream_t st, molt_step_info*
     for (k = 1; k <= p.max_iter; ++k) {
         if ((e = molt::fch_pointwise<T>(static_cast<long long>(n), v, lap, eps * eps, eta * eps * eps, f, pp, st,
                                         &launches)) != cudaSuccess ||
-            (e = K(lp, v, kv, hm, st)) != cudaSuccess ||        // K v
-            (e = K(lp, kv, kkv, mkv, st)) != cudaSuccess ||     // K^2 v, M^{-1} K v
-            (e = K(lp, f, kf, hm, st)) != cudaSuccess ||        // K f
-            (e = K(lp, kf, kkf, hm, st)) != cudaSuccess ||      // K^2 f
-            (e = K(lp, pp, kp, hm, st)) != cudaSuccess ||       // K p
-            (e = H(1, lp, kp, hy, st)) != cudaSuccess ||        // M^{-1} K p
-            (e = H(0, lp, hy, mkp, st)) != cudaSuccess ||
-            (e = X(lp, xw, x2w, st)) != cudaSuccess ||          // X^2 W
-            (e = X(lp, x2w, x3w, st)) != cudaSuccess ||         // X^3 W
-            // W_new = M^{-2} v^n - 3 M^{-1} K v + (3 + c_eta) K^2 v - c_f K^2 f + c_p M^{-1} K p
-            //         + 3 X W - 3 X^2 W + X^3 W
-            (e = lin(tt, m2vn, 1.0, mkv, -3.0, kkv, 3.0 + c_eta, kkf, -c_f, st)) != cudaSuccess ||
-            (e = lin(tt, tt, 1.0, mkp, c_p, xw, 3.0, x2w, -3.0, st)) != cudaSuccess ||
-            (e = lin(Wn, tt, 1.0, x3w, 1.0, nullptr, 0.0, nullptr, 0.0, st)) != cudaSuccess ||
+            // 2A + B and A
+            (e = lin(s1, v, 3.0 + 2.0 * c_eta, f, -2.0 * c_f, pp, c_p, nullptr, 0.0, st)) != cudaSuccess ||
+            (e = lin(aa, v, 3.0 + c_eta, f, -c_f, nullptr, 0.0, nullptr, 0.0, st)) != cudaSuccess ||
+            // C = M^{-1} (2A + B) - H_x A - H_y A
+            (e = H(1, lp, s1, t1, st)) != cudaSuccess || (e = H(0, lp, t1, hm, st)) != cudaSuccess ||
+            (e = H(0, lp, aa, hx, st)) != cudaSuccess || (e = H(1, lp, aa, hy, st)) != cudaSuccess ||
+            (e = lin(cc, hm, 1.0, hx, -1.0, hy, -1.0, nullptr, 0.0, st)) != cudaSuccess ||
+            // E = X W - 3W, D = M^{-1} E - H_x E - H_y E + X W
+            (e = lin(ee, W, -3.0, xw, 1.0, nullptr, 0.0, nullptr, 0.0, st)) != cudaSuccess ||
+            (e = H(1, lp, ee, t1, st)) != cudaSuccess || (e = H(0, lp, t1, hm, st)) != cudaSuccess ||
+            (e = H(0, lp, ee, hx, st)) != cudaSuccess ||
+            (e = lin(dd, hm, 1.0, hx, -1.0, t1, -1.0, xw, 1.0, st)) != cudaSuccess ||
+            // W_new = M^{-2} v^n + M^{-1} (2C + D) - H_x (C + D) - H_y (C + D) + D
+            (e = lin(s2, cc, 2.0, dd, 1.0, nullptr, 0.0, nullptr, 0.0, st)) != cudaSuccess ||
+            (e = lin(s3, cc, 1.0, dd, 1.0, nullptr, 0.0, nullptr, 0.0, st)) != cudaSuccess ||
+            (e = H(1, lp, s2, t1, st)) != cudaSuccess || (e = H(0, lp, t1, hm, st)) != cudaSuccess ||
+            (e = H(0, lp, s3, hx, st)) != cudaSuccess || (e = H(1, lp, s3, hy, st)) != cudaSuccess ||
+            (e = lin(tt, hm, 1.0, hx, -1.0, hy, -1.0, dd, 1.0, st)) != cudaSuccess ||
+            (e = lin(Wn, tt, 1.0, m2vn, 1.0, nullptr, 0.0, nullptr, 0.0, st)) != cudaSuccess ||
             (e = from_w(lp, Wn, vnew, a, st)) != cudaSuccess)
             return fail2(MOLT_ERR_CUDA, std::string("sixth-order 2D iteration: ") + cudaGetErrorString(e));
         res = read_max(vnew, v, st, &e);
