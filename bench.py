@@ -734,6 +734,65 @@ def fch1d_leg():
     return out
 
 
+FCH2D = dict(name="fch2d_4096_be_periodic", n=4096, eps=0.18, eta=1.0, dt=0.05, M=6, amp=0.05, seed=0, iters=10,
+             steps=3)
+# per 2D sixth-order iteration (the regrouped form), in values per point: the pointwise kernel 4,
+# 14 one-field sweeps 28, eleven linear combinations 4 + 3 + 4 + 3 + 5 + 3 + 3 + 5 + 3 + 4 + 5 = 42,
+# the residual 2 and, in FP32, max|v| 1; per step: v^n 2, M^{-2} v^n 8, v, Lap v and X W of W 15,
+# the store 2
+FCH2D_VALUES_ITER = {"fp32": 4 + 28 + 42 + 2 + 1, "fp64": 4 + 28 + 42 + 2}
+FCH2D_VALUES_STEP = 2 + 8 + 15 + 2
+FCH2D_SWEEPS_ITER, FCH2D_SWEEPS_STEP = 14, 7
+
+
+def fch2d_leg():
+    """The sixth-order model on a 2D periodic grid (molt_fch2d_*, the paper's last section, split
+    as in Sec. 5.1) of 4096^2 over [0, 2pi]^2: eps = 0.18, eta = 1, BE dt = 0.05, the 2D initial
+    state of Eq. CH2D_initial plus 0.05 U[-1, 1] (SplitMix64, seed 0), a fixed 10 iterations per
+    step, FP32 and FP64.  Every FP32 field (67 MB) is larger than L2.  Line-sweep points per
+    second and the algorithmic HBM fraction of the step (the regrouped, unfused iteration)."""
+    import torch
+
+    from paper_1611_04214_gb300.inputs import paper_ic_2d, uniform_noise
+    from paper_1611_04214_gb300.molt import Fch2D
+    c = FCH2D
+    n = c["n"]
+    peak, _ = _peaks()
+    u0 = paper_ic_2d(n, n) + uniform_noise((n, n), c["amp"], seed=c["seed"])
+    out = {"workload": c["name"], "grid": [n, n], "eps": c["eps"], "eta": c["eta"], "dt": c["dt"], "scheme": "be",
+           "iters_per_step": c["iters"], "steps": c["steps"],
+           "initial_state": "Eq. CH2D_initial + 0.05 U[-1,1], SplitMix64 seed 0",
+           "l2": "inputs larger than L2 (67 MB per FP32 field)"}
+    for prec in ("fp32", "fp64"):
+        with Fch2D(n, n, eps=c["eps"], eta=c["eta"], quad_order=c["M"], tol=1e-30, max_iter=c["iters"],
+                   precision=prec) as s:
+            u = torch.tensor(u0, dtype=torch.float32 if prec == "fp32" else torch.float64, device="cuda")
+            s.step(u, c["dt"], raise_on_nonconvergence=False)     # warm-up (W = v^n)
+            torch.cuda.synchronize()
+            k0 = s.kernel_launches()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            infos = [s.step(u, c["dt"], raise_on_nonconvergence=False) for _ in range(c["steps"])]
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / c["steps"]
+            launches = (s.kernel_launches() - k0) / c["steps"]
+            finite = bool(torch.isfinite(u).all().item())
+        its = sum(i.iters[0] for i in infos) / c["steps"]
+        pts = n * n
+        size = 4 if prec == "fp32" else 8
+        step_bytes = (FCH2D_VALUES_ITER[prec] * its + FCH2D_VALUES_STEP) * size * pts
+        out[prec] = {"ms_per_step": ms, "ms_per_iteration": ms / its, "iters_per_step": its,
+                     "line_sweep_gpts": (FCH2D_SWEEPS_ITER * its + FCH2D_SWEEPS_STEP) * pts / (ms * 1e-3) / 1e9,
+                     "hbm_frac_step_algorithmic": step_bytes / (ms * 1e-3) / 1e9 / peak,
+                     "algorithmic_bytes_per_point_iteration": FCH2D_VALUES_ITER[prec] * size,
+                     "kernel_launches_per_step": launches, "final_residual": infos[-1].residual,
+                     "field_finite": finite}
+        del u
+        torch.cuda.empty_cache()
+    return out
+
+
 def converged_leg():
     """The 1024^2 Neumann BDF2 workload in full (eps = 0.05, dt = 1e-4, 200 steps, u0 = 0.05 U[-1,1]
     seed 0, BE start), every stage iterated to the tolerance 1e-6 (the tolerance of the paper's 2D
@@ -997,6 +1056,12 @@ def run_ours(args, rank, world, dist):
                 fch = fch1d_leg()
             except Exception as exc:
                 fch = {"error": f"{type(exc).__name__}: {exc}"}
+        fch2 = None
+        if not args.skip_fch:
+            try:
+                fch2 = fch2d_leg()
+            except Exception as exc:
+                fch2 = {"error": f"{type(exc).__name__}: {exc}"}
         last = infos[-1]
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                   "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -1012,7 +1077,7 @@ def run_ours(args, rank, world, dist):
                   "ms_per_step_graph_mode": graph_ms, "fp32_vs_fp64": fp64, "batched": batched,
                   "sweep_microbench": sweeps_mb, "vector_ch": vch, "kernels": kernels,
                   "converged_l2_resident": converged, "oracle_parity": parity, "fma_probe": fp64_probe,
-                  "autotune": tuning, "split3d": split3d, "fch1d": fch}
+                  "autotune": tuning, "split3d": split3d, "fch1d": fch, "fch2d": fch2}
         if parity and "ch2d8192_crop1024_fp32" in parity:
             result["ch2d8192_crop1024_err_vs_oracle"] = {p_: parity[f"ch2d8192_crop1024_{p_}"]["max_rel_err_v"]
                                                     for p_ in ("fp32", "fp64")}
@@ -1035,7 +1100,7 @@ def main():
     ap.add_argument("--skip-3d", action="store_true", help="skip the 3D split-stage leg")
     ap.add_argument("--split3d-only", action="store_true",
                     help="run only the 3D split-stage leg and print its JSON (for profiling)")
-    ap.add_argument("--skip-fch", action="store_true", help="skip the sixth-order model leg")
+    ap.add_argument("--skip-fch", action="store_true", help="skip the sixth-order model legs (1D lines and 2D)")
     ap.add_argument("--fch-only", action="store_true",
                     help="run only the sixth-order model leg and print its JSON (for profiling)")
     ap.add_argument("--skip-converged", action="store_true", help="skip the converged 1024^2 Neumann BDF2 leg")
@@ -1077,7 +1142,7 @@ def main():
         return
     if args.fch_only:
         if rank == 0:
-            print(json.dumps({"fch1d": fch1d_leg()}), flush=True)
+            print(json.dumps({"fch1d": fch1d_leg(), "fch2d": fch2d_leg()}), flush=True)
         return
     if dist:
         dist.barrier()
